@@ -1,0 +1,378 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these retypes the oracle's own formulas: each compares it with an
+independent fact (a Fourier-space derivation of Eq. 2, continuity of the two
+branches, Newton's third law, lattice symmetry, a brute-force minimum-image sum,
+a bit-by-bit key built from exact rationals, list completeness by brute force).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0910_0121_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- Eq. 2
+def test_g_golden_rationals():
+    """Eq. 2 at rational points (tests/golden/g_p3m_eq2.txt, worked from the printed branches)."""
+    rows = []
+    for line in open(os.path.join(GOLDEN, "g_p3m_eq2.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        r, g = line.split()
+        rows.append((Fraction(r), Fraction(g)))
+    assert len(rows) >= 6
+    for R, g in rows:
+        assert oracle.g_p3m(float(R)) == pytest.approx(float(g), rel=1e-15, abs=1e-16)
+
+
+def _shat(x):
+    """Fourier transform of the S2 cloud of radius eta, x = k eta (Hockney & Eastwood)."""
+    if x < 1e-2:
+        return 1.0 - x * x / 15.0 + x ** 4 / 560.0
+    return 12.0 / x ** 4 * (2.0 - 2.0 * math.cos(x) - x * math.sin(x))
+
+
+def _j1(x):
+    if x < 1e-3:
+        return x / 3.0
+    return math.sin(x) / x ** 2 - math.cos(x) / x
+
+
+def test_g_equals_s2_cloud_complement():
+    """g_P3M(R) = 1 - r^2 F_S2(r): the force between two S2 clouds of radius eta, from
+    F(r) = (2/pi) int S(k)^2 k j1(kr) dk, must be the Newtonian force minus the PP part
+    (Sec. 2.1: the PP part is Eq. 1 with the cutoff of Eq. 2)."""
+    from scipy.integrate import quad
+
+    edges = np.linspace(0.0, 400.0, 2001)
+    for R in (0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.9, 2.3):
+        f = lambda k: _shat(k) ** 2 * k * _j1(k * R)
+        tot = sum(quad(f, lo, hi, epsabs=1e-14, epsrel=1e-12, limit=200)[0]
+                  for lo, hi in zip(edges[:-1], edges[1:]))
+        g_fourier = 1.0 - R * R * 2.0 / math.pi * tot
+        assert oracle.g_p3m(R) == pytest.approx(g_fourier, abs=2e-9), R
+
+
+def test_g_smooth_at_branch_points():
+    """Both branches of Eq. 2 meet with equal value, slope and curvature at R=1, and
+    g, g', g'' vanish at R=2 (the S2 cutoff is C^2)."""
+    h = 1e-4
+    for R0 in (1.0, 2.0):
+        gl = [oracle.g_p3m(R0 - k * h) for k in range(3)]
+        gr = [oracle.g_p3m(R0 + k * h) for k in range(3)] if R0 == 1.0 else None
+        # one-sided derivatives from the inner branch
+        d1l = (3 * gl[0] - 4 * gl[1] + gl[2]) / (2 * h)
+        d2l = (gl[0] - 2 * gl[1] + gl[2]) / h ** 2
+        if R0 == 1.0:
+            d1r = (-3 * gr[0] + 4 * gr[1] - gr[2]) / (2 * h)
+            d2r = (gr[0] - 2 * gr[1] + gr[2]) / h ** 2
+            assert abs(d1l - d1r) < 1e-6
+            assert abs(d2l - d2r) < 1e-3
+        else:
+            assert abs(gl[0]) < 1e-15
+            assert abs(d1l) < 1e-6
+            assert abs(d2l) < 1e-3
+    assert oracle.g_p3m(0.0) == 1.0
+    assert oracle.g_p3m(1e-3) == pytest.approx(1.0, abs=2e-9)  # Newtonian at r << eta
+
+
+# --------------------------------------------------------------------------- Eq. 1, two bodies
+def test_two_body_direct_sum():
+    """Direct sum for two particles: attractive, along the separation, magnitude
+    m g(r/eta)/r^2, zero at and beyond r_cut, through the periodic boundary too."""
+    L, rc = 1.0, 0.1
+    eta = rc / 2
+    for r in (1e-4, 0.01, 0.05, 0.07, 0.0999, 0.1, 0.2):
+        for x0 in (0.3, 0.99):  # 0.99 puts the partner across the boundary
+            pos = np.array([[x0, 0.5, 0.5], [x0 + r, 0.5, 0.5]])
+            m = np.array([0.25, 0.5], np.float32)
+            a = oracle.direct(pos, m, L, rc)
+            mag = 0.5 * oracle.g_p3m(r / eta) / r ** 2
+            # g is steep near R = 2, so compare on the Newtonian scale m/r^2 there
+            tol = 1e-12 * (0.5 / r ** 2)
+            assert a[0, 0] == pytest.approx(mag, rel=1e-12, abs=tol)
+            assert a[1, 0] == pytest.approx(-0.25 / 0.5 * mag, rel=1e-12, abs=tol)
+            assert np.all(a[:, 1:] == 0)
+            if r >= rc:
+                assert np.all(a == 0)
+    # Newtonian limit
+    pos = np.array([[0.2, 0.2, 0.2], [0.2, 0.2 + 1e-6, 0.2]])
+    a = oracle.direct(pos, np.ones(2, np.float32), L, rc)
+    assert a[0, 1] == pytest.approx(1.0 / 1e-12, rel=1e-9)
+
+
+def test_momentum_conservation_direct():
+    """Pair antisymmetry of Eq. 1: sum_i m_i a_i = 0."""
+    rng = np.random.default_rng(5)
+    N = 600
+    pos = rng.random((N, 3))
+    pos[:100] = 0.5 + 0.01 * rng.standard_normal((100, 3))
+    m = rng.uniform(0.5, 2.0, N).astype(np.float32)
+    a = oracle.direct(pos, m, 1.0, 0.15)
+    p = (m[:, None].astype(np.float64) * a).sum(axis=0)
+    scale = (m[:, None] * np.abs(a)).sum()
+    assert np.all(np.abs(p) < 1e-13 * scale)
+
+
+def test_lattice_zero_force():
+    """A perfect periodic n^3 lattice has zero short-range force by symmetry."""
+    n = 10
+    q = (np.arange(n) + 0.5) / n
+    pos = np.stack(np.meshgrid(q, q, q, indexing="ij"), -1).reshape(-1, 3)
+    a = oracle.direct(pos, np.full(n ** 3, 1.0 / n ** 3, np.float32), 1.0, 0.3)
+    ref = (1.0 / n ** 3) / (1.0 / n) ** 2
+    assert np.abs(a).max() < 1e-12 * ref
+
+
+def test_softening_reduces_to_plummer_inside():
+    """With eps > 0 and r << eta, the pair force is the Plummer form m r/(r^2+eps^2)^1.5."""
+    d = np.array([1e-4, 0, 0])
+    a = oracle.pair_accel(d, 2.0, eta=0.05, eps=3e-4)
+    assert a[0] == pytest.approx(2.0 * 1e-4 / (1e-8 + 9e-8) ** 1.5 * oracle.g_p3m(1e-4 / 0.05), rel=1e-12)
+
+
+# --------------------------------------------------------------------------- keys and sort
+def _key_exact(x, y, z):
+    """Reference key from exact rationals: floor(x * 2^21) per axis for L=1, bits
+    interleaved with x as the high bit of each triplet, clamped to 2^21-1."""
+    ii = []
+    for v in (x, y, z):
+        f = Fraction(v)
+        f = f - math.floor(f)  # periodic wrap into [0,1) on the exact value
+        i = math.floor(f * 2 ** 21)
+        ii.append(min(i, 2 ** 21 - 1))
+    bits = []
+    for b in range(20, -1, -1):
+        bits += [(ii[0] >> b) & 1, (ii[1] >> b) & 1, (ii[2] >> b) & 1]
+    return int("".join(map(str, bits)), 2)
+
+
+def _interleave(ix, iy, iz, nbits):
+    """Bits of three nbits-bit indices interleaved (x high), as a string of digits."""
+    if nbits == 0:
+        return 0
+    s = "".join(f"{(ix >> b) & 1}{(iy >> b) & 1}{(iz >> b) & 1}" for b in range(nbits - 1, -1, -1))
+    return int(s, 2)
+
+
+def test_keys_hand_positions():
+    ulp = np.nextafter(1.0, 0.0)
+    pts = [(0.0, 0.0, 0.0), (0.5, 0.25, 0.125), (ulp, ulp, ulp), (0.999, 1e-9, 0.5),
+           (1.5, -0.25, 2.75), (0.3, 0.7, 0.1), (2 ** -21, 2 ** -22, 3 * 2 ** -21)]
+    for p in pts:
+        w = [oracle.wrap(v, 1.0) for v in p]
+        k = oracle.morton(*[oracle.cell_index(v, 1.0) for v in w])
+        assert k == _key_exact(*p), p
+    # x == L and tiny negatives wrap to 0
+    assert oracle.wrap(1.0, 1.0) == 0.0
+    assert oracle.wrap(-1e-20, 1.0) == 0.0
+    assert oracle.wrap(-0.25, 1.0) == 0.75
+    assert 0.0 <= oracle.wrap(-1e-300, 3.0) < 3.0
+
+
+def test_sort_is_stable_key_order():
+    rng = np.random.default_rng(2)
+    N = 3000
+    pos = np.floor(rng.random((N, 3)) * 4) / 4 + 0.01  # many equal keys
+    t = oracle.Tree(pos, np.ones(N, np.float32), 1.0, 0.1, n_crit=16)
+    key, perm, xyz, _ = t.sorted()
+    ref = np.array([_key_exact(*p) for p in pos], dtype=np.uint64)
+    assert np.array_equal(perm, np.argsort(ref, kind="stable"))
+    assert np.array_equal(key, ref[perm])
+    assert np.array_equal(xyz, pos[perm])
+
+
+# --------------------------------------------------------------------------- tree
+def _cells_by_definition(keys, n_leaf, lmin):
+    """Brute-force node set: the non-empty cells (level, prefix) all of whose proper
+    ancestors are split (count >= n_leaf or level < lmin), levels 0..21."""
+    keys = [int(k) for k in keys]
+    out = set()
+    for k in range(22):
+        pref = {}
+        for key in keys:
+            p = key >> (3 * (21 - k))
+            pref[p] = pref.get(p, 0) + 1
+        for p, c in pref.items():
+            ok = True
+            for a in range(k):
+                pa = p >> (3 * (k - a))
+                cnt = sum(1 for key in keys if key >> (3 * (21 - a)) == pa)
+                if not (a < lmin or cnt >= n_leaf):
+                    ok = False
+                    break
+            if ok:
+                out.add((k, p))
+    return out
+
+
+@pytest.mark.parametrize("seed,N,n_leaf", [(1, 40, 4), (2, 64, 10), (3, 50, 2)])
+def test_tree_matches_definition(seed, N, n_leaf):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((N, 3))
+    pos[: N // 3] = 0.3 + 1e-5 * rng.random((N // 3, 3))  # a tight clump -> deep levels
+    t = oracle.Tree(pos, np.ones(N, np.float32), 1.0, 0.1, n_crit=8, n_leaf=n_leaf)
+    key, _, _, _ = t.sorted()
+    nodes = t.nodes()
+    got = set()
+    for lvl, ix, iy, iz, b, e, skip, leaf, _ in nodes:
+        p = _interleave(int(ix), int(iy), int(iz), int(lvl))
+        got.add((int(lvl), p))
+        # the node's particles are exactly those with that prefix
+        pk = [int(k) >> (3 * (21 - lvl)) for k in key]
+        assert all(pk[j] == p for j in range(b, e))
+        assert (b == 0 or pk[b - 1] != p) and (e == N or pk[e] != p)
+        cnt = e - b
+        assert leaf == (lvl == 21 or (lvl >= t.lmin and cnt < n_leaf))
+    assert got == _cells_by_definition(key, n_leaf, t.lmin)
+    # preorder + skip: node n's subtree is (n, skip) and children tile the range
+    for n, row in enumerate(nodes):
+        lvl, b, e, skip, leaf = row[0], row[4], row[5], row[6], row[7]
+        kids = []
+        c = n + 1
+        while c < skip:
+            kids.append(c)
+            c = nodes[c, 6]
+        if leaf:
+            assert skip == n + 1
+        else:
+            assert kids and nodes[kids[0], 4] == b and nodes[kids[-1], 5] == e
+            for c0, c1 in zip(kids[:-1], kids[1:]):
+                assert nodes[c0, 5] == nodes[c1, 4]
+            assert all(nodes[c, 0] == lvl + 1 for c in kids)
+
+
+def test_moments_and_groups():
+    pos, m, prm = synth.config_uniform32()
+    pos, m = pos[:5000], m[:5000] * 7.0
+    t = oracle.Tree(pos, m, prm["L"], prm["r_cut"], n_crit=prm["n_crit"])
+    _, _, xyz, ms = t.sorted()
+    nodes, mom, grp = t.nodes(), t.moments(), t.groups()
+    for n in range(0, len(nodes), 7):
+        b, e = nodes[n, 4], nodes[n, 5]
+        M = ms[b:e].astype(np.float64).sum()
+        assert mom[n, 0] == pytest.approx(M, rel=1e-13)
+        com = (ms[b:e, None].astype(np.float64) * xyz[b:e]).sum(0) / M
+        assert np.allclose(mom[n, 1:], com, rtol=0, atol=1e-13)
+    # groups tile [0, N) in order, satisfy the rule, and are maximal
+    b = [nodes[g, 4] for g in grp]
+    e = [nodes[g, 5] for g in grp]
+    assert b[0] == 0 and e[-1] == len(pos) and all(x == y for x, y in zip(e[:-1], b[1:]))
+    for g in grp:
+        assert nodes[g, 0] >= t.lmin and (nodes[g, 5] - nodes[g, 4] <= 64 or nodes[g, 7])
+    # mean group size ~ n_crit/4 (Sec. 3.1.2, after Makino 1991), loosely
+    mean = len(pos) / len(grp)
+    assert 64 / 8 < mean < 64 / 1.5
+
+
+# --------------------------------------------------------------------------- lists and force
+def _clustered(N, seed):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((N, 3))
+    k = N // 4
+    pos[:k] = np.mod(0.02 + 0.01 * rng.standard_normal((k, 3)), 1.0)  # a clump across a corner
+    return pos, rng.uniform(0.5, 1.5, N).astype(np.float32) / N
+
+
+@pytest.mark.parametrize("n_crit", [1, 16, 200])
+def test_theta_zero_tree_equals_direct_sum(n_crit):
+    """theta = 0 opens every node that is not pruned, so the list force must equal the
+    brute-force minimum-image sum (only the summation order differs)."""
+    N = 1500
+    pos, m = _clustered(N, 11)
+    L, rc = 1.0, 0.12
+    ref = oracle.direct(pos, m, L, rc)
+    got = oracle.short_force(pos, m, L, rc, theta=0.0, n_crit=n_crit)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() < 1e-12 * scale
+
+
+def test_list_completeness_and_disjointness():
+    """Every particle within r_cut (minimum image) of a group particle is covered by
+    exactly one list entry; entries never overlap."""
+    N = 800
+    pos, m = _clustered(N, 3)
+    L, rc = 1.0, 0.15
+    t = oracle.Tree(pos, m, L, rc, n_crit=12)
+    t.build_lists(0.6)
+    off, kind, idx, sh = t.lists()
+    nodes = t.nodes()
+    _, _, xyz, _ = t.sorted()
+    grp = t.groups()
+    for gi in range(0, len(grp), 3):
+        cov = np.zeros(N, np.int64)
+        for e in range(off[gi], off[gi + 1]):
+            if kind[e] == 0:
+                cov[idx[e]] += 1
+            else:
+                cov[nodes[idx[e], 4]:nodes[idx[e], 5]] += 1
+        assert cov.max() <= 1
+        b, e_ = nodes[grp[gi], 4], nodes[grp[gi], 5]
+        d = xyz[None, :, :] - xyz[b:e_, None, :]
+        d -= np.rint(d / L) * L
+        near = (np.sqrt((d * d).sum(-1)) < rc).any(0)
+        assert np.all(cov[near] == 1)
+
+
+def test_list_shift_is_min_image_for_near_pairs():
+    """The per-entry image shift equals the per-pair minimum image for every pair in range."""
+    N = 600
+    pos, m = _clustered(N, 8)
+    L, rc = 1.0, 0.2
+    t = oracle.Tree(pos, m, L, rc, n_crit=10)
+    t.build_lists(0.0)
+    off, kind, idx, sh = t.lists()
+    nodes = t.nodes()
+    _, _, xyz, _ = t.sorted()
+    grp = t.groups()
+    for gi in range(len(grp)):
+        b, e_ = nodes[grp[gi], 4], nodes[grp[gi], 5]
+        for e in range(off[gi], off[gi + 1]):
+            j = idx[e]
+            d = xyz[j] + sh[e] * L - xyz[b:e_]
+            dm = xyz[j] - xyz[b:e_]
+            dm -= np.rint(dm / L) * L
+            r = np.sqrt((dm * dm).sum(-1))
+            close = r < rc
+            assert np.allclose(d[close], dm[close], atol=1e-15)
+
+
+def test_tree_error_grows_with_theta():
+    """The tree-vs-direct error is zero to rounding at theta = 0 and grows with the
+    opening angle, roughly as a power near 2 (Sec. 3.1.2 error analysis).  Cell sides are
+    powers of two, so on a small set the growth is stepwise; the exponent between
+    theta = 0.3 and 0.9 is checked loosely in [1, 5]."""
+    N = 12000
+    rng = np.random.default_rng(21)
+    pos = rng.random((N, 3))
+    m = np.full(N, 1.0 / N, np.float32)
+    L, rc = 1.0, 0.3
+    ref = oracle.direct(pos, m, L, rc)
+    ths = (0.0, 0.3, 0.45, 0.6, 0.9)
+    errs = []
+    for th in ths:
+        a = oracle.short_force(pos, m, L, rc, th, n_crit=32)
+        errs.append(np.median(np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+    assert errs[0] < 1e-13
+    assert all(e1 < e2 for e1, e2 in zip(errs[1:-1], errs[2:])), errs
+    expo = math.log(errs[-1] / errs[1]) / math.log(ths[-1] / ths[1])
+    assert 1.0 <= expo <= 5.0, (errs, expo)
+
+
+def test_invalid_arguments_rejected():
+    pos = np.random.default_rng(0).random((10, 3))
+    m = np.ones(10, np.float32)
+    with pytest.raises(ValueError):
+        oracle.Tree(pos, m, 1.0, 0.5, 8)  # r_cut must be < L/2
+    bad = pos.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(ValueError):
+        oracle.Tree(bad, m, 1.0, 0.1, 8)
