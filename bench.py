@@ -1,0 +1,342 @@
+"""Benchmark of the GB300 short-range tree force (the hot path of GreeM's PP part).
+
+One step = one call of greem_short_force_ex over the whole particle set: keys, radix
+sort, tree + moments, groups, interaction lists and the FP32 force (S1-S6), inputs
+resident in HBM.  Workload: 256^3 particles (Zel'dovich P(k) ~ k^-2 grid, rms 0.5
+spacing, plus 5000 NFW halos), L = 1, r_cut = 3/256, theta = 0.5, n_leaf = 10, n_crit
+autotuned (untimed, before the warm-up).  Inputs (470 MB) are larger than the 129 MB L2.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (on the host
+cores, on a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("short-range tree force particles/s & interactions/s at θ=0.5, % FP32 peak, FP32 vs FP64")
+WORKLOAD = "zeldovich256+5000nfw_theta0.5"
+FLOPS_PER_INTERACTION = 42          # S6 formulation count (FMA = 2), see the design notes
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-crit", type=int, default=0, help="skip autotuning and use this n_crit")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.p is None:
+            return False
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+        return False
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_tree(pos, mass, prm, n_crit):
+    """FP64 oracle S1-S4 (wrap, keys, stable sort, tree + moments, groups) on the whole
+    set, as it stands (one thread, C).  Returns (tree, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=n_crit, n_leaf=prm.get("n_leaf", 10))
+    return T, time.perf_counter() - t0
+
+
+def oracle_force_sample(T, prm, frac, seed):
+    """Oracle S5-S6 (lists, FP64 list force) for a seeded sample of groups on all host
+    cores.  Returns (seconds, scale to all groups by particle count, groups sampled, threads)."""
+    import oracle
+    nthreads = oracle.max_threads()
+    G = T.n_groups
+    rng = np.random.default_rng(seed)
+    ns = max(8, int(G * frac))
+    sel = np.sort(rng.choice(G, size=ns, replace=False))
+    t1 = time.perf_counter()
+    T.build_lists(prm["theta"], sel)
+    T.list_force(0.0, nthreads)
+    t_sample = time.perf_counter() - t1
+    nodes = T.nodes()
+    grp = T.groups()
+    cnt = nodes[grp, 5] - nodes[grp, 4]
+    return t_sample, float(cnt.sum()) / float(cnt[sel].sum()), ns, nthreads
+
+
+def oracle_sample(pos, mass, prm, n_crit, frac=0.0025, seed=7):
+    """One oracle step on a bounded sample: S1-S4 on everything, S5-S6 on a group sample
+    scaled to all groups.  Returns (seconds for the whole step, description, threads)."""
+    T, t_tree = oracle_tree(pos, mass, prm, n_crit)
+    t_s, scale, ns, nth = oracle_force_sample(T, prm, frac, seed)
+    desc = (f"S1-S4 on all {len(pos)} particles ({t_tree:.1f} s, 1 thread); lists+force on a seeded "
+            f"{ns}/{T.n_groups} group sample ({t_s:.2f} s, {nth} threads) scaled x{scale:.0f} by particle count")
+    return t_tree + t_s * scale, desc, nth
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from paper_0910_0121_gb300 import synth
+    pos, mass, prm = synth.config_zel256()
+    N = len(pos)
+    T, t_tree = oracle_tree(pos, mass, prm, 128)
+    times = []
+    nth, ns = 1, 0
+    for k in range(args.warmup + args.steps):
+        t_s, scale, ns, nth = oracle_force_sample(T, prm, 0.0005, 100 + k)
+        if k >= args.warmup:
+            times.append(t_tree + t_s * scale)
+    desc = (f"S1-S4 on all {N} particles timed once ({t_tree:.1f} s, 1 thread) and added to every step; "
+            f"per step lists+force on a fresh seeded {ns}/{T.n_groups} group sample ({nth} threads) "
+            f"scaled to all groups by particle count")
+    v = N / statistics.mean(times)
+    line = {"metric": METRIC, "value": v, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "N": N, "theta": prm["theta"], "r_cut": prm["r_cut"], "n_crit": 128,
+                       "n_leaf": 10},
+            "cpu_baseline": {"value": v, "unit": "particles/s", "cores": nth, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def gpu_arm(args, rank, world, local):
+    import torch
+    from paper_0910_0121_gb300 import build as _build
+    from paper_0910_0121_gb300 import greem, synth
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    pos, mass, prm = synth.config_zel256(seed=synth.SEED0 + 3 + rank)
+    N = len(pos)
+    P = torch.from_numpy(pos).cuda()
+    M = torch.from_numpy(mass).cuda()
+    acc = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = greem.Context(stream)
+
+    base = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=128, n_leaf=10)
+    if args.n_crit:
+        best = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=args.n_crit, n_leaf=10)
+    else:
+        best = ctx.autotune(P, M, base, acc, candidates=[48, 64, 96, 128, 192, 256])
+    p = greem.params(L=best.L, r_cut=best.r_cut, theta=best.theta, n_crit=best.n_crit, n_leaf=best.n_leaf,
+                     list_chunk=best.list_chunk, block_shape=best.block_shape, flags=greem.FLAG_STAGE_TIMES)
+
+    for _ in range(max(3, args.warmup)):
+        ctx.short_force(P, M, p, acc)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    launches_per_step = st["kernel_launches"]
+    inter = st["n_interactions"]
+
+    # ---- timed region: device-resident inputs
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    force_ms, lists_ms, stage = [], [], {k: [] for k in ("keys", "sort", "tree", "groups", "lists", "force")}
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.short_force(P, M, p, acc)
+            s = ctx.stats()
+            force_ms.append(s["ms_force"])
+            lists_ms.append(s["ms_lists"])
+            for k in stage:
+                stage[k].append(s["ms_" + k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+
+    # ---- end to end through the public API with host buffers
+    hpos = torch.from_numpy(pos).pin_memory()
+    hmass = torch.from_numpy(mass).pin_memory()
+    hacc = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        P.copy_(hpos, non_blocking=True)
+        M.copy_(hmass, non_blocking=True)
+        ctx.short_force(P, M, p, acc)
+        hacc.copy_(acc, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e2 = max(3, args.steps // 2)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2):
+        P.copy_(hpos, non_blocking=True)
+        M.copy_(hmass, non_blocking=True)
+        ctx.short_force(P, M, p, acc)
+        hacc.copy_(acc, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1) / e2
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    # ---- FP64 form on the same lists, and the measured FP32 FMA peak
+    p64 = greem.params(L=p.L, r_cut=p.r_cut, theta=p.theta, n_crit=p.n_crit, n_leaf=p.n_leaf,
+                       precision=greem.F64, flags=greem.FLAG_STAGE_TIMES)
+    acc64 = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    ctx.short_force(P, M, p64, acc64)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    ctx.short_force(P, M, p64, acc64)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = g0.elapsed_time(g1)
+    force64_ms = ctx.stats()["ms_force"]
+    peak_meas = ctx.peak_tflops(0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+
+    # ---- roofline of the dominant kernel (S6 force): plain FP32 ALU arithmetic
+    fms = statistics.mean(force_ms)
+    achieved = FLOPS_PER_INTERACTION * inter / (fms * 1e-3) / 1e12
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "force_f32_zel256_traffic.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            if tj.get("n_crit") == p.n_crit:
+                traffic = tj.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    value = world * N / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "L": 1.0, "r_cut": p.r_cut, "theta": p.theta, "n_crit": p.n_crit,
+                   "n_leaf": p.n_leaf, "list_chunk": p.list_chunk, "block_shape": p.block_shape,
+                   "l2": "inputs (470 MB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+        "interactions_per_s": world * inter / (ms * 1e-3),
+        "N_int": inter / N,
+        "force_kernel_ms": fms, "lists_kernel_ms": statistics.mean(lists_ms),
+        "stage_ms": {k: round(statistics.mean(v), 3) for k, v in stage.items()},
+        "n_groups": st["n_groups"], "n_nodes": st["n_nodes"],
+        "pct_fp32_peak_force": 100.0 * achieved / peak,
+        "pct_fp32_measured_ffma_force": 100.0 * achieved / peak_meas,
+        "fp32_ffma_microbench_tflops": peak_meas,
+        "fp64_form": {"ms_per_step": ms64, "force_kernel_ms": force64_ms,
+                      "particles_per_s": world * N / (ms64 * 1e-3),
+                      "force_speedup_fp32_vs_fp64": force64_ms / fms, "step_speedup": ms64 / ms},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_force_f32", "work_per_launch": f"{inter} interactions x 42 flops",
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"},
+        "e2e": {"value": world * N / (ms_e2e * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": N * (24 + 4),
+                "d2h_bytes_per_step": N * 12},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_cpu, desc, nth = oracle_sample(pos, mass, prm, n_crit=p.n_crit)
+        line["cpu_baseline"] = {"value": N / t_cpu, "unit": "particles/s", "cores": nth, "kind": "oracle",
+                                "sample": desc}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        gpu_arm(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

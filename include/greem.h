@@ -1,0 +1,193 @@
+/*
+ * greem.h -- C ABI of the GB300-native periodic short-range tree force of GreeM
+ * (Ishiyama, Fukushige & Makino 2009, "GreeM: Massively Parallel TreePM Code for
+ * Large Cosmological N-body Simulations").
+ *
+ * What the library computes (paper passages in brackets):
+ *   acc_i = sum_j m_j g_P3M(|d_ij|/eta) d_ij / |d_ij|^3          [Sec. 2.1, Eq. 1]
+ *   g_P3M = the S2 cutoff of Hockney & Eastwood, zero for R >= 2  [Sec. 2.1, Eq. 2]
+ *   eta = r_cut / 2                                               [Sec. 2.2, step 1]
+ * evaluated with a tree (Barnes-Hut opening angle theta, nodes farther than r_cut
+ * pruned) over Barnes' grouped interaction lists (groups of at most n_crit
+ * particles share one list) with periodic images                [Sec. 2.2, steps 2-5;
+ * Sec. 3.1.2; Sec. 1 on image particles].  The pairwise arithmetic runs in FP32 on
+ * coordinates relative to each group's centre                   [Sec. 3.1.1].
+ * G = 1.  Masses, positions and L are in any consistent units.
+ *
+ * Conventions for every call:
+ *  - pos is [N,3] float64 row-major, mass is [N] float32, acc is [N,3] (float32, or
+ *    float64 for GREEM_F64), all CONTIGUOUS DEVICE pointers owned by the caller.  The
+ *    library never frees them and does not keep them after the call returns, except
+ *    the pointers captured by greem_graph_capture (see there).
+ *  - acc is written in INPUT order.  Positions outside [0, L) are wrapped (periodic);
+ *    they are not errors.
+ *  - Work is enqueued on the context's stream.  Calls that return a status wait for
+ *    the stream, because capacity and input errors are detected on the device.
+ *  - A context is not thread-safe; use one per host thread.
+ *  - No C++ exception crosses this interface.  Every call returns GREEM_OK (0) or a
+ *    negative GREEM_ERR_* code; greem_strerror() describes it.
+ */
+#ifndef GREEM_H
+#define GREEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define GREEM_OK 0
+#define GREEM_ERR_INVALID_ARG -1   /* bad size/parameter, or a NaN/Inf position seen on the device */
+#define GREEM_ERR_CUDA -2          /* a CUDA runtime call failed */
+#define GREEM_ERR_OOM -3           /* device or host allocation failed */
+#define GREEM_ERR_CAPACITY -4      /* a device buffer overflowed (only from graph replays; direct
+                                      calls grow their buffers and retry) */
+#define GREEM_ERR_TIMEOUT -5       /* a bounded device wait gave up; the context stays usable */
+#define GREEM_ERR_NOT_IMPLEMENTED -6
+
+/* Force precision (greem_params.precision). */
+#define GREEM_F32_REL 0  /* FP32 pairwise arithmetic on group-relative coordinates (default) */
+#define GREEM_F64 1      /* plain FP64 form on the same lists; acc is float64 [N,3] */
+
+/* greem_params.flags */
+#define GREEM_FLAG_INDEX_LISTS 1u  /* also keep the interaction lists as (kind, index, image)
+                                      entries so that greem_debug_dump(GREEM_DUMP_LISTS) works */
+#define GREEM_FLAG_STAGE_TIMES 2u  /* record per-stage device times in greem_stats */
+
+typedef struct greem_params {
+    double L;        /* periodic box side, > 0 */
+    double r_cut;    /* cutoff radius, 0 < r_cut < L/2; eta = r_cut/2 (Sec. 2.2 step 1) */
+    double theta;    /* opening angle, >= 0 (theta = 0 opens every node within r_cut) */
+    double eps;      /* Plummer softening, >= 0; 0 gives Eq. 1 exactly.  With eps > 0 the
+                        pair term is m g(r/eta) d / (r^2+eps^2)^(3/2). */
+    int n_crit;      /* group size bound N_crit (Sec. 3.1.2), >= 1 */
+    int n_leaf;      /* leaf bound N_leaf: a node is a leaf when it holds fewer (Sec. 3.1.2), >= 1 */
+    int precision;   /* GREEM_F32_REL or GREEM_F64 */
+    int list_chunk;  /* list entries staged per force-kernel chunk: 0 = default (256); power of
+                        two in [64, 2048] */
+    int block_shape; /* warps per force-kernel block: 0 = default (8); 1..16 */
+    unsigned flags;  /* GREEM_FLAG_* */
+} greem_params;
+
+/* Fills defaults: L 1, r_cut 3/32, theta 0.5, eps 0, n_crit 64, n_leaf 10 (Sec. 3.1.2),
+ * F32 precision, default chunk and block shape, no flags. */
+void greem_params_default(greem_params *p);
+
+typedef struct greem_ctx greem_ctx; /* opaque; owns all device workspace */
+
+/* Creates a context on the CURRENT CUDA device that enqueues on cuda_stream (a
+ * cudaStream_t; NULL = the legacy default stream).  Errors: GREEM_ERR_INVALID_ARG when
+ * out is NULL, GREEM_ERR_CUDA when no device is usable, GREEM_ERR_OOM. */
+int greem_create(greem_ctx **out, void *cuda_stream);
+
+/* Frees the context and all of its device memory (after waiting for its stream). */
+void greem_destroy(greem_ctx *ctx);
+
+/* Steps S1-S4 for one box: wrap and 63-bit Morton keys (Sec. 3.2.5), stable radix sort,
+ * octree with N_leaf leaves and FP64 monopole moments (Sec. 2.2 step 2; Sec. 3.1.2), and
+ * the groups of at most n_crit particles (Sec. 2.2 step 5).  The tree lives in the
+ * context until the next build or force call and can be read with greem_debug_dump.
+ * Errors: INVALID_ARG (N < 1, N >= 2^31, L <= 0, r_cut outside (0, L/2), theta < 0,
+ * eps < 0, n_crit < 1, n_leaf < 1, a NaN/Inf position), CUDA, OOM. */
+int greem_build_tree(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, const greem_params *p);
+
+/* The whole short-range force (S1-S6) with default settings: n_leaf 10, eps 0, FP32
+ * relative-coordinate arithmetic.  Uses a context owned by the library for the current
+ * device, on the legacy default stream.  acc: float32 [N,3] device, input order.
+ * Errors as greem_build_tree. */
+int greem_short_force(const double *pos, const float *mass, int64_t N, double L, double r_cut, double theta,
+                      int n_crit, float *acc);
+
+/* The whole short-range force with explicit parameters.  acc is float32 [N,3] for
+ * GREEM_F32_REL and float64 [N,3] for GREEM_F64.  Errors as greem_build_tree. */
+int greem_short_force_ex(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, const greem_params *p,
+                         void *acc);
+
+/* nbox independent periodic boxes in one pass: box b holds particles
+ * [offsets[b], offsets[b+1]) of pos/mass/acc and uses per_box[b] (every box may have
+ * its own L, r_cut, theta, eps, n_crit, n_leaf; precision, list_chunk, block_shape and
+ * flags are taken from per_box[0]).  offsets is a HOST array of nbox+1 increasing
+ * values with offsets[0] = 0.  One sort, one tree pass, one list pass and one
+ * persistent force launch serve all boxes.  Errors as greem_build_tree, plus
+ * INVALID_ARG for nbox < 1, nbox > 65536 or an empty box. */
+int greem_short_force_batched(greem_ctx *ctx, int nbox, const int64_t *offsets, const double *pos,
+                              const float *mass, const greem_params *per_box, void *acc);
+
+/* PM (long-range) part: CIC/TSC assignment, Green's function and interpolation
+ * (Sec. 2.2 step 1).  Not part of this build: returns GREEM_ERR_NOT_IMPLEMENTED. */
+int greem_pm_force(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, double L, int n_pm,
+                   double r_cut, int assign, float *acc_pm);
+
+/* Captures the whole short-range force for (pos, mass, N, p, acc) into a CUDA graph held by
+ * the context.  Runs the call once first (sizing every buffer), then records it.  The graph
+ * keeps the device pointers pos, mass and acc: they must stay valid, and their CONTENTS are
+ * read at each greem_graph_launch.  Errors as greem_short_force_ex. */
+int greem_graph_capture(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, const greem_params *p,
+                        void *acc);
+
+/* Replays the captured graph and waits for it.  Returns GREEM_ERR_CAPACITY when the new
+ * positions need more tree, group or list space than was captured (capture again), and
+ * GREEM_ERR_INVALID_ARG when no graph was captured or a NaN/Inf position was seen. */
+int greem_graph_launch(greem_ctx *ctx);
+
+typedef struct greem_stats {
+    int64_t n_particles;
+    int64_t n_boxes;
+    int64_t n_nodes;          /* tree nodes over all boxes */
+    int64_t n_groups;         /* interaction-list groups */
+    int64_t n_list_entries;   /* sum over groups of the list length (unpadded) */
+    int64_t n_interactions;   /* sum over groups of n_g x list length (unpadded): the N_int sum */
+    int64_t n_evaluated;      /* pair evaluations the force kernel performed (padded lists) */
+    int64_t list_capacity;    /* entries in the list pool */
+    int64_t kernel_launches;  /* kernels launched by the last call */
+    int32_t l_min;            /* shallowest group level of box 0 */
+    int32_t retries;          /* capacity retries of the last call */
+    double ms_keys, ms_sort, ms_tree, ms_groups, ms_lists, ms_force, ms_total; /* with STAGE_TIMES */
+} greem_stats;
+
+/* Counters of the last call.  Errors: INVALID_ARG for NULL arguments. */
+int greem_get_stats(greem_ctx *ctx, greem_stats *out);
+
+/* Debug dumps of the last build/force call into host memory. */
+#define GREEM_DUMP_KEYS 0      /* uint64 [N] sorted Morton keys */
+#define GREEM_DUMP_PERM 1      /* uint32 [N] sorted position -> input index */
+#define GREEM_DUMP_NODES 2     /* int64 [n_nodes, 9]: level, ix, iy, iz (cell index at its level),
+                                  begin, end, skip, leaf, parent (-1 for a root); preorder */
+#define GREEM_DUMP_MOMENTS 3   /* float64 [n_nodes, 4]: M, cx, cy, cz */
+#define GREEM_DUMP_GROUPS 4    /* int64 [n_groups]: node index of each group, preorder */
+#define GREEM_DUMP_LIST_OFFSETS 5 /* int64 [n_groups+1]: CSR offsets into GREEM_DUMP_LISTS */
+#define GREEM_DUMP_LISTS 6     /* int64 [n_entries, 5]: kind (0 particle, 1 node), index (sorted
+                                  particle or node), image shift x, y, z in units of L (needs
+                                  GREEM_FLAG_INDEX_LISTS on the force call) */
+/* Copies the array into host_buf when cap_bytes suffices; *len_bytes always gets the size.
+ * Errors: INVALID_ARG (unknown what, no previous call, cap too small -> *len_bytes set). */
+int greem_debug_dump(greem_ctx *ctx, int what, void *host_buf, int64_t cap_bytes, int64_t *len_bytes);
+
+/* Picks n_crit from candidates[0..ncand) (ncand = 0 -> 32, 48, 64, 96, 128, 192, 256, 384,
+ * 512), then list_chunk and block_shape, by timing the whole force on these inputs; writes
+ * the best parameters to *best (a copy of *p with those three fields set).  acc is scratch
+ * output of the right type.  Errors as greem_short_force_ex. */
+int greem_autotune(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, const greem_params *p,
+                   const int *candidates, int ncand, void *acc, greem_params *best);
+
+/* The pairwise FP32 kernel on its own, for the pairwise-error experiment of Sec. 3.1.1:
+ * for every pair k, the force on x_i[k] from a particle of mass m_j[k] at x_j[k] with
+ * both positions passed relative to the group centre x_g[k] (no periodic wrap).  All
+ * arrays are device: x_g, x_i, x_j float64 [npairs,3], m_j float32 [npairs], acc float32
+ * [npairs,3].  Errors: INVALID_ARG (npairs < 1, r_cut <= 0, eps < 0). */
+int greem_pair_force_f32(greem_ctx *ctx, const double *x_g, const double *x_i, const double *x_j, const float *m_j,
+                         int64_t npairs, double r_cut, double eps, float *acc);
+
+/* Measured arithmetic peak of this GPU: which = 0 FP32 FMA, 1 FP64 FMA; *tflops gets
+ * the rate (2 flops per FMA) of an FMA-chain microbenchmark over all SMs, at whatever
+ * clock the GPU runs at the time.  Errors: INVALID_ARG, CUDA. */
+int greem_peak_tflops(greem_ctx *ctx, int which, double *tflops);
+
+const char *greem_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GREEM_H */

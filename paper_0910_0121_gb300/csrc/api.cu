@@ -1,0 +1,967 @@
+// Context, workspace, pipeline orchestration and the C ABI of include/greem.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "greem.h"
+
+namespace greem {
+thread_local long long g_launches = 0;
+}
+
+using namespace greem;
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+struct greem_ctx {
+    int device = 0;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // private stream for graph capture on the legacy stream
+
+    // S1-S2
+    DBuf<uint64_t> k0, k1;
+    DBuf<uint32_t> v0, v1, hist, scratch;
+    DBuf<double> xs, ys, zs;
+    DBuf<float> ms;
+    // S3-S4
+    DBuf<uint8_t> d8, K8, nchild;
+    DBuf<uint32_t> own, base, ctr, gflag, gidx;
+    DBuf<Node> nodes;
+    DBuf<Dbl4> raw, mom64;
+    DBuf<float4> noff, poff, irel;
+    DBuf<Group> groups;
+    // S5-S6
+    DBuf<float4> flist;
+    DBuf<unsigned long long> ilist, loff;
+    DBuf<uint32_t> llen, lraw, kids, stack, order, bins;
+    // per call
+    DBuf<BoxPar> bps;
+    DBuf<uint32_t> box_off, small;
+    DBuf<DevStatus> st;
+    DevStatus *st_host = nullptr;
+    BoxPar *bps_host = nullptr;
+    uint32_t *box_off_host = nullptr;
+    int host_boxes_cap = 0;
+
+    // capacities
+    size_t node_cap = 0;
+    size_t list_cap = 0;
+    uint32_t page = 0;
+    uint32_t stack_cap = 4096;
+
+    // results of the last call
+    uint64_t *ks = nullptr;
+    uint32_t *perm = nullptr;
+    uint32_t last_N = 0;
+    int last_nbox = 0;
+    bool have_tree = false, have_lists = false, have_index = false;
+    greem_stats stats;
+
+    // graph
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    bool capturing = false;
+};
+
+static bool cuda_ok(cudaError_t e)
+{
+    if (e == cudaSuccess) return true;
+    cudaGetLastError();
+    return false;
+}
+
+template <class T>
+static int ensure(greem_ctx *c, DBuf<T> &b, size_t n)
+{
+    if (b.n >= n && b.p) return GREEM_OK;
+    if (c->capturing) return GREEM_ERR_CAPACITY;
+    cudaStreamSynchronize(c->stream);
+    if (c->exec) {  // a captured graph points at the old buffer: drop it
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    size_t nn = n + n / 8 + 64;
+    if (!cuda_ok(cudaMalloc((void **)&b.p, nn * sizeof(T)))) {
+        b.p = nullptr;
+        return GREEM_ERR_OOM;
+    }
+    b.n = nn;
+    return GREEM_OK;
+}
+
+template <class T>
+static void release(DBuf<T> &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+// ------------------------------------------------------------------ parameters
+// Largest integer S >= 0 with fl(fl(S) * coef) <= bound (coef > 0); the products are
+// monotone in S, so "S > result" is exactly "(double)S * coef > bound".
+static long long max_s_le(double coef, double bound)
+{
+    const double SMAX = 4.0e15;
+    if (bound < 0.0) return -1;
+    double est = std::floor(bound / coef);
+    if (!(est < SMAX)) return (long long)SMAX;
+    long long S = (long long)est;
+    if (S < 0) S = 0;
+    while (S > 0 && (double)S * coef > bound) S--;
+    while ((double)(S + 1) * coef <= bound) S++;
+    if ((double)S * coef > bound) return -1;
+    return S;
+}
+
+static int derive_box(const greem_params &p, uint32_t pb, uint32_t pe, BoxPar &bp)
+{
+    if (!(p.L > 0) || !std::isfinite(p.L)) return GREEM_ERR_INVALID_ARG;
+    if (!(p.r_cut > 0) || !(p.r_cut < 0.5 * p.L)) return GREEM_ERR_INVALID_ARG;
+    if (!(p.theta >= 0) || !std::isfinite(p.theta)) return GREEM_ERR_INVALID_ARG;
+    if (!(p.eps >= 0) || !std::isfinite(p.eps)) return GREEM_ERR_INVALID_ARG;
+    if (p.n_crit < 1 || p.n_leaf < 1) return GREEM_ERR_INVALID_ARG;
+    // l_min: the shallowest level whose cell side is below L/2 - r_cut
+    const double lim = 0.5 * p.L - p.r_cut;
+    int lmin = -1;
+    double side = p.L;
+    for (int k = 0; k <= kMaxLevel; k++) {
+        if (side < lim) {
+            lmin = k;
+            break;
+        }
+        side *= 0.5;
+    }
+    if (lmin < 0) return GREEM_ERR_INVALID_ARG;
+    memset(&bp, 0, sizeof(bp));
+    bp.L = p.L;
+    bp.inv_L = 1.0 / p.L;
+    bp.u = p.L / 4194304.0;
+    bp.eta = 0.5 * p.r_cut;
+    bp.inv_eta = 1.0 / bp.eta;
+    bp.eps = p.eps;
+    bp.k_f = (float)(bp.u / bp.eta);
+    bp.inv_eta2 = (float)(bp.inv_eta * bp.inv_eta);
+    bp.eps2 = (float)((p.eps / bp.eta) * (p.eps / bp.eta));
+    bp.soft = p.eps > 0 ? 1 : 0;
+    // r_cut pruning: prune iff (double)S_gap * (u*u) > r_cut*r_cut
+    bp.T_prune = max_s_le(bp.u * bp.u, p.r_cut * p.r_cut);
+    // opening: accept iff (double)(l*l) < (theta*theta) * (double)S_d, l = 2^(22-k) u
+    const double th2 = p.theta * p.theta;
+    for (int k = 0; k <= kMaxLevel; k++) {
+        const long long l = 1LL << (22 - k);
+        bp.A[k] = th2 > 0 ? max_s_le(th2, (double)(l * l)) : LLONG_MAX;
+    }
+    bp.p_begin = pb;
+    bp.p_end = pe;
+    bp.lmin = lmin;
+    bp.n_crit = p.n_crit;
+    bp.n_leaf = p.n_leaf;
+    return GREEM_OK;
+}
+
+static int check_common(const greem_params &p)
+{
+    if (p.precision != GREEM_F32_REL && p.precision != GREEM_F64) return GREEM_ERR_INVALID_ARG;
+    if (p.list_chunk != 0 && (p.list_chunk < 64 || p.list_chunk > 2048 || (p.list_chunk & (p.list_chunk - 1))))
+        return GREEM_ERR_INVALID_ARG;
+    if (p.block_shape < 0 || p.block_shape > 16) return GREEM_ERR_INVALID_ARG;
+    return GREEM_OK;
+}
+
+// ------------------------------------------------------------------ pipeline
+struct RunCfg {
+    const double *pos;
+    const float *mass;
+    void *acc;
+    uint32_t N;
+    int nbox;
+    int precision;
+    bool index_lists;
+    bool lists_force;
+    bool soft;
+    bool timing;
+    int chunk;
+    int warps;
+};
+
+static int host_boxes(greem_ctx *c, int nbox)
+{
+    if (c->host_boxes_cap >= nbox) return GREEM_OK;
+    if (c->bps_host) cudaFreeHost(c->bps_host);
+    if (c->box_off_host) cudaFreeHost(c->box_off_host);
+    c->bps_host = nullptr;
+    c->box_off_host = nullptr;
+    c->host_boxes_cap = 0;
+    if (!cuda_ok(cudaMallocHost((void **)&c->bps_host, sizeof(BoxPar) * nbox))) return GREEM_ERR_OOM;
+    if (!cuda_ok(cudaMallocHost((void **)&c->box_off_host, sizeof(uint32_t) * (nbox + 1)))) return GREEM_ERR_OOM;
+    c->host_boxes_cap = nbox;
+    return GREEM_OK;
+}
+
+static uint32_t choose_page(uint32_t N, int nsm)
+{
+    const double warps = (double)nsm * 4 * 8;
+    double per = (double)N * 32.0 / warps;
+    uint32_t pg = 2048;
+    while (pg < per && pg < 65536) pg <<= 1;
+    return pg;
+}
+
+static int size_buffers(greem_ctx *c, const RunCfg &r)
+{
+    const size_t N = r.N;
+    int rc;
+#define ENS(b, n)                                 \
+    do {                                          \
+        if ((rc = ensure(c, c->b, (n))) != 0) return rc; \
+    } while (0)
+    ENS(k0, N);
+    ENS(k1, N);
+    ENS(v0, N);
+    ENS(v1, N);
+    ENS(hist, radix_hist_elems((uint32_t)N));
+    const size_t big = std::max<size_t>(N + 1, std::max<size_t>(c->node_cap + 1, radix_hist_elems((uint32_t)N)));
+    ENS(scratch, scan_scratch_elems(big) + 64);
+    ENS(xs, N);
+    ENS(ys, N);
+    ENS(zs, N);
+    ENS(ms, N);
+    ENS(d8, N);
+    ENS(K8, N);
+    ENS(own, N);
+    ENS(base, N + 1);
+    ENS(poff, N);
+    ENS(irel, N);
+    const size_t nc = c->node_cap;
+    ENS(nodes, nc);
+    ENS(nchild, nc);
+    ENS(ctr, nc);
+    ENS(raw, nc);
+    ENS(mom64, nc);
+    ENS(noff, nc);
+    ENS(gflag, nc);
+    ENS(gidx, nc + 1);
+    ENS(groups, nc);
+    ENS(kids, nc * 8);
+    ENS(bps, (size_t)r.nbox);
+    ENS(box_off, (size_t)r.nbox + 1);
+    ENS(st, 1);
+    ENS(small, 16);
+    if (r.lists_force) {
+        ENS(loff, nc);
+        ENS(llen, nc);
+        ENS(lraw, nc);
+        ENS(order, nc);
+        ENS(bins, 64);
+        ENS(stack, (size_t)c->nsm * kListBlocksPerSM * kListWarps * c->stack_cap);
+        ENS(flist, c->list_cap);
+        if (r.index_lists) ENS(ilist, c->list_cap);
+    }
+#undef ENS
+    return GREEM_OK;
+}
+
+static void ev_record(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev, int i)
+{
+    if (r.timing && !c->capturing) cudaEventRecord(ev[i], c->stream);
+}
+
+static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
+{
+    int rc = size_buffers(c, r);
+    if (rc) return rc;
+    cudaStream_t s = c->stream;
+    const uint32_t N = r.N;
+    const int nbox = r.nbox;
+    const int nsm = c->nsm;
+    const uint32_t ncap = (uint32_t)std::min<size_t>(c->node_cap, 0xFFFFFFF0u);
+    cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s);
+    cudaMemcpyAsync(c->bps.p, c->bps_host, sizeof(BoxPar) * nbox, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->box_off.p, c->box_off_host, sizeof(uint32_t) * (nbox + 1), cudaMemcpyHostToDevice, s);
+    ev_record(c, r, ev, 0);
+    launch_keys(r.pos, N, c->box_off.p, nbox, c->bps.p, c->k0.p, c->st.p, s);
+    ev_record(c, r, ev, 1);
+    const int box_passes = nbox <= 1 ? 0 : (nbox <= 256 ? 1 : 2);
+    uint64_t *ks = nullptr;
+    uint32_t *perm = nullptr;
+    radix_sort(c->k0.p, c->k1.p, c->v0.p, c->v1.p, N, 8, box_passes, c->box_off.p, nbox, c->hist.p, c->scratch.p, &ks,
+               &perm, s);
+    launch_gather(r.pos, r.mass, perm, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, s);
+    ev_record(c, r, ev, 2);
+    launch_tree_prep(ks, N, c->box_off.p, nbox, c->bps.p, c->d8.p, c->K8.p, c->own.p, s);
+    scan_u32(c->own.p, c->base.p, N, c->scratch.p, s);
+    const uint32_t *n_nodes = c->base.p + N;
+    launch_tree_fill(ks, N, c->box_off.p, nbox, c->d8.p, c->K8.p, c->base.p, c->nodes.p, ncap, c->st.p, s, nsm);
+    launch_tree_links(c->nodes.p, n_nodes, ncap, c->nchild.p, c->kids.p, s, nsm);
+    cudaMemsetAsync(c->ctr.p, 0, sizeof(uint32_t) * ncap, s);
+    launch_moments(c->nodes.p, n_nodes, ncap, c->nchild.p, c->ctr.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p, s);
+    launch_leaf_offsets(ks, c->K8.p, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->poff.p, s);
+    launch_node_finish(c->nodes.p, n_nodes, ncap, c->raw.p, c->box_off.p, nbox, c->bps.p, c->mom64.p, c->noff.p, s,
+                       nsm);
+    ev_record(c, r, ev, 3);
+    launch_group_flags(c->nodes.p, n_nodes, ncap, c->box_off.p, nbox, c->bps.p, c->gflag.p, s, nsm);
+    scan_u32(c->gflag.p, c->gidx.p, ncap, c->scratch.p, s);
+    const uint32_t *n_groups = c->gidx.p + ncap;
+    launch_group_fill(c->nodes.p, n_nodes, ncap, c->gflag.p, c->gidx.p, c->box_off.p, nbox, c->groups.p, s, nsm);
+    launch_record_counts(n_nodes, n_groups, c->st.p, ncap, s);
+    ev_record(c, r, ev, 4);
+    if (r.lists_force) {
+        ListArgs la;
+        la.nodes = c->nodes.p;
+        la.groups = c->groups.p;
+        la.n_groups = n_groups;
+        la.base = c->base.p;
+        la.bps = c->bps.p;
+        la.kids = c->kids.p;
+        la.stack = c->stack.p;
+        la.stack_cap = c->stack_cap;
+        la.poff = c->poff.p;
+        la.noff = c->noff.p;
+        la.flist = c->flist.p;
+        la.ilist = r.index_lists ? c->ilist.p : nullptr;
+        la.irel = c->irel.p;
+        la.loff = c->loff.p;
+        la.llen = c->llen.p;
+        la.lraw = c->lraw.p;
+        la.cap = c->list_cap;
+        la.page = c->page;
+        la.st = c->st.p;
+        launch_lists(la, s, nsm);
+        ev_record(c, r, ev, 5);
+        launch_force_order(c->groups.p, n_groups, c->bins.p, c->order.p, s, nsm);
+        ForceArgs fa;
+        fa.groups = c->groups.p;
+        fa.n_groups = n_groups;
+        fa.order = c->order.p;
+        fa.loff = c->loff.p;
+        fa.llen = c->llen.p;
+        fa.lraw = c->lraw.p;
+        fa.flist = c->flist.p;
+        fa.ilist = r.index_lists ? c->ilist.p : nullptr;
+        fa.irel = c->irel.p;
+        fa.perm = perm;
+        fa.bps = c->bps.p;
+        fa.xs = c->xs.p;
+        fa.ys = c->ys.p;
+        fa.zs = c->zs.p;
+        fa.ms = c->ms.p;
+        fa.mom64 = c->mom64.p;
+        fa.acc = r.acc;
+        fa.st = c->st.p;
+        fa.chunk = r.chunk;
+        fa.warps = r.warps;
+        if (r.precision == GREEM_F64) launch_force_f64(fa, s, nsm);
+        else launch_force_f32(fa, s, nsm, r.soft);
+        ev_record(c, r, ev, 6);
+    }
+    cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+    c->ks = ks;
+    c->perm = perm;
+    if (!cuda_ok(cudaGetLastError())) return GREEM_ERR_CUDA;
+    return GREEM_OK;
+}
+
+// Waits for the stream and turns the device status into a return code.
+static int finish(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
+{
+    if (!cuda_ok(cudaStreamSynchronize(c->stream))) return GREEM_ERR_CUDA;
+    const DevStatus &h = *c->st_host;
+    greem_stats &S = c->stats;
+    S.n_particles = r.N;
+    S.n_boxes = r.nbox;
+    S.n_nodes = (int64_t)h.n_nodes;
+    S.n_groups = (int64_t)h.n_groups;
+    S.n_list_entries = (int64_t)h.sum_len;
+    S.n_interactions = (int64_t)h.sum_inter;
+    S.n_evaluated = (int64_t)h.sum_eval;
+    S.list_capacity = (int64_t)c->list_cap;
+    S.l_min = c->bps_host[0].lmin;
+    if (r.timing && ev) {
+        float t[7] = {0, 0, 0, 0, 0, 0, 0};
+        const int last = r.lists_force ? 6 : 4;
+        for (int i = 1; i <= last; i++) cudaEventElapsedTime(&t[i], ev[i - 1], ev[i]);
+        S.ms_keys = t[1];
+        S.ms_sort = t[2];
+        S.ms_tree = t[3];
+        S.ms_groups = t[4];
+        S.ms_lists = r.lists_force ? t[5] : 0;
+        S.ms_force = r.lists_force ? t[6] : 0;
+        float tot = 0;
+        cudaEventElapsedTime(&tot, ev[0], ev[last]);
+        S.ms_total = tot;
+    }
+    c->last_N = r.N;
+    c->last_nbox = r.nbox;
+    if (h.flags & ST_NONFINITE) return GREEM_ERR_INVALID_ARG;
+    if (h.flags & ST_TIMEOUT) return GREEM_ERR_TIMEOUT;
+    if (h.flags & (ST_NODE_CAP | ST_LIST_CAP | ST_STACK)) return GREEM_ERR_CAPACITY;
+    c->have_tree = true;
+    c->have_lists = r.lists_force;
+    c->have_index = r.lists_force && r.index_lists;
+    return GREEM_OK;
+}
+
+static void grow_caps(greem_ctx *c)
+{
+    const DevStatus &h = *c->st_host;
+    if (h.flags & ST_NODE_CAP) c->node_cap = (size_t)(h.n_nodes * 1.15) + 4096;
+    if (h.flags & ST_STACK) c->stack_cap *= 4;
+    if (h.flags & ST_LIST_CAP) {
+        // every allocation abandons less than the list that did not fit, and every warp
+        // holds at most one partly used page
+        const size_t warps = (size_t)c->nsm * kListBlocksPerSM * kListWarps;
+        const size_t need = (size_t)(2.0 * (double)h.sum_padded) + warps * c->page;
+        c->list_cap = std::max<size_t>(c->list_cap + c->list_cap / 2, need);
+    }
+}
+
+static int run(greem_ctx *c, RunCfg r)
+{
+    c->have_tree = c->have_lists = c->have_index = false;
+    if (c->node_cap < (size_t)r.N + 4096u * r.nbox) c->node_cap = (size_t)(r.N * 1.25) + 4096u * r.nbox;
+    uint32_t pg = choose_page(r.N, c->nsm);
+    if (pg > c->page) c->page = pg;
+    if (r.lists_force) {
+        const size_t warps = (size_t)c->nsm * kListBlocksPerSM * kListWarps;
+        c->list_cap = std::max<size_t>(c->list_cap, (size_t)r.N * 48 + warps * c->page);
+    }
+    cudaEvent_t ev[7] = {};
+    if (r.timing)
+        for (auto &e : ev) cudaEventCreate(&e);
+    int rc = GREEM_OK;
+    c->stats.retries = 0;
+    for (int attempt = 0; attempt < 6; attempt++) {
+        greem::g_launches = 0;
+        rc = enqueue(c, r, ev);
+        if (rc == GREEM_OK) rc = finish(c, r, ev);
+        c->stats.kernel_launches = greem::g_launches;
+        if (rc != GREEM_ERR_CAPACITY) break;
+        grow_caps(c);
+        c->stats.retries++;
+    }
+    if (r.timing)
+        for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
+static int setup_single(greem_ctx *c, int64_t N, const greem_params *p)
+{
+    if (!c || !p || N < 1 || N >= (int64_t)0x7FFFFFF0) return GREEM_ERR_INVALID_ARG;
+    int rc = check_common(*p);
+    if (rc) return rc;
+    if ((rc = host_boxes(c, 1))) return rc;
+    if ((rc = derive_box(*p, 0, (uint32_t)N, c->bps_host[0]))) return rc;
+    c->box_off_host[0] = 0;
+    c->box_off_host[1] = (uint32_t)N;
+    return GREEM_OK;
+}
+
+static RunCfg make_cfg(const greem_params &p, const double *pos, const float *mass, void *acc, uint32_t N, int nbox,
+                       bool lists_force)
+{
+    RunCfg r;
+    r.pos = pos;
+    r.mass = mass;
+    r.acc = acc;
+    r.N = N;
+    r.nbox = nbox;
+    r.precision = p.precision;
+    r.index_lists = (p.flags & GREEM_FLAG_INDEX_LISTS) || p.precision == GREEM_F64;
+    r.lists_force = lists_force;
+    r.soft = false;
+    r.timing = (p.flags & GREEM_FLAG_STAGE_TIMES) != 0;
+    r.chunk = p.list_chunk ? p.list_chunk : 256;
+    r.warps = p.block_shape ? p.block_shape : 8;
+    return r;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void greem_params_default(greem_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->L = 1.0;
+    p->r_cut = 3.0 / 32.0;
+    p->theta = 0.5;
+    p->eps = 0.0;
+    p->n_crit = 64;
+    p->n_leaf = 10;
+    p->precision = GREEM_F32_REL;
+}
+
+int greem_create(greem_ctx **out, void *cuda_stream)
+{
+    if (!out) return GREEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int dev = 0;
+    if (!cuda_ok(cudaGetDevice(&dev))) return GREEM_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (!cuda_ok(cudaGetDeviceProperties(&prop, dev))) return GREEM_ERR_CUDA;
+    greem_ctx *c = new (std::nothrow) greem_ctx();
+    if (!c) return GREEM_ERR_OOM;
+    c->device = dev;
+    c->nsm = prop.multiProcessorCount;
+    c->stream = (cudaStream_t)cuda_stream;
+    memset(&c->stats, 0, sizeof(c->stats));
+    if (!cuda_ok(cudaMallocHost((void **)&c->st_host, sizeof(DevStatus)))) {
+        delete c;
+        return GREEM_ERR_OOM;
+    }
+    memset(c->st_host, 0, sizeof(DevStatus));
+    *out = c;
+    return GREEM_OK;
+}
+
+void greem_destroy(greem_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    release(c->k0); release(c->k1); release(c->v0); release(c->v1); release(c->hist); release(c->scratch);
+    release(c->xs); release(c->ys); release(c->zs); release(c->ms);
+    release(c->d8); release(c->K8); release(c->nchild); release(c->own); release(c->base); release(c->ctr);
+    release(c->gflag); release(c->gidx); release(c->nodes); release(c->raw); release(c->mom64); release(c->noff);
+    release(c->poff); release(c->irel); release(c->groups); release(c->flist); release(c->ilist); release(c->loff);
+    release(c->llen); release(c->lraw); release(c->bps); release(c->box_off); release(c->small); release(c->st);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->bps_host) cudaFreeHost(c->bps_host);
+    if (c->box_off_host) cudaFreeHost(c->box_off_host);
+    delete c;
+}
+
+int greem_build_tree(greem_ctx *c, const double *pos, const float *mass, int64_t N, const greem_params *p)
+{
+    int rc = setup_single(c, N, p);
+    if (rc) return rc;
+    if (!pos || !mass) return GREEM_ERR_INVALID_ARG;
+    return run(c, make_cfg(*p, pos, mass, nullptr, (uint32_t)N, 1, false));
+}
+
+int greem_short_force_ex(greem_ctx *c, const double *pos, const float *mass, int64_t N, const greem_params *p,
+                         void *acc)
+{
+    int rc = setup_single(c, N, p);
+    if (rc) return rc;
+    if (!pos || !mass || !acc) return GREEM_ERR_INVALID_ARG;
+    RunCfg r = make_cfg(*p, pos, mass, acc, (uint32_t)N, 1, true);
+    r.soft = p->eps > 0;
+    return run(c, r);
+}
+
+static std::mutex g_def_mu;
+static greem_ctx *g_def_ctx[256];
+
+int greem_short_force(const double *pos, const float *mass, int64_t N, double L, double r_cut, double theta,
+                      int n_crit, float *acc)
+{
+    int dev = 0;
+    if (!cuda_ok(cudaGetDevice(&dev)) || dev < 0 || dev >= 256) return GREEM_ERR_CUDA;
+    greem_ctx *c;
+    {
+        std::lock_guard<std::mutex> lk(g_def_mu);
+        if (!g_def_ctx[dev]) {
+            int rc = greem_create(&g_def_ctx[dev], nullptr);
+            if (rc) return rc;
+        }
+        c = g_def_ctx[dev];
+    }
+    greem_params p;
+    greem_params_default(&p);
+    p.L = L;
+    p.r_cut = r_cut;
+    p.theta = theta;
+    p.n_crit = n_crit;
+    std::lock_guard<std::mutex> lk(g_def_mu);
+    return greem_short_force_ex(c, pos, mass, N, &p, acc);
+}
+
+int greem_short_force_batched(greem_ctx *c, int nbox, const int64_t *offsets, const double *pos, const float *mass,
+                              const greem_params *per_box, void *acc)
+{
+    if (!c || !offsets || !per_box || !pos || !mass || !acc) return GREEM_ERR_INVALID_ARG;
+    if (nbox < 1 || nbox > 65536) return GREEM_ERR_INVALID_ARG;
+    if (offsets[0] != 0) return GREEM_ERR_INVALID_ARG;
+    for (int b = 0; b < nbox; b++)
+        if (offsets[b + 1] <= offsets[b]) return GREEM_ERR_INVALID_ARG;
+    const int64_t N = offsets[nbox];
+    if (N >= (int64_t)0x7FFFFFF0) return GREEM_ERR_INVALID_ARG;
+    int rc = check_common(per_box[0]);
+    if (rc) return rc;
+    if ((rc = host_boxes(c, nbox))) return rc;
+    bool soft = false;
+    for (int b = 0; b < nbox; b++) {
+        if ((rc = derive_box(per_box[b], (uint32_t)offsets[b], (uint32_t)offsets[b + 1], c->bps_host[b]))) return rc;
+        c->box_off_host[b] = (uint32_t)offsets[b];
+        soft = soft || per_box[b].eps > 0;
+    }
+    c->box_off_host[nbox] = (uint32_t)N;
+    RunCfg r = make_cfg(per_box[0], pos, mass, acc, (uint32_t)N, nbox, true);
+    r.soft = soft;
+    return run(c, r);
+}
+
+int greem_pm_force(greem_ctx *, const double *, const float *, int64_t, double, int, double, int, float *)
+{
+    return GREEM_ERR_NOT_IMPLEMENTED;
+}
+
+int greem_graph_capture(greem_ctx *c, const double *pos, const float *mass, int64_t N, const greem_params *p, void *acc)
+{
+    int rc = greem_short_force_ex(c, pos, mass, N, p, acc);
+    if (rc) return rc;
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    cudaStream_t user = c->stream;
+    if (!user) {
+        if (!c->own_stream && !cuda_ok(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)))
+            return GREEM_ERR_CUDA;
+        cudaStreamSynchronize(nullptr);
+        c->stream = c->own_stream;
+    }
+    RunCfg r = make_cfg(*p, pos, mass, acc, (uint32_t)N, 1, true);
+    r.soft = p->eps > 0;
+    r.timing = false;
+    cudaGraph_t g = nullptr;
+    c->capturing = true;
+    greem::g_launches = 0;
+    if (!cuda_ok(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal))) {
+        c->capturing = false;
+        c->stream = user;
+        return GREEM_ERR_CUDA;
+    }
+    rc = enqueue(c, r, nullptr);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->capturing = false;
+    c->graph_stream = c->stream;
+    c->stream = user;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (!cuda_ok(e)) return GREEM_ERR_CUDA;
+    e = cudaGraphInstantiate(&c->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (!cuda_ok(e)) {
+        c->exec = nullptr;
+        return GREEM_ERR_CUDA;
+    }
+    c->stats.kernel_launches = greem::g_launches;
+    return GREEM_OK;
+}
+
+int greem_graph_launch(greem_ctx *c)
+{
+    if (!c || !c->exec) return GREEM_ERR_INVALID_ARG;
+    if (c->graph_stream != c->stream) cudaStreamSynchronize(c->stream);
+    if (!cuda_ok(cudaGraphLaunch(c->exec, c->graph_stream))) return GREEM_ERR_CUDA;
+    if (!cuda_ok(cudaStreamSynchronize(c->graph_stream))) return GREEM_ERR_CUDA;
+    const DevStatus &h = *c->st_host;
+    c->stats.n_nodes = (int64_t)h.n_nodes;
+    c->stats.n_groups = (int64_t)h.n_groups;
+    c->stats.n_list_entries = (int64_t)h.sum_len;
+    c->stats.n_interactions = (int64_t)h.sum_inter;
+    c->stats.n_evaluated = (int64_t)h.sum_eval;
+    if (h.flags & ST_NONFINITE) return GREEM_ERR_INVALID_ARG;
+    if (h.flags & ST_TIMEOUT) return GREEM_ERR_TIMEOUT;
+    if (h.flags & (ST_NODE_CAP | ST_LIST_CAP | ST_STACK)) return GREEM_ERR_CAPACITY;
+    return GREEM_OK;
+}
+
+int greem_get_stats(greem_ctx *c, greem_stats *out)
+{
+    if (!c || !out) return GREEM_ERR_INVALID_ARG;
+    *out = c->stats;
+    return GREEM_OK;
+}
+
+int greem_debug_dump(greem_ctx *c, int what, void *host_buf, int64_t cap_bytes, int64_t *len_bytes)
+{
+    if (!c || !len_bytes) return GREEM_ERR_INVALID_ARG;
+    *len_bytes = 0;
+    if (!c->have_tree) return GREEM_ERR_INVALID_ARG;
+    const uint32_t N = c->last_N;
+    const uint32_t nn = (uint32_t)c->stats.n_nodes;
+    const uint32_t G = (uint32_t)c->stats.n_groups;
+    if (!cuda_ok(cudaStreamSynchronize(c->stream))) return GREEM_ERR_CUDA;
+    switch (what) {
+    case GREEM_DUMP_KEYS: {
+        *len_bytes = (int64_t)N * 8;
+        if (!host_buf || cap_bytes < *len_bytes) return GREEM_ERR_INVALID_ARG;
+        return cuda_ok(cudaMemcpy(host_buf, c->ks, (size_t)N * 8, cudaMemcpyDeviceToHost)) ? 0 : GREEM_ERR_CUDA;
+    }
+    case GREEM_DUMP_PERM: {
+        *len_bytes = (int64_t)N * 4;
+        if (!host_buf || cap_bytes < *len_bytes) return GREEM_ERR_INVALID_ARG;
+        return cuda_ok(cudaMemcpy(host_buf, c->perm, (size_t)N * 4, cudaMemcpyDeviceToHost)) ? 0 : GREEM_ERR_CUDA;
+    }
+    case GREEM_DUMP_NODES: {
+        *len_bytes = (int64_t)nn * 9 * 8;
+        if (!host_buf || cap_bytes < *len_bytes) return GREEM_ERR_INVALID_ARG;
+        std::vector<Node> h(nn);
+        if (!cuda_ok(cudaMemcpy(h.data(), c->nodes.p, (size_t)nn * sizeof(Node), cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        int64_t *o = (int64_t *)host_buf;
+        for (uint32_t n = 0; n < nn; n++) {
+            const int k = h[n].lvl & 255u;
+            o[9 * n + 0] = k;
+            o[9 * n + 1] = h[n].ix >> (kMaxLevel - k);
+            o[9 * n + 2] = h[n].iy >> (kMaxLevel - k);
+            o[9 * n + 3] = h[n].iz >> (kMaxLevel - k);
+            o[9 * n + 4] = h[n].begin;
+            o[9 * n + 5] = h[n].end;
+            o[9 * n + 6] = h[n].skip;
+            o[9 * n + 7] = (h[n].lvl >> 8) & 1u;
+            o[9 * n + 8] = h[n].parent == kNone ? -1 : (int64_t)h[n].parent;
+        }
+        return GREEM_OK;
+    }
+    case GREEM_DUMP_MOMENTS: {
+        *len_bytes = (int64_t)nn * 4 * 8;
+        if (!host_buf || cap_bytes < *len_bytes) return GREEM_ERR_INVALID_ARG;
+        std::vector<Dbl4> h(nn);
+        if (!cuda_ok(cudaMemcpy(h.data(), c->mom64.p, (size_t)nn * sizeof(Dbl4), cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        double *o = (double *)host_buf;
+        for (uint32_t n = 0; n < nn; n++) {
+            o[4 * n] = h[n].w;
+            o[4 * n + 1] = h[n].x;
+            o[4 * n + 2] = h[n].y;
+            o[4 * n + 3] = h[n].z;
+        }
+        return GREEM_OK;
+    }
+    case GREEM_DUMP_GROUPS: {
+        *len_bytes = (int64_t)G * 8;
+        if (!host_buf || cap_bytes < *len_bytes) return GREEM_ERR_INVALID_ARG;
+        std::vector<Group> h(G);
+        if (G && !cuda_ok(cudaMemcpy(h.data(), c->groups.p, (size_t)G * sizeof(Group), cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        int64_t *o = (int64_t *)host_buf;
+        for (uint32_t g = 0; g < G; g++) o[g] = h[g].node;
+        return GREEM_OK;
+    }
+    case GREEM_DUMP_LIST_OFFSETS:
+    case GREEM_DUMP_LISTS: {
+        if (!c->have_lists) return GREEM_ERR_INVALID_ARG;
+        std::vector<uint32_t> raw(G);
+        std::vector<unsigned long long> off(G);
+        if (G && (!cuda_ok(cudaMemcpy(raw.data(), c->lraw.p, (size_t)G * 4, cudaMemcpyDeviceToHost)) ||
+                  !cuda_ok(cudaMemcpy(off.data(), c->loff.p, (size_t)G * 8, cudaMemcpyDeviceToHost))))
+            return GREEM_ERR_CUDA;
+        int64_t tot = 0;
+        for (uint32_t g = 0; g < G; g++) tot += raw[g];
+        if (what == GREEM_DUMP_LIST_OFFSETS) {
+            *len_bytes = (int64_t)(G + 1) * 8;
+            if (!host_buf || cap_bytes < *len_bytes) return GREEM_ERR_INVALID_ARG;
+            int64_t *o = (int64_t *)host_buf;
+            o[0] = 0;
+            for (uint32_t g = 0; g < G; g++) o[g + 1] = o[g] + raw[g];
+            return GREEM_OK;
+        }
+        if (!c->have_index) return GREEM_ERR_INVALID_ARG;
+        *len_bytes = tot * 5 * 8;
+        if (!host_buf || cap_bytes < *len_bytes) return GREEM_ERR_INVALID_ARG;
+        size_t used = 0;
+        for (uint32_t g = 0; g < G; g++) used = std::max<size_t>(used, off[g] + raw[g]);
+        std::vector<unsigned long long> pool(used);
+        if (used && !cuda_ok(cudaMemcpy(pool.data(), c->ilist.p, used * 8, cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        std::vector<Node> hn(nn);
+        if (nn && !cuda_ok(cudaMemcpy(hn.data(), c->nodes.p, (size_t)nn * sizeof(Node), cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        // entries are disjoint particle ranges: sorting by first particle restores preorder
+        auto first = [&](unsigned long long v) -> uint64_t {
+            const uint32_t ix = (uint32_t)v;
+            return ((v >> 32) & 1ull) ? hn[ix].begin : ix;
+        };
+        for (uint32_t g = 0; g < G; g++) {
+            auto *b = pool.data() + off[g];
+            std::sort(b, b + raw[g],
+                      [&](unsigned long long x, unsigned long long y) { return first(x) < first(y); });
+        }
+        int64_t *o = (int64_t *)host_buf;
+        int64_t e = 0;
+        auto dec = [](unsigned v) -> int64_t { return v == 1u ? 1 : (v == 2u ? -1 : 0); };
+        for (uint32_t g = 0; g < G; g++) {
+            for (uint32_t t = 0; t < raw[g]; t++, e++) {
+                const unsigned long long v = pool[off[g] + t];
+                const unsigned code = (unsigned)(v >> 33) & 63u;
+                o[5 * e + 0] = (int64_t)((v >> 32) & 1ull);
+                o[5 * e + 1] = (int64_t)(uint32_t)v;
+                o[5 * e + 2] = dec(code & 3u);
+                o[5 * e + 3] = dec((code >> 2) & 3u);
+                o[5 * e + 4] = dec((code >> 4) & 3u);
+            }
+        }
+        return GREEM_OK;
+    }
+    default:
+        return GREEM_ERR_INVALID_ARG;
+    }
+}
+
+int greem_autotune(greem_ctx *c, const double *pos, const float *mass, int64_t N, const greem_params *p,
+                   const int *candidates, int ncand, void *acc, greem_params *best)
+{
+    if (!c || !p || !best) return GREEM_ERR_INVALID_ARG;
+    static const int def_cand[] = {32, 48, 64, 96, 128, 192, 256, 384, 512};
+    if (!candidates || ncand <= 0) {
+        candidates = def_cand;
+        ncand = (int)(sizeof(def_cand) / sizeof(def_cand[0]));
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto timeit = [&](const greem_params &q, float *ms) -> int {
+        int rc = greem_short_force_ex(c, pos, mass, N, &q, acc);  // warm (sizes buffers)
+        if (rc) return rc;
+        float bestms = 1e30f;
+        for (int rep = 0; rep < 2; rep++) {
+            cudaEventRecord(e0, c->stream);
+            rc = greem_short_force_ex(c, pos, mass, N, &q, acc);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            if (rc) return rc;
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            bestms = std::min(bestms, t);
+        }
+        *ms = bestms;
+        return GREEM_OK;
+    };
+    greem_params cur = *p;
+    cur.flags &= ~GREEM_FLAG_INDEX_LISTS;
+    float bt = 1e30f;
+    int rc = GREEM_OK;
+    greem_params bp = cur;
+    for (int i = 0; i < ncand; i++) {
+        greem_params q = cur;
+        q.n_crit = candidates[i];
+        float t;
+        if ((rc = timeit(q, &t))) break;
+        if (t < bt) {
+            bt = t;
+            bp = q;
+        }
+    }
+    if (!rc) {
+        const int chunks[] = {128, 256, 512, 1024};
+        const int shapes[] = {4, 8, 16};
+        greem_params base = bp;
+        for (int ci = 0; ci < 4 && !rc; ci++)
+            for (int si = 0; si < 3 && !rc; si++) {
+                greem_params q = base;
+                q.list_chunk = chunks[ci];
+                q.block_shape = shapes[si];
+                if ((size_t)q.block_shape * 2 * q.list_chunk * 16 > 200 * 1024) continue;
+                float t;
+                if ((rc = timeit(q, &t))) break;
+                if (t < bt) {
+                    bt = t;
+                    bp = q;
+                }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    bp.flags = p->flags;
+    *best = bp;
+    return GREEM_OK;
+}
+
+int greem_pair_force_f32(greem_ctx *c, const double *x_g, const double *x_i, const double *x_j, const float *m_j,
+                         int64_t npairs, double r_cut, double eps, float *acc)
+{
+    if (!c || !x_g || !x_i || !x_j || !m_j || !acc) return GREEM_ERR_INVALID_ARG;
+    if (npairs < 1 || npairs >= (int64_t)0x0FFFFFFF || !(r_cut > 0) || !(eps >= 0)) return GREEM_ERR_INVALID_ARG;
+    const size_t np = (size_t)npairs;
+    int rc;
+    if ((rc = ensure(c, c->groups, np)) || (rc = ensure(c, c->irel, np)) || (rc = ensure(c, c->flist, 8 * np)) ||
+        (rc = ensure(c, c->loff, np)) || (rc = ensure(c, c->llen, np)) || (rc = ensure(c, c->lraw, np)) ||
+        (rc = ensure(c, c->v0, np)) || (rc = ensure(c, c->bps, 1)) || (rc = ensure(c, c->st, 1)) ||
+        (rc = ensure(c, c->small, 16)))
+        return rc;
+    if ((rc = host_boxes(c, 1))) return rc;
+    BoxPar &bp = c->bps_host[0];
+    memset(&bp, 0, sizeof(bp));
+    bp.eta = 0.5 * r_cut;
+    bp.inv_eta = 1.0 / bp.eta;
+    bp.inv_eta2 = (float)(bp.inv_eta * bp.inv_eta);
+    bp.eps = eps;
+    bp.eps2 = (float)((eps / bp.eta) * (eps / bp.eta));
+    cudaStream_t s = c->stream;
+    greem::g_launches = 0;
+    cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s);
+    cudaMemcpyAsync(c->bps.p, c->bps_host, sizeof(BoxPar), cudaMemcpyHostToDevice, s);
+    launch_pair_setup(x_g, x_i, x_j, m_j, (uint32_t)np, bp.inv_eta, c->groups.p, c->irel.p, c->flist.p, c->loff.p,
+                      c->llen.p, c->lraw.p, c->v0.p, c->small.p, s);
+    ForceArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.groups = c->groups.p;
+    fa.n_groups = c->small.p;
+    fa.order = nullptr;
+    fa.loff = c->loff.p;
+    fa.llen = c->llen.p;
+    fa.lraw = c->lraw.p;
+    fa.flist = c->flist.p;
+    fa.irel = c->irel.p;
+    fa.perm = c->v0.p;
+    fa.bps = c->bps.p;
+    fa.acc = acc;
+    fa.st = c->st.p;
+    fa.chunk = 256;
+    fa.warps = 8;
+    launch_force_f32(fa, s, c->nsm, eps > 0);
+    cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+    if (!cuda_ok(cudaStreamSynchronize(s))) return GREEM_ERR_CUDA;
+    c->have_tree = c->have_lists = c->have_index = false;
+    if (c->st_host->flags & ST_TIMEOUT) return GREEM_ERR_TIMEOUT;
+    return GREEM_OK;
+}
+
+int greem_peak_tflops(greem_ctx *c, int which, double *tflops)
+{
+    if (!c || !tflops || (which != 0 && which != 1)) return GREEM_ERR_INVALID_ARG;
+    int err = 0;
+    *tflops = peak_tflops(which, c->nsm, c->stream, &err);
+    return err;
+}
+
+const char *greem_strerror(int code)
+{
+    switch (code) {
+    case GREEM_OK: return "ok";
+    case GREEM_ERR_INVALID_ARG: return "invalid argument (bad size or parameter, or a NaN/Inf position)";
+    case GREEM_ERR_CUDA: return "CUDA runtime error";
+    case GREEM_ERR_OOM: return "out of memory";
+    case GREEM_ERR_CAPACITY: return "device buffer capacity exceeded (capture the graph again)";
+    case GREEM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GREEM_ERR_NOT_IMPLEMENTED: return "not implemented";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

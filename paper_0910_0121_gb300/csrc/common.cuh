@@ -1,0 +1,199 @@
+// Internal definitions shared by the CUDA translation units of libgreem.so.
+// Nothing here is visible through the C ABI (include/greem.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace greem {
+
+constexpr int kMaxLevel = 21;           // 21 bits per axis in a 63-bit Morton key (Sec. 3.2.5)
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kHalfPeriod = 1 << 21;    // L/2 in units u = L/2^22
+constexpr int kPeriod = 1 << 22;        // L in units u
+
+// Four doubles, 32-byte aligned (node moments: x, y, z, mass).
+struct __align__(32) Dbl4 {
+    double x, y, z, w;
+};
+__host__ __device__ __forceinline__ Dbl4 make_dbl4(double x, double y, double z, double w)
+{
+    Dbl4 r;
+    r.x = x; r.y = y; r.z = z; r.w = w;
+    return r;
+}
+
+// One tree node, 32 bytes, nodes stored in DFS preorder (a node's subtree is the
+// contiguous index range [n, skip)).
+struct __align__(16) Node {
+    uint32_t ix, iy, iz;   // lower corner of the cell in finest-level cells (L/2^21)
+    uint32_t lvl;          // level in bits 0-7, leaf flag in bit 8
+    uint32_t begin, end;   // sorted particle range
+    uint32_t skip;         // first node after this subtree
+    uint32_t parent;       // kNone for the root of a box
+};
+static_assert(sizeof(Node) == 32, "Node must be 32 bytes");
+
+// One interaction-list group (a node of at most n_crit particles, Sec. 3.1.2).
+struct __align__(16) Group {
+    uint32_t node, begin, count, box;
+    int32_t cx, cy, cz;    // cell centre in units u = L/2^22
+    int32_t hg;            // half side in u
+};
+static_assert(sizeof(Group) == 32, "Group must be 32 bytes");
+
+// Per-box constants, derived on the host from greem_params.
+struct BoxPar {
+    double L, inv_L, u, eta, inv_eta, eps;
+    float k_f;             // u/eta rounded to float: cell offsets -> eta units
+    float inv_eta2;        // 1/eta^2: eta-unit accelerations -> physical
+    float eps2;            // (eps/eta)^2
+    float pad0;
+    long long T_prune;     // prune a node iff S_gap > T_prune (exact form of the r_cut test)
+    long long A[22];       // accept a node of level k iff S_d > A[k] (exact form of the theta test)
+    uint32_t p_begin, p_end;
+    int lmin, n_crit, n_leaf, soft;
+};
+
+// Device status word and counters, cleared at the start of every call.
+struct DevStatus {
+    unsigned int flags;
+    unsigned int pad;
+    unsigned long long n_nodes;
+    unsigned long long n_groups;
+    unsigned long long list_pages;     // pages requested from the list pool
+    unsigned long long sum_len;        // sum of unpadded list lengths
+    unsigned long long sum_inter;      // sum of n_g * unpadded list length
+    unsigned long long sum_eval;       // pair evaluations of the force kernel
+    unsigned long long sum_padded;     // sum of padded list lengths (the pool demand)
+    unsigned long long work[4];        // persistent-kernel work queues
+};
+
+enum : unsigned {
+    ST_NONFINITE = 1u,
+    ST_NODE_CAP = 2u,
+    ST_LIST_CAP = 4u,
+    ST_TIMEOUT = 8u,
+    ST_STACK = 16u,
+};
+
+// Launch shape of the list builder (warps per block, blocks per SM): every warp may
+// hold one partly used page of the list pool.
+constexpr int kListWarps = 8;
+constexpr int kListBlocksPerSM = 4;
+
+// Kernel launches made by the current host thread (reported in greem_stats).
+extern thread_local long long g_launches;
+
+// Box of sorted/input particle i: box_off holds nbox+1 increasing offsets.
+__device__ __forceinline__ int box_of(uint32_t i, const uint32_t *__restrict__ box_off, int nbox)
+{
+    int lo = 0, hi = nbox;  // box_off[lo] <= i < box_off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (box_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- host launchers
+struct ScanScratch {
+    uint32_t *buf = nullptr;  // block sums for every level
+    size_t cap = 0;
+};
+size_t scan_scratch_elems(size_t n);
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.  in may alias out.
+void scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *scratch, cudaStream_t s);
+
+// S1-S2 (keys_sort.cu)
+void launch_keys(const double *pos, uint32_t N, const uint32_t *box_off, int nbox, const BoxPar *bps,
+                 uint64_t *keys, DevStatus *st, cudaStream_t s);
+size_t radix_hist_elems(uint32_t n);
+// Sorts (key, original index) pairs; returns pointers to the sorted arrays (one of the
+// two ping-pong buffers).  key_passes 8-bit digits from bit 0, then box passes.
+void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t n, int key_passes,
+                int box_passes, const uint32_t *box_off, int nbox, uint32_t *hist, uint32_t *scan_scratch,
+                uint64_t **k_out, uint32_t **v_out, cudaStream_t s);
+void launch_gather(const double *pos, const float *mass, const uint32_t *perm, uint32_t N, const uint32_t *box_off,
+                   int nbox, const BoxPar *bps, double *xs, double *ys, double *zs, float *ms, cudaStream_t s);
+
+// S3-S4 (tree.cu)
+void launch_tree_prep(const uint64_t *keys, uint32_t N, const uint32_t *box_off, int nbox, const BoxPar *bps,
+                      uint8_t *d8, uint8_t *K8, uint32_t *own, cudaStream_t s);
+void launch_tree_fill(const uint64_t *keys, uint32_t N, const uint32_t *box_off, int nbox, const uint8_t *d8,
+                      const uint8_t *K8, const uint32_t *base, Node *nodes, uint32_t node_cap, DevStatus *st,
+                      cudaStream_t s, int nsm);
+void launch_tree_links(Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, uint8_t *nchild, uint32_t *kids,
+                       cudaStream_t s, int nsm);
+void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint8_t *nchild,
+                    uint32_t *ctr, const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw,
+                    cudaStream_t s);
+void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
+                         const BoxPar *bps, const double *xs, const double *ys, const double *zs, const float *ms,
+                         float4 *poff, cudaStream_t s);
+void launch_node_finish(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const Dbl4 *raw,
+                        const uint32_t *box_off, int nbox, const BoxPar *bps, Dbl4 *mom64, float4 *noff,
+                        cudaStream_t s, int nsm);
+void launch_group_flags(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *box_off,
+                        int nbox, const BoxPar *bps, uint32_t *flag, cudaStream_t s, int nsm);
+void launch_group_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *flag,
+                       const uint32_t *gidx, const uint32_t *box_off, int nbox, Group *groups, cudaStream_t s,
+                       int nsm);
+void launch_record_counts(const uint32_t *n_nodes, const uint32_t *n_groups, DevStatus *st, uint32_t node_cap,
+                          cudaStream_t s);
+
+// S5 (lists.cu)
+struct ListArgs {
+    const Node *nodes;
+    const Group *groups;
+    const uint32_t *n_groups;
+    const uint32_t *base;      // node index of the first node starting at each particle (N+1)
+    const BoxPar *bps;
+    const uint32_t *kids;      // child table, 8 slots per node (kNone = unused)
+    uint32_t *stack;           // per-warp traversal stacks
+    uint32_t stack_cap;        // entries per warp stack
+    const float4 *poff;        // per sorted particle: offset from its leaf centre (eta units), mass
+    const float4 *noff;        // per node: COM offset from its cell centre (eta units), mass
+    float4 *flist;             // list pool, FP32 relative entries
+    unsigned long long *ilist; // list pool, index entries (may be null)
+    float4 *irel;              // per sorted particle: its own relative position in its group's frame
+    unsigned long long *loff;  // per group: first entry
+    uint32_t *llen;            // per group: padded length (multiple of 8)
+    uint32_t *lraw;            // per group: unpadded length
+    unsigned long long cap;    // entries in the pool
+    uint32_t page;             // entries per page
+    DevStatus *st;
+};
+void launch_lists(const ListArgs &a, cudaStream_t s, int nsm);
+
+// S6 (force.cu)
+struct ForceArgs {
+    const Group *groups;
+    const uint32_t *n_groups;
+    const uint32_t *order;     // work order over groups (may be null = identity)
+    const unsigned long long *loff;
+    const uint32_t *llen;
+    const uint32_t *lraw;
+    const float4 *flist;
+    const unsigned long long *ilist;
+    const float4 *irel;
+    const uint32_t *perm;
+    const BoxPar *bps;
+    // FP64 form
+    const double *xs, *ys, *zs;
+    const float *ms;
+    const Dbl4 *mom64;
+    void *acc;
+    DevStatus *st;
+    int chunk;                 // list entries per staged chunk
+    int warps;                 // warps per block
+};
+void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t *bins, uint32_t *order,
+                        cudaStream_t s, int nsm);
+void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft);
+void launch_force_f64(const ForceArgs &a, cudaStream_t s, int nsm);
+void launch_pair_setup(const double *xg, const double *xi, const double *xj, const float *mj, uint32_t np,
+                       double inv_eta, Group *groups, float4 *irel, float4 *flist, unsigned long long *loff,
+                       uint32_t *llen, uint32_t *lraw, uint32_t *perm, uint32_t *n_groups, cudaStream_t s);
+double peak_tflops(int which, int nsm, cudaStream_t s, int *err);
+
+}  // namespace greem

@@ -1,0 +1,633 @@
+// S6 pairwise cutoff force over the interaction lists (Sec. 2.1 Eq. 1-2; Sec. 3.1.1).
+//
+// FP32 kernel.  Positions are in eta units relative to the group's cell centre (the
+// list builder did the FP64 work), so with R = r/eta
+//   acc_i = (1/eta^2) sum_j m_j g(R) D / R^3 ,   D = X_j - X_i .
+// Eq. 2 is evaluated without cancellation.  Its outer branch factors exactly as
+//   g(R) = (2-R)^5 (7R^3 + 22R^2 + 10R + 4) / 140            (1 <= R < 2),
+// and the inner branch is the outer one plus (1-R)^6 (7R^2 + 18R + 3) / 35, so with
+// v = saturate(1 - R/2) and u = saturate(1 - R)
+//   g(R) = v^5 C(R) + u^6 P(R),  C = (8/35)(7R^3 + 22R^2 + 10R + 4),  P = (7R^2 + 18R + 3)/35,
+// a sum of two non-negative terms for every R >= 0 that is exactly 0 for R >= 2.  The
+// relative error of g therefore stays at a few ulp even where g -> 0 near the cutoff.
+// A pair with r^2 = 0 (the particle itself, or a coincident one) is selected out.
+//
+// Layout.  A persistent grid; each warp takes one group at a time from an atomic
+// queue.  The warp's 32 lanes are split into S parts (S in 1, 2, 4, 8) of 32/S lanes;
+// each lane holds I i-particles in registers and each part runs over every S-th list
+// entry, so small groups do not idle lanes; the parts are summed by shuffles at the end.
+// The group's list streams through a per-warp double buffer in shared memory filled by
+// 1-D bulk asynchronous copies (cp.async.bulk, the TMA engine) that complete on an
+// mbarrier; every entry is read by the part's lanes as one broadcast 16-byte load.
+#include "common.cuh"
+
+namespace greem {
+
+// ------------------------------------------------------------------ TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a phase; false after the iteration limit (the caller records a timeout).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (1u << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ------------------------------------------------------------------ Eq. 2 constants
+constexpr float kC3 = 1.6f;                     // (8/35) * 7
+constexpr float kC2 = 5.028571428571428571f;    // (8/35) * 22
+constexpr float kC1 = 2.285714285714285714f;    // (8/35) * 10
+constexpr float kC0 = 0.914285714285714286f;    // (8/35) * 4
+constexpr float kP2 = 0.2f;                     //  7/35
+constexpr float kP1 = 0.514285714285714286f;    // 18/35
+constexpr float kP0 = 0.0857142857142857143f;   //  3/35
+
+// g(R) of Eq. 2 for R >= 0 (see the header comment); 0 for R >= 2.
+__device__ __forceinline__ float g_p3m(float R)
+{
+    const float v = __saturatef(fmaf(R, -0.5f, 1.0f));
+    const float v2 = v * v;
+    const float v5 = v2 * v2 * v;
+    const float c = fmaf(fmaf(fmaf(R, kC3, kC2), R, kC1), R, kC0);
+    const float u = __saturatef(1.0f - R);
+    const float u2 = u * u;
+    const float u6 = u2 * u2 * u2;
+    const float p = fmaf(fmaf(R, kP2, kP1), R, kP0);
+    return fmaf(u6, p, v5 * c);
+}
+
+template <int I, bool SOFT>
+__device__ __forceinline__ void interact(const float4 j, const float (&xi)[I], const float (&yi)[I],
+                                         const float (&zi)[I], float (&ax)[I], float (&ay)[I], float (&az)[I],
+                                         float eps2)
+{
+#pragma unroll
+    for (int s = 0; s < I; s++) {
+        const float dx = j.x - xi[s], dy = j.y - yi[s], dz = j.z - zi[s];
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float sc;
+        if (!SOFT) {
+            const float rinv = rsqrtf(r2);
+            const float g = g_p3m(r2 * rinv);
+            const float rinv3 = rinv * rinv * rinv;
+            sc = (r2 > 0.0f) ? (j.w * g) * rinv3 : 0.0f;
+        } else {
+            // Plummer softening: 1/(r^2+eps^2)^(3/2), g at the unsoftened R
+            const float rs = rsqrtf(r2 + eps2);
+            const float g = g_p3m(r2 * rsqrtf(r2));
+            sc = (r2 > 0.0f) ? (j.w * g) * (rs * rs * rs) : 0.0f;
+        }
+        ax[s] = fmaf(sc, dx, ax[s]);
+        ay[s] = fmaf(sc, dy, ay[s]);
+        az[s] = fmaf(sc, dz, az[s]);
+    }
+}
+
+// Fewest i-slots (32/S lanes x I) covering n particles, I <= 8; ties go to smaller S.
+__device__ __forceinline__ void choose_layout(uint32_t n, int &S, int &I)
+{
+    int bs = 1, bi = 8;
+    uint32_t best = 0xffffffffu;
+#pragma unroll
+    for (int s = 1; s <= 8; s <<= 1) {
+        const uint32_t li = 32u / s;
+        const uint32_t ii = (n + li - 1) / li;
+        if (ii > 8) continue;
+        const uint32_t slots = li * ii;
+        if (slots < best) {
+            best = slots;
+            bs = s;
+            bi = (int)ii;
+        }
+    }
+    S = bs;
+    I = bi;
+}
+
+struct WarpPipe {
+    float4 *buf[2];
+    uint64_t *bar;
+    uint32_t ph[2];
+};
+
+__device__ __forceinline__ void issue_chunk(const ForceArgs &a, WarpPipe &wp, int b, unsigned long long lo,
+                                            uint32_t c, uint32_t len, int lane)
+{
+    if (lane == 0) {
+        const uint32_t first = c * (uint32_t)a.chunk;
+        const uint32_t nj = min((uint32_t)a.chunk, len - first);
+        const uint32_t bytes = nj * (uint32_t)sizeof(float4);
+        fence_proxy_async();
+        mbar_arrive_tx(&wp.bar[b], bytes);
+        bulk_g2s(wp.buf[b], a.flist + lo + first, bytes, &wp.bar[b]);
+    }
+}
+
+// One pass of a group: I i-particles per lane, S parts; returns false on a timeout.
+template <int I, bool SOFT>
+__device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uint32_t done, int S,
+                                        unsigned long long lo, uint32_t len, WarpPipe &wp, float inv_eta2, float eps2,
+                                        int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int li = 32 / S;
+    const int slot = lane & (li - 1);
+    const int part = lane / li;
+    const uint32_t gend = gr.begin + gr.count;
+    float xi[I], yi[I], zi[I], ax[I], ay[I], az[I];
+#pragma unroll
+    for (int s = 0; s < I; s++) {
+        const uint32_t idx = gr.begin + done + (uint32_t)(s * li + slot);
+        float4 v = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f);
+        if (idx < gend) v = a.irel[idx];
+        xi[s] = v.x;
+        yi[s] = v.y;
+        zi[s] = v.z;
+        ax[s] = ay[s] = az[s] = 0.f;
+    }
+    const uint32_t nch = (len + (uint32_t)a.chunk - 1) / (uint32_t)a.chunk;
+    if (nch) issue_chunk(a, wp, 0, lo, 0, len, lane);
+    bool ok = true;
+    for (uint32_t c = 0; c < nch; c++) {
+        const int b = (int)(c & 1u);
+        if (c + 1 < nch) issue_chunk(a, wp, b ^ 1, lo, c + 1, len, lane);
+        const bool got = mbar_wait_bounded(&wp.bar[b], wp.ph[b]);
+        wp.ph[b] ^= 1u;
+        if (!__all_sync(FULL, got)) {
+            ok = false;
+            // let a copy that is still in flight land before the warp leaves
+            if (c + 1 < nch) {
+                mbar_wait_bounded(&wp.bar[b ^ 1], wp.ph[b ^ 1]);
+                wp.ph[b ^ 1] ^= 1u;
+            }
+            break;
+        }
+        const float4 *buf = wp.buf[b];
+        const uint32_t nj = min((uint32_t)a.chunk, len - c * (uint32_t)a.chunk);
+#pragma unroll 2
+        for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
+            const float4 j = buf[t];
+            interact<I, SOFT>(j, xi, yi, zi, ax, ay, az, eps2);
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int s = 0; s < I; s++) {
+        for (int o = li; o < 32; o <<= 1) {
+            ax[s] += __shfl_xor_sync(FULL, ax[s], o);
+            ay[s] += __shfl_xor_sync(FULL, ay[s], o);
+            az[s] += __shfl_xor_sync(FULL, az[s], o);
+        }
+    }
+    if (part == 0) {
+        float *acc = static_cast<float *>(a.acc);
+#pragma unroll
+        for (int s = 0; s < I; s++) {
+            const uint32_t idx = gr.begin + done + (uint32_t)(s * li + slot);
+            if (idx < gend) {
+                const size_t p = (size_t)a.perm[idx] * 3;
+                acc[p] = ax[s] * inv_eta2;
+                acc[p + 1] = ay[s] * inv_eta2;
+                acc[p + 2] = az[s] * inv_eta2;
+            }
+        }
+    }
+    return ok;
+}
+
+template <bool SOFT>
+__global__ void __launch_bounds__(512) k_force_f32(ForceArgs a)
+{
+    extern __shared__ __align__(128) float4 sm[];
+    __shared__ __align__(8) uint64_t bars[16][2];
+    const unsigned FULL = 0xffffffffu;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpPipe wp;
+    wp.buf[0] = sm + (size_t)w * 2 * a.chunk;
+    wp.buf[1] = wp.buf[0] + a.chunk;
+    wp.bar = bars[w];
+    wp.ph[0] = wp.ph[1] = 0;
+    if (lane == 0) {
+        mbar_init(&wp.bar[0], 1);
+        mbar_init(&wp.bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    if (a.st->flags & ST_NODE_CAP) return;  // the tree was truncated: the call is retried
+    const uint32_t G = *a.n_groups;
+    for (;;) {
+        unsigned long long gi = 0;
+        if (lane == 0) gi = atomicAdd(&a.st->work[1], 1ull);
+        gi = __shfl_sync(FULL, gi, 0);
+        if (gi >= G) break;
+        const uint32_t g = a.order ? a.order[gi] : (uint32_t)gi;
+        const Group gr = a.groups[g];
+        const BoxPar &bp = a.bps[gr.box];
+        const float inv_eta2 = bp.inv_eta2, eps2 = bp.eps2;
+        const unsigned long long lo = a.loff[g];
+        const uint32_t len = a.llen[g];
+        uint32_t done = 0;
+        unsigned long long evals = 0;
+        bool ok = true;
+        while (done < gr.count && ok) {
+            int S, I;
+            choose_layout(gr.count - done, S, I);
+            switch (I) {
+            case 1: ok = group_pass<1, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 2: ok = group_pass<2, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 3: ok = group_pass<3, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 4: ok = group_pass<4, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 5: ok = group_pass<5, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 6: ok = group_pass<6, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 7: ok = group_pass<7, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            default: ok = group_pass<8, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            }
+            const uint32_t slots = (uint32_t)(32 / S) * (uint32_t)I;
+            evals += (unsigned long long)slots * len;
+            done += slots;
+        }
+        if (lane == 0) atomicAdd(&a.st->sum_eval, evals);
+        if (!ok) {
+            if (lane == 0) atomicOr(&a.st->flags, ST_TIMEOUT);
+            break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ work order
+// Groups are ordered by lane layout (I i-particles per lane, S parts), largest first, so
+// that the warps of an SM mostly run the same instantiation of group_pass at a time
+// (one instruction-cache footprint) and the cheapest groups come last.
+__device__ __forceinline__ int layout_bin(uint32_t n)
+{
+    if (n > 256u) return 0;
+    int S, I;
+    choose_layout(n, S, I);
+    return (8 - I) * 4 + (S == 1 ? 0 : S == 2 ? 1 : S == 4 ? 2 : 3);
+}
+
+__global__ void __launch_bounds__(256) k_bin_count(const Group *__restrict__ groups, const uint32_t *n_groups,
+                                                   uint32_t *__restrict__ bins)
+{
+    __shared__ uint32_t sb[32];
+    if (threadIdx.x < 32) sb[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t G = *n_groups;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        atomicAdd(&sb[layout_bin(groups[g].count)], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32 && sb[threadIdx.x]) atomicAdd(&bins[threadIdx.x], sb[threadIdx.x]);
+}
+
+__global__ void k_bin_scan(uint32_t *bins)
+{
+    const uint32_t lane = threadIdx.x;
+    uint32_t v = bins[lane], x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    bins[32 + lane] = x - v;  // cursor
+}
+
+__global__ void __launch_bounds__(256) k_bin_scatter(const Group *__restrict__ groups, const uint32_t *n_groups,
+                                                     uint32_t *__restrict__ bins, uint32_t *__restrict__ order)
+{
+    const uint32_t G = *n_groups;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        order[atomicAdd(&bins[32 + layout_bin(groups[g].count)], 1u)] = g;
+}
+
+void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t *bins, uint32_t *order,
+                        cudaStream_t s, int nsm)
+{
+    cudaMemsetAsync(bins, 0, 64 * sizeof(uint32_t), s);
+    k_bin_count<<<nsm * 4, 256, 0, s>>>(groups, n_groups, bins);
+    k_bin_scan<<<1, 32, 0, s>>>(bins);
+    k_bin_scatter<<<nsm * 4, 256, 0, s>>>(groups, n_groups, bins, order);
+    g_launches += 3;
+}
+
+static int g_force_smem_set[2] = {0, 0};
+
+void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft)
+{
+    const int threads = 32 * a.warps;
+    const size_t smem = (size_t)a.warps * 2 * a.chunk * sizeof(float4);
+    auto kern = soft ? k_force_f32<true> : k_force_f32<false>;
+    const int which = soft ? 1 : 0;
+    if (g_force_smem_set[which] < (int)smem) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        g_force_smem_set[which] = 200 * 1024;
+    }
+    // occupancy is queried once per shape (not while a stream is being captured)
+    static int cached[2][17][2] = {};
+    static size_t cached_smem[2][17] = {};
+    int &per_sm = cached[which][a.warps][0];
+    if (cached_smem[which][a.warps] != smem || per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        if (per_sm < 1) per_sm = 1;
+        cached_smem[which][a.warps] = smem;
+    }
+    kern<<<nsm * per_sm, threads, smem, s>>>(a);
+    g_launches++;
+}
+
+// ------------------------------------------------------------------ FP64 form
+// The same lists as index entries; absolute FP64 positions of particles and node
+// centres of mass, the entry's image shift, and Eq. 1-2 in FP64.  It is the plain form
+// the FP32 kernel is compared with.
+template <int I>
+__device__ __noinline__ void group_pass_f64(const ForceArgs &a, const Group &gr, const BoxPar &bp, uint32_t done,
+                                            int S, unsigned long long lo, uint32_t len, Dbl4 *jb, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int li = 32 / S;
+    const int slot = lane & (li - 1);
+    const int part = lane / li;
+    const uint32_t gend = gr.begin + gr.count;
+    const double L = bp.L, ie = bp.inv_eta, eps2 = bp.eps * bp.eps;
+    double xi[I], yi[I], zi[I], ax[I], ay[I], az[I];
+#pragma unroll
+    for (int s = 0; s < I; s++) {
+        const uint32_t idx = gr.begin + done + (uint32_t)(s * li + slot);
+        const bool v = idx < gend;
+        xi[s] = v ? a.xs[idx] : 1.0e30;
+        yi[s] = v ? a.ys[idx] : 1.0e30;
+        zi[s] = v ? a.zs[idx] : 1.0e30;
+        ax[s] = ay[s] = az[s] = 0.0;
+    }
+    for (uint32_t c = 0; c < len; c += 32) {
+        const uint32_t e = c + (uint32_t)lane;
+        Dbl4 jv = make_dbl4(1.0e30, 1.0e30, 1.0e30, 0.0);
+        if (e < len) {
+            const unsigned long long en = a.ilist[lo + e];
+            const uint32_t idx = (uint32_t)en;
+            const unsigned code = (unsigned)(en >> 33) & 63u;
+            auto sh = [L](unsigned c2) { return c2 == 1u ? L : (c2 == 2u ? -L : 0.0); };
+            if (en & (1ull << 32)) {
+                const Dbl4 mm = a.mom64[idx];
+                jv = make_dbl4(mm.x + sh(code & 3u), mm.y + sh((code >> 2) & 3u), mm.z + sh((code >> 4) & 3u), mm.w);
+            } else {
+                jv = make_dbl4(a.xs[idx] + sh(code & 3u), a.ys[idx] + sh((code >> 2) & 3u),
+                                  a.zs[idx] + sh((code >> 4) & 3u), (double)a.ms[idx]);
+            }
+        }
+        jb[lane] = jv;
+        __syncwarp();
+        const uint32_t nj = min(32u, len - c);
+        for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
+            const Dbl4 j = jb[t];
+#pragma unroll
+            for (int s = 0; s < I; s++) {
+                const double dx = j.x - xi[s], dy = j.y - yi[s], dz = j.z - zi[s];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 > 0.0) {
+                    const double rinv = rsqrt(r2);
+                    const double R = r2 * rinv * ie;
+                    if (R < 2.0) {
+                        const double v = 1.0 - 0.5 * R;
+                        const double u = R < 1.0 ? 1.0 - R : 0.0;
+                        const double v2 = v * v, u2 = u * u;
+                        const double g = v2 * v2 * v * (8.0 / 35.0) * (((7.0 * R + 22.0) * R + 10.0) * R + 4.0) +
+                                         u2 * u2 * u2 * ((7.0 * R + 18.0) * R + 3.0) / 35.0;
+                        double rinv3;
+                        if (eps2 > 0.0) {
+                            const double rs = rsqrt(r2 + eps2);
+                            rinv3 = rs * rs * rs;
+                        } else {
+                            rinv3 = rinv * rinv * rinv;
+                        }
+                        const double f = j.w * g * rinv3;
+                        ax[s] += f * dx;
+                        ay[s] += f * dy;
+                        az[s] += f * dz;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int s = 0; s < I; s++) {
+        for (int o = li; o < 32; o <<= 1) {
+            ax[s] += __shfl_xor_sync(FULL, ax[s], o);
+            ay[s] += __shfl_xor_sync(FULL, ay[s], o);
+            az[s] += __shfl_xor_sync(FULL, az[s], o);
+        }
+    }
+    if (part == 0) {
+        double *acc = static_cast<double *>(a.acc);
+#pragma unroll
+        for (int s = 0; s < I; s++) {
+            const uint32_t idx = gr.begin + done + (uint32_t)(s * li + slot);
+            if (idx < gend) {
+                const size_t p = (size_t)a.perm[idx] * 3;
+                acc[p] = ax[s];
+                acc[p + 1] = ay[s];
+                acc[p + 2] = az[s];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_force_f64(ForceArgs a)
+{
+    __shared__ Dbl4 jbuf[8][32];
+    const unsigned FULL = 0xffffffffu;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (a.st->flags & ST_NODE_CAP) return;
+    const uint32_t G = *a.n_groups;
+    for (;;) {
+        unsigned long long gi = 0;
+        if (lane == 0) gi = atomicAdd(&a.st->work[2], 1ull);
+        gi = __shfl_sync(FULL, gi, 0);
+        if (gi >= G) break;
+        const uint32_t g = a.order ? a.order[gi] : (uint32_t)gi;
+        const Group gr = a.groups[g];
+        const BoxPar &bp = a.bps[gr.box];
+        const unsigned long long lo = a.loff[g];
+        const uint32_t len = a.lraw[g];
+        uint32_t done = 0;
+        unsigned long long evals = 0;
+        while (done < gr.count) {
+            int S, I;
+            choose_layout(gr.count - done, S, I);
+            switch (I) {
+            case 1: group_pass_f64<1>(a, gr, bp, done, S, lo, len, jbuf[w], lane); break;
+            case 2: group_pass_f64<2>(a, gr, bp, done, S, lo, len, jbuf[w], lane); break;
+            case 3: group_pass_f64<3>(a, gr, bp, done, S, lo, len, jbuf[w], lane); break;
+            case 4: group_pass_f64<4>(a, gr, bp, done, S, lo, len, jbuf[w], lane); break;
+            case 5: group_pass_f64<5>(a, gr, bp, done, S, lo, len, jbuf[w], lane); break;
+            case 6: group_pass_f64<6>(a, gr, bp, done, S, lo, len, jbuf[w], lane); break;
+            case 7: group_pass_f64<7>(a, gr, bp, done, S, lo, len, jbuf[w], lane); break;
+            default: group_pass_f64<8>(a, gr, bp, done, S, lo, len, jbuf[w], lane); break;
+            }
+            const uint32_t slots = (uint32_t)(32 / S) * (uint32_t)I;
+            evals += (unsigned long long)slots * len;
+            done += slots;
+        }
+        if (lane == 0) atomicAdd(&a.st->sum_eval, evals);
+    }
+}
+
+void launch_force_f64(const ForceArgs &a, cudaStream_t s, int nsm)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64, 256, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    k_force_f64<<<nsm * per_sm, 256, 0, s>>>(a);
+    g_launches++;
+}
+
+// ------------------------------------------------------------------ pairwise experiment
+// Every pair k becomes a one-particle group with a one-entry list (padded to 8):
+// i and j are passed relative to x_g in eta units (FP64 subtract, one FP32 rounding).
+__global__ void k_pair_setup(const double *__restrict__ xg, const double *__restrict__ xi,
+                             const double *__restrict__ xj, const float *__restrict__ mj, uint32_t np, double inv_eta,
+                             Group *groups, float4 *irel, float4 *flist, unsigned long long *loff, uint32_t *llen,
+                             uint32_t *lraw, uint32_t *perm, uint32_t *n_groups)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) *n_groups = np;
+    if (k >= np) return;
+    Group g;
+    g.node = 0;
+    g.begin = k;
+    g.count = 1;
+    g.box = 0;
+    g.cx = g.cy = g.cz = 0;
+    g.hg = 0;
+    groups[k] = g;
+    float r[3], q[3];
+    for (int c = 0; c < 3; c++) {
+        r[c] = (float)__dmul_rn(__dsub_rn(xi[3 * (size_t)k + c], xg[3 * (size_t)k + c]), inv_eta);
+        q[c] = (float)__dmul_rn(__dsub_rn(xj[3 * (size_t)k + c], xg[3 * (size_t)k + c]), inv_eta);
+    }
+    irel[k] = make_float4(r[0], r[1], r[2], 0.f);
+    flist[8 * (size_t)k] = make_float4(q[0], q[1], q[2], mj[k]);
+    for (int e = 1; e < 8; e++) flist[8 * (size_t)k + e] = make_float4(16.f, 16.f, 16.f, 0.f);
+    loff[k] = 8ull * k;
+    llen[k] = 8;
+    lraw[k] = 1;
+    perm[k] = k;
+}
+
+void launch_pair_setup(const double *xg, const double *xi, const double *xj, const float *mj, uint32_t np,
+                       double inv_eta, Group *groups, float4 *irel, float4 *flist, unsigned long long *loff,
+                       uint32_t *llen, uint32_t *lraw, uint32_t *perm, uint32_t *n_groups, cudaStream_t s)
+{
+    k_pair_setup<<<(np + 255) / 256, 256, 0, s>>>(xg, xi, xj, mj, np, inv_eta, groups, irel, flist, loff, llen, lraw,
+                                                   perm, n_groups);
+    g_launches++;
+}
+
+// ------------------------------------------------------------------ peak microbenchmarks
+__global__ void __launch_bounds__(256) k_peak_f32(float *out, int iters)
+{
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = threadIdx.x * 1e-9f + k;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+#pragma unroll
+            for (int k = 0; k < 8; k++) v[k] = fmaf(v[k], 0.9999f, 1e-7f);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += v[k];
+    if (s == 1234.5f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) k_peak_f64(double *out, int iters)
+{
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = threadIdx.x * 1e-9 + k;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+#pragma unroll
+            for (int k = 0; k < 8; k++) v[k] = fma(v[k], 0.9999, 1e-7);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += v[k];
+    if (s == 1234.5) out[0] = s;
+}
+
+double peak_tflops(int which, int nsm, cudaStream_t s, int *err)
+{
+    *err = 0;
+    void *out = nullptr;
+    if (cudaMalloc(&out, 64) != cudaSuccess) {
+        *err = -3;
+        return 0.0;
+    }
+    const int blocks = nsm * 8, threads = 256;
+    const int iters = which == 0 ? 4000 : 64;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(e0, s);
+        if (which == 0) k_peak_f32<<<blocks, threads, 0, s>>>((float *)out, iters);
+        else k_peak_f64<<<blocks, threads, 0, s>>>((double *)out, iters);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double flops = 2.0 * 8 * 16 * (double)iters * blocks * threads;
+        const double tf = flops / (ms * 1e-3) / 1e12;
+        if (rep > 0 && tf > best) best = tf;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) *err = -2;
+    cudaFree(out);
+    return best;
+}
+
+}  // namespace greem

@@ -1,0 +1,399 @@
+// S3 octree + monopole moments and S4 groups, built from the sorted Morton keys.
+//
+// The tree is the paper's local tree (Sec. 2.2 step 2) with the N_leaf stop rule
+// (Sec. 3.1.2: a node holding fewer than N_leaf particles is not subdivided).  Levels
+// above l_min are always split so that every accepted node and every group is small
+// enough for a single periodic image shift per node.
+//
+// Construction without recursion.  Let d_i be the first level at which key i differs
+// from key i-1 (0 for the first particle of a box, 22 for equal keys): the cells of
+// levels d_i..21 that contain particle i start at i.  Let K_i be the level of the leaf
+// containing i: the deepest level whose parent cell holds at least N_leaf particles
+// (or lies above l_min), capped at 21.  A level-j cell holds >= N_leaf particles iff
+// some window of N_leaf consecutive sorted particles containing i shares its level-j
+// prefix, so K_i comes from a sliding maximum over such windows.  Particle i then owns
+// the nodes (i, d_i) ... (i, K_i); an exclusive scan of the ownership counts numbers
+// the nodes in DFS preorder, because preorder is the order of (begin, level).
+#include "common.cuh"
+
+namespace greem {
+
+__device__ __forceinline__ int lcp_level(uint64_t a, uint64_t b)
+{
+    uint64_t x = a ^ b;
+    if (x == 0) return kMaxLevel;
+    return (__clzll((long long)x) - 1) / 3;  // bit 63 is zero in both keys
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+
+__global__ void __launch_bounds__(256) k_tree_prep(const uint64_t *__restrict__ keys, uint32_t N,
+                                                   const uint32_t *__restrict__ box_off, int nbox,
+                                                   const BoxPar *__restrict__ bps, uint8_t *__restrict__ d8,
+                                                   uint8_t *__restrict__ K8, uint32_t *__restrict__ own)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = box_of(i, box_off, nbox);
+    const long long o = box_off[b], e = box_off[b + 1];
+    const int nl = bps[b].n_leaf, lmin = bps[b].lmin;
+    const uint64_t ki = keys[i];
+    int d = (i == (uint32_t)o) ? 0 : lcp_level(keys[i - 1], ki) + 1;
+    int J = -1;
+    long long tlo = (long long)i - nl + 1;
+    if (tlo < o) tlo = o;
+    long long thi = e - nl;
+    if (thi > (long long)i) thi = i;
+    for (long long t = tlo; t <= thi; t++) {
+        int w = lcp_level(keys[t], keys[t + nl - 1]);
+        J = w > J ? w : J;
+    }
+    int K = J + 1;
+    K = K < lmin ? lmin : K;
+    K = K > kMaxLevel ? kMaxLevel : K;
+    d8[i] = (uint8_t)d;
+    K8[i] = (uint8_t)K;
+    own[i] = d <= K ? (uint32_t)(K - d + 1) : 0u;
+}
+
+void launch_tree_prep(const uint64_t *keys, uint32_t N, const uint32_t *box_off, int nbox, const BoxPar *bps,
+                      uint8_t *d8, uint8_t *K8, uint32_t *own, cudaStream_t s)
+{
+    k_tree_prep<<<(N + 255) / 256, 256, 0, s>>>(keys, N, box_off, nbox, bps, d8, K8, own);
+    g_launches++;
+}
+
+// End of the level-k cell that contains sorted particle i (k >= 1): the first index
+// j in (lo, e] whose level-k prefix differs, searched by galloping from lo, where lo
+// is known to share the prefix.
+__device__ __forceinline__ uint32_t cell_end(const uint64_t *__restrict__ keys, uint32_t lo, uint32_t e,
+                                             uint64_t pfx, int shift)
+{
+    uint32_t step = 1, hi;
+    for (;;) {
+        uint32_t j = lo + step;
+        if (j >= e) { hi = e; break; }
+        if ((keys[j] >> shift) != pfx) { hi = j; break; }
+        lo = j;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if ((keys[mid] >> shift) == pfx) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+__global__ void __launch_bounds__(256) k_tree_fill(const uint64_t *__restrict__ keys, uint32_t N,
+                                                   const uint32_t *__restrict__ box_off, int nbox,
+                                                   const uint8_t *__restrict__ d8, const uint8_t *__restrict__ K8,
+                                                   const uint32_t *__restrict__ base, Node *__restrict__ nodes,
+                                                   uint32_t node_cap, DevStatus *st)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint32_t b0 = base[i];
+    const uint32_t own = base[i + 1] - b0;
+    if (i == N - 1 && base[N] > node_cap) atomicOr(&st->flags, ST_NODE_CAP);
+    if (own == 0) return;
+    const int b = box_of(i, box_off, nbox);
+    const uint32_t e = box_off[b + 1];
+    const int d = d8[i], K = K8[i];
+    const uint64_t key = keys[i];
+    const uint32_t cx = compact3(key >> 2), cy = compact3(key >> 1), cz = compact3(key);
+    uint32_t end = i + 1;
+    for (int k = K; k >= d; k--) {
+        const uint32_t n = b0 + (uint32_t)(k - d);
+        if (k == 0) {
+            end = e;
+        } else {
+            const int shift = 3 * (kMaxLevel - k);
+            end = cell_end(keys, end - 1, e, key >> shift, shift);
+        }
+        if (n < node_cap) {
+            const uint32_t mask = k == 0 ? 0u : ~((1u << (kMaxLevel - k)) - 1u);
+            Node nd;
+            nd.ix = cx & mask;
+            nd.iy = cy & mask;
+            nd.iz = cz & mask;
+            nd.lvl = (uint32_t)k | (k == K ? 256u : 0u);
+            nd.begin = i;
+            nd.end = end;
+            nd.skip = base[end];
+            nd.parent = kNone;
+            nodes[n] = nd;
+        }
+    }
+}
+
+void launch_tree_fill(const uint64_t *keys, uint32_t N, const uint32_t *box_off, int nbox, const uint8_t *d8,
+                      const uint8_t *K8, const uint32_t *base, Node *nodes, uint32_t node_cap, DevStatus *st,
+                      cudaStream_t s, int nsm)
+{
+    (void)nsm;
+    k_tree_fill<<<(N + 255) / 256, 256, 0, s>>>(keys, N, box_off, nbox, d8, K8, base, nodes, node_cap, st);
+    g_launches++;
+}
+
+__device__ __forceinline__ uint32_t node_count(const uint32_t *n_nodes, uint32_t cap)
+{
+    uint32_t n = *n_nodes;
+    return n < cap ? n : cap;
+}
+
+// Parent links, child counts and the child table (up to 8 children per internal node,
+// unused slots kNone): the children of an internal node p are p+1 and then the skip
+// chain while it stays inside p's particle range.
+__global__ void __launch_bounds__(256) k_tree_links(Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
+                                                    uint32_t node_cap, uint8_t *__restrict__ nchild,
+                                                    uint32_t *__restrict__ kids)
+{
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += gridDim.x * blockDim.x) {
+        const Node np = nodes[p];
+        uint32_t slot[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) slot[k] = kNone;
+        uint32_t cnt = 0;
+        if (!(np.lvl & 256u)) {
+            uint32_t c = p + 1;
+            while (c < nn && nodes[c].begin < np.end && cnt < 8) {
+                nodes[c].parent = p;
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    if (k == (int)cnt) slot[k] = c;
+                cnt++;
+                c = nodes[c].skip;
+            }
+        }
+        nchild[p] = (uint8_t)cnt;
+        uint4 *kp = reinterpret_cast<uint4 *>(kids + (size_t)p * 8);
+        kp[0] = make_uint4(slot[0], slot[1], slot[2], slot[3]);
+        kp[1] = make_uint4(slot[4], slot[5], slot[6], slot[7]);
+    }
+}
+
+void launch_tree_links(Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, uint8_t *nchild, uint32_t *kids,
+                       cudaStream_t s, int nsm)
+{
+    k_tree_links<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, nchild, kids);
+    g_launches++;
+}
+
+// Monopole moments (Sec. 3.1.2, centre-of-mass approximation), bottom up, one thread
+// per node.  A leaf sums its particles in FP64; the last child to finish (atomic
+// arrival counter) sums the raw moments of all children of its parent in child order and
+// climbs on.  The order of every sum is fixed, so the result does not depend on
+// scheduling.
+__global__ void __launch_bounds__(256) k_moments(const Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
+                                                 uint32_t node_cap, const uint8_t *__restrict__ nchild,
+                                                 uint32_t *__restrict__ ctr, const double *__restrict__ xs,
+                                                 const double *__restrict__ ys, const double *__restrict__ zs,
+                                                 const float *__restrict__ ms, Dbl4 *raw)
+{
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    const Node nd = nodes[n];
+    if (!(nd.lvl & 256u)) return;
+    double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (uint32_t j = nd.begin; j < nd.end; j++) {
+        const double m = (double)ms[j];
+        M += m;
+        sx = fma(m, xs[j], sx);
+        sy = fma(m, ys[j], sy);
+        sz = fma(m, zs[j], sz);
+    }
+    raw[n] = make_dbl4(sx, sy, sz, M);
+    uint32_t cur = n;
+    for (;;) {
+        const uint32_t p = nodes[cur].parent;
+        if (p == kNone) break;
+        __threadfence();
+        const uint32_t old = atomicAdd(&ctr[p], 1u);
+        if (old + 1u != (uint32_t)nchild[p]) break;
+        __threadfence();
+        const uint32_t pend = nodes[p].end;
+        Dbl4 a = make_dbl4(0.0, 0.0, 0.0, 0.0);
+        for (uint32_t c = p + 1; c < nn && nodes[c].begin < pend; c = nodes[c].skip) {
+            const double2 *rp = reinterpret_cast<const double2 *>(raw + c);
+            const double2 r0 = __ldcg(rp), r1 = __ldcg(rp + 1);  // L2, not a stale L1 line
+            a.x += r0.x;
+            a.y += r0.y;
+            a.z += r1.x;
+            a.w += r1.y;
+        }
+        raw[p] = a;
+        cur = p;
+    }
+}
+
+void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint8_t *nchild,
+                    uint32_t *ctr, const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw,
+                    cudaStream_t s)
+{
+    k_moments<<<(node_cap + 255) / 256, 256, 0, s>>>(nodes, n_nodes, node_cap, nchild, ctr, xs, ys, zs, ms, raw);
+    g_launches++;
+}
+
+// Each particle's offset from the centre of its leaf cell (level K_i) in eta units: the
+// FP64 subtraction is done once per particle, then rounded to FP32 for the list builder.
+__global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ K8,
+                                                      uint32_t N, const uint32_t *__restrict__ box_off, int nbox,
+                                                      const BoxPar *__restrict__ bps, const double *__restrict__ xs,
+                                                      const double *__restrict__ ys, const double *__restrict__ zs,
+                                                      const float *__restrict__ ms, float4 *__restrict__ poff)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const BoxPar &bp = bps[box_of(i, box_off, nbox)];
+    const int k = K8[i];
+    const uint32_t h = 1u << (kMaxLevel - k);
+    const uint32_t mask = ~(h - 1u);
+    const uint64_t key = keys[i];
+    const double u = bp.u, ie = bp.inv_eta;
+    const double cxa = __dmul_rn((double)(2u * (compact3(key >> 2) & mask) + h), u);
+    const double cya = __dmul_rn((double)(2u * (compact3(key >> 1) & mask) + h), u);
+    const double cza = __dmul_rn((double)(2u * (compact3(key) & mask) + h), u);
+    poff[i] = make_float4((float)__dmul_rn(__dsub_rn(xs[i], cxa), ie), (float)__dmul_rn(__dsub_rn(ys[i], cya), ie),
+                          (float)__dmul_rn(__dsub_rn(zs[i], cza), ie), ms[i]);
+}
+
+void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
+                         const BoxPar *bps, const double *xs, const double *ys, const double *zs, const float *ms,
+                         float4 *poff, cudaStream_t s)
+{
+    k_leaf_offsets<<<(N + 255) / 256, 256, 0, s>>>(keys, K8, N, box_off, nbox, bps, xs, ys, zs, ms, poff);
+    g_launches++;
+}
+
+// COM = S/M (the cell centre for a massless node), and the COM's offset from the node's
+// cell centre in eta units for the list builder.
+__global__ void __launch_bounds__(256) k_node_finish(const Node *__restrict__ nodes,
+                                                     const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
+                                                     const Dbl4 *__restrict__ raw,
+                                                     const uint32_t *__restrict__ box_off, int nbox,
+                                                     const BoxPar *__restrict__ bps, Dbl4 *__restrict__ mom64,
+                                                     float4 *__restrict__ noff)
+{
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
+        const Node nd = nodes[n];
+        const BoxPar &bp = bps[box_of(nd.begin, box_off, nbox)];
+        const int k = nd.lvl & 255u;
+        const uint32_t h = 1u << (kMaxLevel - k);
+        const double u = bp.u, ie = bp.inv_eta;
+        const double cxa = __dmul_rn((double)(2u * nd.ix + h), u);
+        const double cya = __dmul_rn((double)(2u * nd.iy + h), u);
+        const double cza = __dmul_rn((double)(2u * nd.iz + h), u);
+        const Dbl4 r = raw[n];
+        double cx = cxa, cy = cya, cz = cza;
+        if (r.w > 0.0) {
+            const double inv = 1.0 / r.w;
+            cx = r.x * inv;
+            cy = r.y * inv;
+            cz = r.z * inv;
+        }
+        mom64[n] = make_dbl4(cx, cy, cz, r.w);
+        noff[n] = make_float4((float)__dmul_rn(__dsub_rn(cx, cxa), ie), (float)__dmul_rn(__dsub_rn(cy, cya), ie),
+                              (float)__dmul_rn(__dsub_rn(cz, cza), ie), (float)r.w);
+    }
+}
+
+void launch_node_finish(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const Dbl4 *raw,
+                        const uint32_t *box_off, int nbox, const BoxPar *bps, Dbl4 *mom64, float4 *noff,
+                        cudaStream_t s, int nsm)
+{
+    k_node_finish<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, raw, box_off, nbox, bps, mom64, noff);
+    g_launches++;
+}
+
+// S4 groups (Sec. 2.2 step 5, Sec. 3.1.2 N_crit): a node is a group when it is at level
+// >= l_min and holds at most n_crit particles (or is a leaf), and its parent is not.
+__device__ __forceinline__ bool group_cond(const Node &nd, const BoxPar &bp)
+{
+    const int k = nd.lvl & 255u;
+    return k >= bp.lmin && ((int)(nd.end - nd.begin) <= bp.n_crit || (nd.lvl & 256u));
+}
+
+__global__ void __launch_bounds__(256) k_group_flags(const Node *__restrict__ nodes,
+                                                     const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
+                                                     const uint32_t *__restrict__ box_off, int nbox,
+                                                     const BoxPar *__restrict__ bps, uint32_t *__restrict__ flag)
+{
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < node_cap; n += gridDim.x * blockDim.x) {
+        uint32_t f = 0;
+        if (n < nn) {
+            const Node nd = nodes[n];
+            const BoxPar &bp = bps[box_of(nd.begin, box_off, nbox)];
+            if (group_cond(nd, bp)) f = (nd.parent == kNone || !group_cond(nodes[nd.parent], bp)) ? 1u : 0u;
+        }
+        flag[n] = f;
+    }
+}
+
+void launch_group_flags(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *box_off,
+                        int nbox, const BoxPar *bps, uint32_t *flag, cudaStream_t s, int nsm)
+{
+    k_group_flags<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, box_off, nbox, bps, flag);
+    g_launches++;
+}
+
+__global__ void __launch_bounds__(256) k_group_fill(const Node *__restrict__ nodes,
+                                                    const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
+                                                    const uint32_t *__restrict__ flag,
+                                                    const uint32_t *__restrict__ gidx,
+                                                    const uint32_t *__restrict__ box_off, int nbox,
+                                                    Group *__restrict__ groups)
+{
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
+        if (!flag[n]) continue;
+        const Node nd = nodes[n];
+        const int k = nd.lvl & 255u;
+        const int32_t h = 1 << (kMaxLevel - k);
+        Group g;
+        g.node = n;
+        g.begin = nd.begin;
+        g.count = nd.end - nd.begin;
+        g.box = (uint32_t)box_of(nd.begin, box_off, nbox);
+        g.cx = 2 * (int32_t)nd.ix + h;
+        g.cy = 2 * (int32_t)nd.iy + h;
+        g.cz = 2 * (int32_t)nd.iz + h;
+        g.hg = h;
+        groups[gidx[n]] = g;
+    }
+}
+
+void launch_group_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *flag,
+                       const uint32_t *gidx, const uint32_t *box_off, int nbox, Group *groups, cudaStream_t s, int nsm)
+{
+    k_group_fill<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, flag, gidx, box_off, nbox, groups);
+    g_launches++;
+}
+
+__global__ void k_record_counts(const uint32_t *n_nodes, const uint32_t *n_groups, DevStatus *st, uint32_t node_cap)
+{
+    st->n_nodes = *n_nodes;
+    st->n_groups = n_groups ? *n_groups : 0;
+    if (*n_nodes > node_cap) atomicOr(&st->flags, ST_NODE_CAP);
+}
+
+void launch_record_counts(const uint32_t *n_nodes, const uint32_t *n_groups, DevStatus *st, uint32_t node_cap,
+                          cudaStream_t s)
+{
+    k_record_counts<<<1, 1, 0, s>>>(n_nodes, n_groups, st, node_cap);
+    g_launches++;
+}
+
+}  // namespace greem

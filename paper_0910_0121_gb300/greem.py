@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libgreem.so (include/greem.h): argument marshalling only.
+
+Every step of the short-range force runs in the library's CUDA kernels; this module
+passes torch CUDA tensors as device pointers together with torch's current stream.
+It fails loudly when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgreem.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_OOM = -3
+ERR_CAPACITY = -4
+ERR_TIMEOUT = -5
+ERR_NOT_IMPLEMENTED = -6
+
+F32_REL = 0
+F64 = 1
+FLAG_INDEX_LISTS = 1
+FLAG_STAGE_TIMES = 2
+
+DUMP_KEYS, DUMP_PERM, DUMP_NODES, DUMP_MOMENTS, DUMP_GROUPS, DUMP_LIST_OFFSETS, DUMP_LISTS = range(7)
+
+
+class GreemError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = _lib().greem_strerror(code).decode() if _lib_loaded() else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("r_cut", ctypes.c_double), ("theta", ctypes.c_double),
+                ("eps", ctypes.c_double), ("n_crit", ctypes.c_int), ("n_leaf", ctypes.c_int),
+                ("precision", ctypes.c_int), ("list_chunk", ctypes.c_int), ("block_shape", ctypes.c_int),
+                ("flags", ctypes.c_uint)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_particles", "n_boxes", "n_nodes", "n_groups", "n_list_entries",
+                                             "n_interactions", "n_evaluated", "list_capacity",
+                                             "kernel_launches")] + \
+               [("l_min", ctypes.c_int32), ("retries", ctypes.c_int32)] + \
+               [(n, ctypes.c_double) for n in ("ms_keys", "ms_sort", "ms_tree", "ms_groups", "ms_lists",
+                                              "ms_force", "ms_total")]
+
+
+_lock = threading.Lock()
+_L = None
+
+
+def _lib_loaded() -> bool:
+    return _L is not None
+
+
+def _lib():
+    global _L
+    with _lock:
+        if _L is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libgreem.so is not built ({LIB_PATH}); run paper_0910_0121_gb300/build.py")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+            P = ctypes.POINTER(Params)
+            L.greem_params_default.argtypes = [P]
+            L.greem_params_default.restype = None
+            L.greem_create.argtypes = [ctypes.POINTER(vp), vp]
+            L.greem_destroy.argtypes = [vp]
+            L.greem_destroy.restype = None
+            L.greem_build_tree.argtypes = [vp, vp, vp, i64, P]
+            L.greem_short_force.argtypes = [vp, vp, i64, dbl, dbl, dbl, i32, vp]
+            L.greem_short_force_ex.argtypes = [vp, vp, vp, i64, P, vp]
+            L.greem_short_force_batched.argtypes = [vp, i32, vp, vp, vp, P, vp]
+            L.greem_pm_force.argtypes = [vp, vp, vp, i64, dbl, i32, dbl, i32, vp]
+            L.greem_graph_capture.argtypes = [vp, vp, vp, i64, P, vp]
+            L.greem_graph_launch.argtypes = [vp]
+            L.greem_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+            L.greem_debug_dump.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
+            L.greem_autotune.argtypes = [vp, vp, vp, i64, P, vp, i32, vp, P]
+            L.greem_pair_force_f32.argtypes = [vp, vp, vp, vp, vp, i64, dbl, dbl, vp]
+            L.greem_peak_tflops.argtypes = [vp, i32, ctypes.POINTER(dbl)]
+            L.greem_strerror.argtypes = [i32]
+            L.greem_strerror.restype = ctypes.c_char_p
+            for f in ("greem_create", "greem_build_tree", "greem_short_force", "greem_short_force_ex",
+                      "greem_short_force_batched", "greem_pm_force", "greem_graph_capture", "greem_graph_launch",
+                      "greem_get_stats", "greem_debug_dump", "greem_autotune", "greem_pair_force_f32",
+                      "greem_peak_tflops"):
+                getattr(L, f).restype = i32
+            _L = L
+    return _L
+
+
+def lib():
+    """The loaded C library (raises ImportError when it has not been built)."""
+    return _lib()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise GreemError(rc, what)
+
+
+def _dev(t, dtype, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def params(L=1.0, r_cut=3.0 / 32, theta=0.5, n_crit=64, n_leaf=10, eps=0.0, precision=F32_REL, list_chunk=0,
+           block_shape=0, flags=0) -> Params:
+    p = Params()
+    _lib().greem_params_default(ctypes.byref(p))
+    p.L, p.r_cut, p.theta, p.eps = float(L), float(r_cut), float(theta), float(eps)
+    p.n_crit, p.n_leaf, p.precision = int(n_crit), int(n_leaf), int(precision)
+    p.list_chunk, p.block_shape, p.flags = int(list_chunk), int(block_shape), int(flags)
+    return p
+
+
+class Context:
+    """greem_ctx bound to a CUDA stream (default: torch's current stream at creation)."""
+
+    def __init__(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(_lib().greem_create(ctypes.byref(h), ctypes.c_void_p(stream.cuda_stream)), "greem_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().greem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- calls
+    def build_tree(self, pos, mass, p: Params):
+        import torch
+        N = pos.shape[0]
+        _check(_lib().greem_build_tree(self._h, _dev(pos, torch.float64, (N, 3), "pos"),
+                                       _dev(mass, torch.float32, (N,), "mass"), N, ctypes.byref(p)),
+               "greem_build_tree")
+
+    def short_force(self, pos, mass, p: Params, acc=None):
+        import torch
+        N = pos.shape[0]
+        dt = torch.float64 if p.precision == F64 else torch.float32
+        if acc is None:
+            acc = torch.empty((N, 3), dtype=dt, device=pos.device)
+        _check(_lib().greem_short_force_ex(self._h, _dev(pos, torch.float64, (N, 3), "pos"),
+                                           _dev(mass, torch.float32, (N,), "mass"), N, ctypes.byref(p),
+                                           _dev(acc, dt, (N, 3), "acc")), "greem_short_force_ex")
+        return acc
+
+    def short_force_batched(self, pos, mass, offsets, per_box, acc=None):
+        import torch
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        nbox = off.shape[0] - 1
+        N = int(off[-1])
+        arr = (Params * nbox)(*per_box)
+        dt = torch.float64 if per_box[0].precision == F64 else torch.float32
+        if acc is None:
+            acc = torch.empty((N, 3), dtype=dt, device=pos.device)
+        _check(_lib().greem_short_force_batched(self._h, nbox, off.ctypes.data_as(ctypes.c_void_p),
+                                                _dev(pos, torch.float64, (N, 3), "pos"),
+                                                _dev(mass, torch.float32, (N,), "mass"), arr,
+                                                _dev(acc, dt, (N, 3), "acc")), "greem_short_force_batched")
+        return acc
+
+    def graph_capture(self, pos, mass, p: Params, acc):
+        import torch
+        N = pos.shape[0]
+        dt = torch.float64 if p.precision == F64 else torch.float32
+        _check(_lib().greem_graph_capture(self._h, _dev(pos, torch.float64, (N, 3), "pos"),
+                                          _dev(mass, torch.float32, (N,), "mass"), N, ctypes.byref(p),
+                                          _dev(acc, dt, (N, 3), "acc")), "greem_graph_capture")
+
+    def graph_launch(self) -> int:
+        return _lib().greem_graph_launch(self._h)
+
+    def autotune(self, pos, mass, p: Params, acc, candidates=None) -> Params:
+        import torch
+        N = pos.shape[0]
+        best = Params()
+        cand = None if candidates is None else (ctypes.c_int * len(candidates))(*candidates)
+        dt = torch.float64 if p.precision == F64 else torch.float32
+        _check(_lib().greem_autotune(self._h, _dev(pos, torch.float64, (N, 3), "pos"),
+                                     _dev(mass, torch.float32, (N,), "mass"), N, ctypes.byref(p),
+                                     cand, 0 if cand is None else len(candidates), _dev(acc, dt, (N, 3), "acc"),
+                                     ctypes.byref(best)), "greem_autotune")
+        return best
+
+    def pair_force_f32(self, xg, xi, xj, mj, r_cut, eps=0.0, acc=None):
+        import torch
+        P = xg.shape[0]
+        if acc is None:
+            acc = torch.empty((P, 3), dtype=torch.float32, device=xg.device)
+        _check(_lib().greem_pair_force_f32(self._h, _dev(xg, torch.float64, (P, 3), "x_g"),
+                                           _dev(xi, torch.float64, (P, 3), "x_i"),
+                                           _dev(xj, torch.float64, (P, 3), "x_j"),
+                                           _dev(mj, torch.float32, (P,), "m_j"), P, float(r_cut), float(eps),
+                                           _dev(acc, torch.float32, (P, 3), "acc")), "greem_pair_force_f32")
+        return acc
+
+    def peak_tflops(self, which: int = 0) -> float:
+        v = ctypes.c_double()
+        _check(_lib().greem_peak_tflops(self._h, int(which), ctypes.byref(v)), "greem_peak_tflops")
+        return v.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(_lib().greem_get_stats(self._h, ctypes.byref(s)), "greem_get_stats")
+        return {n: getattr(s, n) for n, _ in Stats._fields_}
+
+    def dump(self, what: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        rc = _lib().greem_debug_dump(self._h, int(what), None, 0, ctypes.byref(n))
+        if n.value == 0 and rc != OK:
+            raise GreemError(rc, "greem_debug_dump")
+        buf = np.zeros(max(n.value, 8) // 8 + 1, dtype=np.int64)
+        _check(_lib().greem_debug_dump(self._h, int(what), buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes,
+                                       ctypes.byref(n)), "greem_debug_dump")
+        raw = buf.view(np.uint8)[: n.value]
+        if what == DUMP_KEYS:
+            return raw.view(np.uint64).copy()
+        if what == DUMP_PERM:
+            return raw.view(np.uint32).copy()
+        if what == DUMP_NODES:
+            return raw.view(np.int64).reshape(-1, 9).copy()
+        if what == DUMP_MOMENTS:
+            return raw.view(np.float64).reshape(-1, 4).copy()
+        if what in (DUMP_GROUPS, DUMP_LIST_OFFSETS):
+            return raw.view(np.int64).copy()
+        if what == DUMP_LISTS:
+            return raw.view(np.int64).reshape(-1, 5).copy()
+        raise ValueError(what)
+
+
+def short_force(pos, mass, L: float, r_cut: float, theta: float, n_crit: int, acc=None):
+    """greem_short_force: the whole force with defaults, library-owned context on the
+    current device (legacy default stream).  pos float64 [N,3], mass float32 [N] CUDA."""
+    import torch
+    N = pos.shape[0]
+    if acc is None:
+        acc = torch.empty((N, 3), dtype=torch.float32, device=pos.device)
+    torch.cuda.current_stream().synchronize()
+    _check(_lib().greem_short_force(_dev(pos, torch.float64, (N, 3), "pos"), _dev(mass, torch.float32, (N,), "mass"),
+                                    N, float(L), float(r_cut), float(theta), int(n_crit),
+                                    _dev(acc, torch.float32, (N, 3), "acc")), "greem_short_force")
+    return acc

@@ -1,0 +1,300 @@
+"""GPU path (libgreem.so through the C ABI) against the FP64 CPU oracle.
+
+Integer stages (keys, sort order, tree topology, groups, interaction lists) must be
+bit-exact; moments agree to summation order (1e-13); the FP32 force is held to the
+bounds median <= 1e-5 and 99.9th percentile <= 1e-4 of the relative error against the
+oracle's FP64 force on identical lists; the FP64 form to 1e-11.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0910_0121_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0910_0121_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_0910_0121_gb300 import greem  # noqa: E402
+
+MED_BOUND, P999_BOUND = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = greem.Context()
+    yield c
+    c.close()
+
+
+def _t(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).cuda()
+
+
+def gpu_force(ctx, pos, mass, prm, precision=greem.F32_REL, flags=greem.FLAG_INDEX_LISTS, **kw):
+    p = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=prm["n_crit"],
+                     n_leaf=prm.get("n_leaf", 10), eps=prm.get("eps", 0.0), precision=precision, flags=flags, **kw)
+    acc = ctx.short_force(_t(pos, np.float64), _t(mass, np.float32), p)
+    torch.cuda.synchronize()
+    return acc.cpu().numpy().astype(np.float64)
+
+
+def rel_err(a, ref):
+    """Per-particle |a - ref| / |ref|; particles with |ref| below 1e-6 of the median
+    magnitude are left out (they have no meaningful relative error)."""
+    na = np.linalg.norm(ref, axis=1)
+    keep = na > 1e-6 * np.median(na[na > 0]) if np.any(na > 0) else na > 0
+    return np.linalg.norm(a - ref, axis=1)[keep] / na[keep]
+
+
+def clustered(N, seed, L=1.0):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((N, 3)) * L
+    k = N // 3
+    pos[:k] = np.mod(0.01 * L + 0.02 * L * rng.standard_normal((k, 3)), L)   # clump across a corner
+    pos[k:k + 50] = pos[k + 60]                                             # coincident particles
+    return pos, rng.uniform(0.5, 1.5, N).astype(np.float32) / N
+
+
+CASES = {
+    "uniform32": lambda: synth.config_uniform32(),
+    "clustered": lambda: (*clustered(6000, 4), dict(L=1.0, r_cut=0.08, theta=0.5, n_crit=64, n_leaf=10)),
+    "nfw24": lambda: synth.config_nfw128(n_side=24, n_halos=12),
+    "boxL3": lambda: (*clustered(3001, 9, L=3.0), dict(L=3.0, r_cut=0.4, theta=0.7, n_crit=40, n_leaf=6)),
+    "crit1": lambda: (*clustered(700, 5), dict(L=1.0, r_cut=0.2, theta=0.4, n_crit=1, n_leaf=1)),
+    "bigcrit": lambda: (*clustered(4000, 6), dict(L=1.0, r_cut=0.15, theta=0.5, n_crit=700, n_leaf=20)),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, ctx):
+    pos, mass, prm = CASES[request.param]()
+    prm = dict(prm)
+    if not prm.get("n_crit"):
+        prm["n_crit"] = 64
+    acc32 = gpu_force(ctx, pos, mass, prm)
+    dumps = {w: ctx.dump(w) for w in (greem.DUMP_KEYS, greem.DUMP_PERM, greem.DUMP_NODES, greem.DUMP_MOMENTS,
+                                      greem.DUMP_GROUPS, greem.DUMP_LIST_OFFSETS, greem.DUMP_LISTS)}
+    T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm.get("n_leaf", 10))
+    T.build_lists(prm["theta"])
+    return dict(name=request.param, pos=pos, mass=mass, prm=prm, acc32=acc32, dumps=dumps, T=T)
+
+
+def test_keys_and_sort_bit_exact(case):
+    key, perm, _, _ = case["T"].sorted()
+    assert np.array_equal(case["dumps"][greem.DUMP_KEYS], key)
+    assert np.array_equal(case["dumps"][greem.DUMP_PERM].astype(np.int64), perm)
+
+
+def test_tree_bit_exact(case):
+    on = case["T"].nodes()
+    gn = case["dumps"][greem.DUMP_NODES]
+    assert gn.shape == on.shape
+    assert np.array_equal(gn[:, :8], on[:, :8])
+    # parent links: each node's parent is the innermost node whose subtree contains it
+    par = gn[:, 8]
+    assert par[0] == -1
+    idx = np.arange(len(gn))
+    kids = par >= 0
+    assert np.all(par[kids] < idx[kids]) and np.all(gn[par[kids], 6] >= idx[kids] + 1)
+    assert np.all(gn[par[kids], 0] == gn[kids, 0] - 1)
+
+
+def test_moments_to_summation_order(case):
+    om = case["T"].moments()
+    gm = case["dumps"][greem.DUMP_MOMENTS]
+    assert gm.shape == om.shape
+    assert np.allclose(gm[:, 0], om[:, 0], rtol=1e-13, atol=0)
+    L = case["prm"]["L"]
+    assert np.abs(gm[:, 1:] - om[:, 1:]).max() <= 1e-13 * L
+
+
+def test_groups_bit_exact(case):
+    assert np.array_equal(case["dumps"][greem.DUMP_GROUPS], case["T"].groups())
+
+
+def test_lists_bit_exact(case):
+    off, kind, idx, sh = case["T"].lists()
+    assert np.array_equal(case["dumps"][greem.DUMP_LIST_OFFSETS], off)
+    gl = case["dumps"][greem.DUMP_LISTS]
+    assert gl.shape[0] == kind.shape[0]
+    assert np.array_equal(gl[:, 0], kind.astype(np.int64))
+    assert np.array_equal(gl[:, 1], idx)
+    assert np.array_equal(gl[:, 2:], sh.astype(np.int64))
+
+
+def test_force_f32_within_bounds(case):
+    ref = case["T"].list_force_input_order()
+    e = rel_err(case["acc32"], ref)
+    assert np.median(e) <= MED_BOUND, np.median(e)
+    assert np.quantile(e, 0.999) <= P999_BOUND, np.quantile(e, 0.999)
+
+
+def test_force_f64_form(case, ctx):
+    ref = case["T"].list_force_input_order()
+    a = gpu_force(ctx, case["pos"], case["mass"], case["prm"], precision=greem.F64)
+    scale = np.abs(ref).max()
+    assert np.abs(a - ref).max() <= 1e-11 * scale
+
+
+# --------------------------------------------------------------------------- plain definition
+@pytest.mark.parametrize("precision", [greem.F64, greem.F32_REL])
+def test_theta_zero_equals_direct_sum(ctx, precision):
+    pos, mass = clustered(3000, 12)
+    prm = dict(L=1.0, r_cut=0.1, theta=0.0, n_crit=48)
+    ref = oracle.direct(pos, mass, 1.0, 0.1)
+    a = gpu_force(ctx, pos, mass, prm, precision=precision, flags=0)
+    if precision == greem.F64:
+        assert np.abs(a - ref).max() <= 1e-11 * np.abs(ref).max()
+    else:
+        e = rel_err(a, ref)
+        assert np.median(e) <= MED_BOUND and np.quantile(e, 0.999) <= P999_BOUND
+
+
+def test_uniform32_fp64_against_direct_sum(ctx):
+    """32^3 uniform, r_cut = 3/32, theta = 0.5, n_crit = 64, FP64 form vs brute force."""
+    pos, mass, prm = synth.config_uniform32()
+    ref = oracle.direct(pos, mass, prm["L"], prm["r_cut"])
+    a = gpu_force(ctx, pos, mass, prm, precision=greem.F64, flags=0)
+    e = rel_err(a, ref)
+    # the tree approximation at theta = 0.5 (reported, not a parity bound): most
+    # particles' lists open every node within r_cut, a few accept nodes near r_cut
+    print(f"uniform32 tree vs direct: median {np.median(e):.2e} p99 {np.quantile(e, 0.99):.2e} "
+          f"p99.9 {np.quantile(e, 0.999):.2e}")
+    assert np.median(e) < 1e-4
+    assert np.quantile(e, 0.99) < 1e-2
+
+
+# --------------------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("N", [1, 2, 9, 10, 11, 3071, 3072, 3073])
+def test_small_and_ragged_sizes(ctx, N):
+    rng = np.random.default_rng(N)
+    pos = rng.random((N, 3))
+    if N >= 2:
+        pos[1] = pos[0] + [0.01, -0.02, 0.005]
+    mass = np.full(N, 1.0 / max(N, 1), np.float32)
+    prm = dict(L=1.0, r_cut=0.2, theta=0.5, n_crit=16)
+    ref = oracle.short_force(pos, mass, 1.0, 0.2, 0.5, 16)
+    for precision in (greem.F64, greem.F32_REL):
+        a = gpu_force(ctx, pos, mass, prm, precision=precision, flags=0)
+        if N == 1:
+            assert np.all(a == 0)
+        else:
+            e = rel_err(a, ref)
+            assert np.median(e) <= MED_BOUND and np.quantile(e, 0.999) <= P999_BOUND
+
+
+def test_wrapped_and_coincident_positions(ctx):
+    rng = np.random.default_rng(3)
+    N = 2000
+    pos = rng.random((N, 3))
+    pos[:200] += rng.integers(-3, 4, (200, 3))      # outside [0, L): wrapped
+    pos[200] = [1.0, 0.0, -0.0]                       # exactly L and signed zero
+    pos[201] = [np.nextafter(1.0, 0), 0.5, 0.5]
+    pos[300:340] = pos[341]                           # 41 coincident particles
+    mass = np.full(N, 1.0 / N, np.float32)
+    prm = dict(L=1.0, r_cut=0.12, theta=0.6, n_crit=32)
+    T = oracle.Tree(pos, mass, 1.0, 0.12, 32)
+    T.build_lists(0.6)
+    a = gpu_force(ctx, pos, mass, prm)
+    key, _, _, _ = T.sorted()
+    assert np.array_equal(ctx.dump(greem.DUMP_KEYS), key)
+    ref = T.list_force_input_order()
+    e = rel_err(a, ref)
+    assert np.median(e) <= MED_BOUND and np.quantile(e, 0.999) <= P999_BOUND
+    assert np.all(np.isfinite(a))
+
+
+def test_softening(ctx):
+    pos, mass = clustered(3000, 21)
+    prm = dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=64, eps=0.1 / 300)
+    T = oracle.Tree(pos, mass, 1.0, 0.1, 64)
+    T.build_lists(0.5)
+    ref = T.list_force_input_order(eps=prm["eps"])
+    for precision in (greem.F32_REL, greem.F64):
+        a = gpu_force(ctx, pos, mass, prm, precision=precision, flags=0)
+        e = rel_err(a, ref)
+        assert np.median(e) <= MED_BOUND and np.quantile(e, 0.999) <= P999_BOUND
+
+
+# --------------------------------------------------------------------------- systems paths
+def test_batched_equals_single_boxes(ctx):
+    boxes = [clustered(n, 30 + n) for n in (1500, 4097, 777, 2600)]
+    prms = [dict(L=1.0, r_cut=rc, theta=th, n_crit=nc) for rc, th, nc in
+            ((0.1, 0.5, 64), (0.07, 0.3, 32), (0.2, 0.8, 100), (0.05, 0.5, 48))]
+    singles = [gpu_force(ctx, p, m, prm, flags=0) for (p, m), prm in zip(boxes, prms)]
+    pos = np.concatenate([b[0] for b in boxes])
+    mass = np.concatenate([b[1] for b in boxes])
+    off = np.cumsum([0] + [len(b[0]) for b in boxes])
+    per = [greem.params(**prm) for prm in prms]
+    acc = ctx.short_force_batched(_t(pos, np.float64), _t(mass, np.float32), off, per)
+    torch.cuda.synchronize()
+    acc = acc.cpu().numpy().astype(np.float64)
+    for b in range(len(boxes)):
+        assert np.array_equal(acc[off[b]:off[b + 1]], singles[b])
+
+
+def test_graph_replay_matches_direct_call(ctx):
+    pos, mass = clustered(5000, 40)
+    prm = dict(L=1.0, r_cut=0.08, theta=0.5, n_crit=64)
+    p = greem.params(**prm)
+    P, M = _t(pos, np.float64), _t(mass, np.float32)
+    acc = torch.zeros((5000, 3), dtype=torch.float32, device="cuda")
+    ctx.graph_capture(P, M, p, acc)
+    for shift in (0.0, 0.003):
+        newpos = np.mod(pos + shift, 1.0)
+        P.copy_(_t(newpos, np.float64))
+        acc.zero_()
+        assert ctx.graph_launch() == greem.OK
+        torch.cuda.synchronize()
+        ref = gpu_force(ctx, newpos, mass, prm, flags=0)
+        assert np.array_equal(acc.cpu().numpy().astype(np.float64), ref)
+
+
+def test_default_entry_point_matches_ex(ctx):
+    pos, mass = clustered(2500, 50)
+    acc = greem.short_force(_t(pos, np.float64), _t(mass, np.float32), 1.0, 0.1, 0.5, 64)
+    torch.cuda.synchronize()
+    ref = gpu_force(ctx, pos, mass, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=64), flags=0)
+    assert np.array_equal(acc.cpu().numpy().astype(np.float64), ref)
+
+
+def test_invalid_inputs_are_errors(ctx):
+    pos, mass = clustered(100, 1)
+    bad = pos.copy()
+    bad[17, 2] = np.inf
+    with pytest.raises(greem.GreemError) as ei:
+        gpu_force(ctx, bad, mass, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=8))
+    assert ei.value.code == greem.ERR_INVALID_ARG
+    for prm in (dict(L=1.0, r_cut=0.5, theta=0.5, n_crit=8), dict(L=1.0, r_cut=0.1, theta=-1.0, n_crit=8),
+                dict(L=0.0, r_cut=0.1, theta=0.5, n_crit=8), dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=0)):
+        with pytest.raises(greem.GreemError):
+            gpu_force(ctx, pos, mass, prm)
+    # the context is still usable afterwards
+    gpu_force(ctx, pos, mass, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=8))
+    assert greem.lib().greem_pm_force(ctx._h, None, None, 0, 1.0, 32, 0.1, 0, None) == greem.ERR_NOT_IMPLEMENTED
+
+
+# --------------------------------------------------------------------------- pairwise error (Sec. 3.1.1)
+def test_pairwise_fp32_error_e1(ctx):
+    """The pairwise experiment of Sec. 3.1.1 (Fig. 2): r_cut = 5.859375e-3, eps = 1.953125e-5,
+    256 x_i x 1024 x_j; the relative error of the FP32 pair force is ~1e-5 beyond eps."""
+    rc, eps = 5.859375e-3, 1.953125e-5
+    xg, xi, xj, mj = synth.e1_pairs(r_cut=rc)
+    a = ctx.pair_force_f32(_t(xg, np.float64), _t(xi, np.float64), _t(xj, np.float64), _t(mj, np.float32), rc, eps)
+    torch.cuda.synchronize()
+    a = a.cpu().numpy().astype(np.float64)
+    d = xj - xi
+    r = np.linalg.norm(d, axis=1)
+    ref = np.stack([oracle.pair_accel(d[k], 1.0, rc / 2, eps) for k in range(len(r))])
+    f = np.linalg.norm(ref, axis=1)
+    beyond = (r > eps) & (r < 0.75 * rc)
+    err = np.linalg.norm(a - ref, axis=1)[beyond] / f[beyond]
+    assert np.median(err) < 1e-5
+    assert np.quantile(err, 0.99) < 1e-4
+    assert np.all(a[r >= rc] == 0)
