@@ -170,6 +170,22 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def traffic_per_launch(list_entries):
+    """DRAM bytes of one force launch, from the ncu record in profiles/ (bytes per list
+    entry on a smaller case) scaled by this launch's list entries; None when the force
+    kernel's source changed since the record was taken."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "force_f32_traffic.txt")
+    src = os.path.join(ROOT, "paper_0910_0121_gb300", "csrc", "force.cu")
+    try:
+        kv = dict(l.split(":", 1) for l in open(rec) if ":" in l and not l.startswith("#"))
+        if kv["force_cu_sha256_16"].strip() != hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]:
+            return None
+        return float(kv["bytes_per_list_entry"]) * list_entries
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def gpu_arm(args, rank, world, local):
     import torch
@@ -280,15 +296,7 @@ def gpu_arm(args, rank, world, local):
     fms = statistics.mean(force_ms)
     achieved = FLOPS_PER_INTERACTION * inter / (fms * 1e-3) / 1e12
     peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "force_f32_zel256_traffic.json")
-    if os.path.exists(prof):
-        try:
-            tj = json.load(open(prof))
-            if tj.get("n_crit") == p.n_crit:
-                traffic = tj.get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = traffic_per_launch(st["n_list_entries"])
 
     value = world * N / (ms * 1e-3)
     line = {
@@ -302,7 +310,7 @@ def gpu_arm(args, rank, world, local):
         "N_int": inter / N,
         "force_kernel_ms": fms, "lists_kernel_ms": statistics.mean(lists_ms),
         "stage_ms": {k: round(statistics.mean(v), 3) for k, v in stage.items()},
-        "n_groups": st["n_groups"], "n_nodes": st["n_nodes"],
+        "n_groups": st["n_groups"], "n_nodes": st["n_nodes"], "n_list_entries": st["n_list_entries"],
         "pct_fp32_peak_force": 100.0 * achieved / peak,
         "pct_fp32_measured_ffma_force": 100.0 * achieved / peak_meas,
         "fp32_ffma_microbench_tflops": peak_meas,

@@ -46,7 +46,7 @@ struct greem_ctx {
     // S5-S6
     DBuf<float4> flist;
     DBuf<unsigned long long> ilist, loff;
-    DBuf<uint32_t> llen, lraw, kids, stack, order, bins;
+    DBuf<uint32_t> llen, lraw, kids, stack, order, bins, lvl;
     // per call
     DBuf<BoxPar> bps;
     DBuf<uint32_t> box_off, small;
@@ -152,6 +152,11 @@ static int derive_box(const greem_params &p, uint32_t pb, uint32_t pe, BoxPar &b
     memset(&bp, 0, sizeof(bp));
     bp.L = p.L;
     bp.inv_L = 1.0 / p.L;
+    {
+        int e = 0;
+        const double mfrac = std::frexp(p.L, &e);  // L = mfrac * 2^e, mfrac in [0.5, 1)
+        bp.pow2_e = (mfrac == 0.5 && e - 1 > -900 && e - 1 < 900) ? e - 1 : kNotPow2;
+    }
     bp.u = p.L / 4194304.0;
     bp.eta = 0.5 * p.r_cut;
     bp.inv_eta = 1.0 / bp.eta;
@@ -260,6 +265,7 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
     ENS(gidx, nc + 1);
     ENS(groups, nc);
     ENS(kids, nc * 8);
+    ENS(lvl, 96);
     ENS(bps, (size_t)r.nbox);
     ENS(box_off, (size_t)r.nbox + 1);
     ENS(st, 1);
@@ -269,7 +275,7 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
         ENS(llen, nc);
         ENS(lraw, nc);
         ENS(order, nc);
-        ENS(bins, 64);
+        ENS(bins, 128);
         ENS(stack, (size_t)c->nsm * kListBlocksPerSM * kListWarps * c->stack_cap);
         ENS(flist, c->list_cap);
         if (r.index_lists) ENS(ilist, c->list_cap);
@@ -310,8 +316,8 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     const uint32_t *n_nodes = c->base.p + N;
     launch_tree_fill(ks, N, c->box_off.p, nbox, c->d8.p, c->K8.p, c->base.p, c->nodes.p, ncap, c->st.p, s, nsm);
     launch_tree_links(c->nodes.p, n_nodes, ncap, c->nchild.p, c->kids.p, s, nsm);
-    cudaMemsetAsync(c->ctr.p, 0, sizeof(uint32_t) * ncap, s);
-    launch_moments(c->nodes.p, n_nodes, ncap, c->nchild.p, c->ctr.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p, s);
+    launch_moments(c->nodes.p, n_nodes, ncap, c->kids.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p, c->lvl.p,
+                   c->ctr.p, s, nsm);
     launch_leaf_offsets(ks, c->K8.p, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->poff.p, s);
     launch_node_finish(c->nodes.p, n_nodes, ncap, c->raw.p, c->box_off.p, nbox, c->bps.p, c->mom64.p, c->noff.p, s,
                        nsm);
@@ -542,7 +548,8 @@ void greem_destroy(greem_ctx *c)
     release(c->d8); release(c->K8); release(c->nchild); release(c->own); release(c->base); release(c->ctr);
     release(c->gflag); release(c->gidx); release(c->nodes); release(c->raw); release(c->mom64); release(c->noff);
     release(c->poff); release(c->irel); release(c->groups); release(c->flist); release(c->ilist); release(c->loff);
-    release(c->llen); release(c->lraw); release(c->bps); release(c->box_off); release(c->small); release(c->st);
+    release(c->llen); release(c->lraw); release(c->kids); release(c->stack); release(c->order); release(c->bins);
+    release(c->lvl); release(c->bps); release(c->box_off); release(c->small); release(c->st);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->bps_host) cudaFreeHost(c->bps_host);
     if (c->box_off_host) cudaFreeHost(c->box_off_host);

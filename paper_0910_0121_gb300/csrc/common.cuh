@@ -52,7 +52,10 @@ struct BoxPar {
     long long A[22];       // accept a node of level k iff S_d > A[k] (exact form of the theta test)
     uint32_t p_begin, p_end;
     int lmin, n_crit, n_leaf, soft;
+    int pow2_e;            // L = 2^pow2_e exactly, or kNotPow2
+    int pad1;
 };
+constexpr int kNotPow2 = -100000;
 
 // Device status word and counters, cleared at the start of every call.
 struct DevStatus {
@@ -124,9 +127,9 @@ void launch_tree_fill(const uint64_t *keys, uint32_t N, const uint32_t *box_off,
                       cudaStream_t s, int nsm);
 void launch_tree_links(Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, uint8_t *nchild, uint32_t *kids,
                        cudaStream_t s, int nsm);
-void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint8_t *nchild,
-                    uint32_t *ctr, const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw,
-                    cudaStream_t s);
+void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
+                    const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw, uint32_t *lvl,
+                    uint32_t *inodes, cudaStream_t s, int nsm);
 void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
                          const BoxPar *bps, const double *xs, const double *ys, const double *zs, const float *ms,
                          float4 *poff, cudaStream_t s);

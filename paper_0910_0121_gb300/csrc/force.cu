@@ -79,14 +79,29 @@ constexpr float kP2 = 0.2f;                     //  7/35
 constexpr float kP1 = 0.514285714285714286f;    // 18/35
 constexpr float kP0 = 0.0857142857142857143f;   //  3/35
 
+// saturate(a*b + c) and saturate(a + b) as single instructions (the .sat modifier clamps
+// to [0, 1] and turns NaN into 0)
+__device__ __forceinline__ float fma_sat(float a, float b, float c)
+{
+    float d;
+    asm("fma.rn.ftz.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float add_sat(float a, float b)
+{
+    float d;
+    asm("add.rn.ftz.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 // g(R) of Eq. 2 for R >= 0 (see the header comment); 0 for R >= 2.
 __device__ __forceinline__ float g_p3m(float R)
 {
-    const float v = __saturatef(fmaf(R, -0.5f, 1.0f));
+    const float v = fma_sat(R, -0.5f, 1.0f);
     const float v2 = v * v;
     const float v5 = v2 * v2 * v;
     const float c = fmaf(fmaf(fmaf(R, kC3, kC2), R, kC1), R, kC0);
-    const float u = __saturatef(1.0f - R);
+    const float u = add_sat(1.0f, -R);
     const float u2 = u * u;
     const float u6 = u2 * u2 * u2;
     const float p = fmaf(fmaf(R, kP2, kP1), R, kP0);
@@ -120,13 +135,23 @@ __device__ __forceinline__ void interact(const float4 j, const float (&xi)[I], c
     }
 }
 
-// Fewest i-slots (32/S lanes x I) covering n particles, I <= 8; ties go to smaller S.
+// Lane layout of one pass: S parts of li = 32/S lanes, I i-particles per lane.  The pass
+// covering the n remaining particles is the one with the fewest slots li*I >= n; when that
+// wastes more than n/8 slots and n > 32, the pass instead takes the largest slot count
+// <= n and leaves the rest to another pass over the same list.  Ties go to more parts
+// (fewer lanes per part, more i per lane): each list entry's load and loop overhead is
+// then shared by more pairs.
 __device__ __forceinline__ void choose_layout(uint32_t n, int &S, int &I)
 {
+    if (n > 256u) {
+        S = 1;
+        I = 8;
+        return;
+    }
     int bs = 1, bi = 8;
     uint32_t best = 0xffffffffu;
 #pragma unroll
-    for (int s = 1; s <= 8; s <<= 1) {
+    for (int s = 32; s >= 1; s >>= 1) {
         const uint32_t li = 32u / s;
         const uint32_t ii = (n + li - 1) / li;
         if (ii > 8) continue;
@@ -135,6 +160,20 @@ __device__ __forceinline__ void choose_layout(uint32_t n, int &S, int &I)
             best = slots;
             bs = s;
             bi = (int)ii;
+        }
+    }
+    if (n > 32u && best - n > n / 8u) {
+        uint32_t lo = 0;
+#pragma unroll
+        for (int s = 32; s >= 1; s >>= 1) {
+            const uint32_t li = 32u / s;
+            uint32_t ii = n / li;
+            ii = ii > 8u ? 8u : ii;
+            if (ii >= 1 && li * ii > lo) {
+                lo = li * ii;
+                bs = s;
+                bi = (int)ii;
+            }
         }
     }
     S = bs;
@@ -201,10 +240,18 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
         }
         const float4 *buf = wp.buf[b];
         const uint32_t nj = min((uint32_t)a.chunk, len - c * (uint32_t)a.chunk);
+        if constexpr (I <= 2) {
+#pragma unroll 4
+            for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
+                const float4 j = buf[t];
+                interact<I, SOFT>(j, xi, yi, zi, ax, ay, az, eps2);
+            }
+        } else {
 #pragma unroll 2
-        for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
-            const float4 j = buf[t];
-            interact<I, SOFT>(j, xi, yi, zi, ax, ay, az, eps2);
+            for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
+                const float4 j = buf[t];
+                interact<I, SOFT>(j, xi, yi, zi, ax, ay, az, eps2);
+            }
         }
         __syncwarp();
     }
@@ -300,32 +347,38 @@ __device__ __forceinline__ int layout_bin(uint32_t n)
     if (n > 256u) return 0;
     int S, I;
     choose_layout(n, S, I);
-    return (8 - I) * 4 + (S == 1 ? 0 : S == 2 ? 1 : S == 4 ? 2 : 3);
+    return (8 - I) * 6 + (31 - __clz(S));
 }
 
 __global__ void __launch_bounds__(256) k_bin_count(const Group *__restrict__ groups, const uint32_t *n_groups,
                                                    uint32_t *__restrict__ bins)
 {
-    __shared__ uint32_t sb[32];
-    if (threadIdx.x < 32) sb[threadIdx.x] = 0;
+    __shared__ uint32_t sb[64];
+    if (threadIdx.x < 64) sb[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t G = *n_groups;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
         atomicAdd(&sb[layout_bin(groups[g].count)], 1u);
     __syncthreads();
-    if (threadIdx.x < 32 && sb[threadIdx.x]) atomicAdd(&bins[threadIdx.x], sb[threadIdx.x]);
+    if (threadIdx.x < 64 && sb[threadIdx.x]) atomicAdd(&bins[threadIdx.x], sb[threadIdx.x]);
 }
 
 __global__ void k_bin_scan(uint32_t *bins)
 {
     const uint32_t lane = threadIdx.x;
-    uint32_t v = bins[lane], x = v;
+    const uint32_t v0 = bins[lane], v1 = bins[32 + lane];
+    uint32_t x0 = v0, x1 = v1;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= (uint32_t)o) x += y;
+        uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+        if (lane >= (uint32_t)o) {
+            x0 += y0;
+            x1 += y1;
+        }
     }
-    bins[32 + lane] = x - v;  // cursor
+    const uint32_t tot0 = __shfl_sync(0xffffffffu, x0, 31);
+    bins[64 + lane] = x0 - v0;        // cursors
+    bins[96 + lane] = tot0 + x1 - v1;
 }
 
 __global__ void __launch_bounds__(256) k_bin_scatter(const Group *__restrict__ groups, const uint32_t *n_groups,
@@ -333,13 +386,13 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const Group *__restrict__ g
 {
     const uint32_t G = *n_groups;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
-        order[atomicAdd(&bins[32 + layout_bin(groups[g].count)], 1u)] = g;
+        order[atomicAdd(&bins[64 + layout_bin(groups[g].count)], 1u)] = g;
 }
 
 void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t *bins, uint32_t *order,
                         cudaStream_t s, int nsm)
 {
-    cudaMemsetAsync(bins, 0, 64 * sizeof(uint32_t), s);
+    cudaMemsetAsync(bins, 0, 128 * sizeof(uint32_t), s);
     k_bin_count<<<nsm * 4, 256, 0, s>>>(groups, n_groups, bins);
     k_bin_scan<<<1, 32, 0, s>>>(bins);
     k_bin_scatter<<<nsm * 4, 256, 0, s>>>(groups, n_groups, bins, order);

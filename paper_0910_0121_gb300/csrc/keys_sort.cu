@@ -48,6 +48,33 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v)
     return x;
 }
 
+// Power-of-two box side (the usual L = 1): (r/L) 2^21 = r 2^(21-e) exactly, so the cell
+// index is read from the bits of r with integer operations only (no FP64 pipe work).
+// Same result as cell21(): the quotient is exact, and floor of the scaled value is the
+// integer part of the binary expansion.
+__device__ __forceinline__ uint32_t cell21_pow2(double r, int e)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(r);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return 0;  // zero or subnormal
+    const unsigned long long mant = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = (ex - 1023) - 52 + 21 - e;  // value = mant * 2^sh
+    long long i;
+    if (sh >= 0) i = sh >= 11 ? (1ll << 62) : (long long)(mant << sh);
+    else i = -sh >= 64 ? 0 : (long long)(mant >> (-sh));
+    i = i > 2097151 ? 2097151 : i;
+    return (uint32_t)i;
+}
+
+// Wrap with the in-range test done on the bit pattern (non-negative doubles order like
+// their bits): x in [0, L) returns x unchanged; anything else takes the FP64 formula.
+__device__ __forceinline__ double wrap_pos_fast(double x, double L)
+{
+    const long long bx = __double_as_longlong(x), bl = __double_as_longlong(L);
+    if (bx >= 0 && bx < bl) return x;
+    return wrap_pos(x, L);
+}
+
 __global__ void __launch_bounds__(256) k_keys(const double *__restrict__ pos, uint32_t N,
                                               const uint32_t *__restrict__ box_off, int nbox,
                                               const BoxPar *__restrict__ bps, uint64_t *__restrict__ keys,
@@ -58,14 +85,26 @@ __global__ void __launch_bounds__(256) k_keys(const double *__restrict__ pos, ui
     const BoxPar &bp = bps[box_of(i, box_off, nbox)];
     const double L = bp.L, invL = bp.inv_L;
     double x = pos[3 * (size_t)i], y = pos[3 * (size_t)i + 1], z = pos[3 * (size_t)i + 2];
-    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+    // finite test on the exponent bits (integer pipe)
+    const auto nonfinite = [](double v) {
+        return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+    };
+    if (nonfinite(x) || nonfinite(y) || nonfinite(z)) {
         atomicOr(&st->flags, ST_NONFINITE);
         keys[i] = 0;
         return;
     }
-    uint64_t k = (spread3(cell21(wrap_pos(x, L), L, invL)) << 2) | (spread3(cell21(wrap_pos(y, L), L, invL)) << 1) |
-                 spread3(cell21(wrap_pos(z, L), L, invL));
-    keys[i] = k;
+    uint32_t cx, cy, cz;
+    if (bp.pow2_e != kNotPow2) {
+        cx = cell21_pow2(wrap_pos_fast(x, L), bp.pow2_e);
+        cy = cell21_pow2(wrap_pos_fast(y, L), bp.pow2_e);
+        cz = cell21_pow2(wrap_pos_fast(z, L), bp.pow2_e);
+    } else {
+        cx = cell21(wrap_pos_fast(x, L), L, invL);
+        cy = cell21(wrap_pos_fast(y, L), L, invL);
+        cz = cell21(wrap_pos_fast(z, L), L, invL);
+    }
+    keys[i] = (spread3(cx) << 2) | (spread3(cy) << 1) | spread3(cz);
 }
 
 void launch_keys(const double *pos, uint32_t N, const uint32_t *box_off, int nbox, const BoxPar *bps,
@@ -251,9 +290,9 @@ __global__ void __launch_bounds__(256) k_gather(const double *__restrict__ pos, 
     if (i >= N) return;
     uint32_t j = perm[i];
     double L = bps[box_of(i, box_off, nbox)].L;
-    xs[i] = wrap_pos(pos[3 * (size_t)j], L);
-    ys[i] = wrap_pos(pos[3 * (size_t)j + 1], L);
-    zs[i] = wrap_pos(pos[3 * (size_t)j + 2], L);
+    xs[i] = wrap_pos_fast(pos[3 * (size_t)j], L);
+    ys[i] = wrap_pos_fast(pos[3 * (size_t)j + 1], L);
+    zs[i] = wrap_pos_fast(pos[3 * (size_t)j + 2], L);
     ms[i] = mass[j];
 }
 

@@ -189,60 +189,106 @@ void launch_tree_links(Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, 
     g_launches++;
 }
 
-// Monopole moments (Sec. 3.1.2, centre-of-mass approximation), bottom up, one thread
-// per node.  A leaf sums its particles in FP64; the last child to finish (atomic
-// arrival counter) sums the raw moments of all children of its parent in child order and
-// climbs on.  The order of every sum is fixed, so the result does not depend on
-// scheduling.
-__global__ void __launch_bounds__(256) k_moments(const Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
-                                                 uint32_t node_cap, const uint8_t *__restrict__ nchild,
-                                                 uint32_t *__restrict__ ctr, const double *__restrict__ xs,
-                                                 const double *__restrict__ ys, const double *__restrict__ zs,
-                                                 const float *__restrict__ ms, Dbl4 *raw)
+// Monopole moments (Sec. 3.1.2, centre-of-mass approximation), bottom up.  Leaves sum
+// their particles in FP64 (one thread per leaf, in sorted order); internal nodes are
+// bucketed by level and each level, deepest first, sums its children's raw moments in
+// child order (one thread per node, full warps: FP64 issue is expensive on this GPU).
+// Every sum has a fixed order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_moments_leaf(const Node *__restrict__ nodes,
+                                                      const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
+                                                      const double *__restrict__ xs, const double *__restrict__ ys,
+                                                      const double *__restrict__ zs, const float *__restrict__ ms,
+                                                      Dbl4 *__restrict__ raw, uint32_t *__restrict__ lvl)
+{
+    __shared__ uint32_t cnt[32];
+    if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < nn) {
+        const Node nd = nodes[n];
+        if (nd.lvl & 256u) {
+            double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+            for (uint32_t j = nd.begin; j < nd.end; j++) {
+                const double m = (double)ms[j];
+                M += m;
+                sx = fma(m, xs[j], sx);
+                sy = fma(m, ys[j], sy);
+                sz = fma(m, zs[j], sz);
+            }
+            raw[n] = make_dbl4(sx, sy, sz, M);
+        } else {
+            atomicAdd(&cnt[nd.lvl & 255u], 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && cnt[threadIdx.x]) atomicAdd(&lvl[threadIdx.x], cnt[threadIdx.x]);
+}
+
+// lvl[0..32): internal nodes per level -> lvl[32..64): level start, lvl[64..96): cursor
+__global__ void k_level_scan(uint32_t *lvl)
+{
+    const uint32_t lane = threadIdx.x;
+    const uint32_t v = lvl[lane];
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    lvl[32 + lane] = x - v;
+    lvl[64 + lane] = x - v;
+}
+
+__global__ void __launch_bounds__(256) k_level_scatter(const Node *__restrict__ nodes,
+                                                       const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
+                                                       uint32_t *__restrict__ lvl, uint32_t *__restrict__ inodes)
 {
     const uint32_t nn = node_count(n_nodes, node_cap);
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
-    const Node nd = nodes[n];
-    if (!(nd.lvl & 256u)) return;
-    double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-    for (uint32_t j = nd.begin; j < nd.end; j++) {
-        const double m = (double)ms[j];
-        M += m;
-        sx = fma(m, xs[j], sx);
-        sy = fma(m, ys[j], sy);
-        sz = fma(m, zs[j], sz);
-    }
-    raw[n] = make_dbl4(sx, sy, sz, M);
-    uint32_t cur = n;
-    for (;;) {
-        const uint32_t p = nodes[cur].parent;
-        if (p == kNone) break;
-        __threadfence();
-        const uint32_t old = atomicAdd(&ctr[p], 1u);
-        if (old + 1u != (uint32_t)nchild[p]) break;
-        __threadfence();
-        const uint32_t pend = nodes[p].end;
+    const uint32_t l = nodes[n].lvl;
+    if (!(l & 256u)) inodes[atomicAdd(&lvl[64 + (l & 255u)], 1u)] = n;
+}
+
+__global__ void __launch_bounds__(256) k_moments_level(int level, const uint32_t *__restrict__ lvl,
+                                                       const uint32_t *__restrict__ inodes,
+                                                       const uint32_t *__restrict__ kids, Dbl4 *__restrict__ raw)
+{
+    const uint32_t b = lvl[32 + level], e = b + lvl[level];
+    for (uint32_t i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
+        const uint32_t p = inodes[i];
+        const uint4 *kp = reinterpret_cast<const uint4 *>(kids + (size_t)p * 8);
+        const uint4 k0 = kp[0], k1 = kp[1];
+        const uint32_t kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
         Dbl4 a = make_dbl4(0.0, 0.0, 0.0, 0.0);
-        for (uint32_t c = p + 1; c < nn && nodes[c].begin < pend; c = nodes[c].skip) {
-            const double2 *rp = reinterpret_cast<const double2 *>(raw + c);
-            const double2 r0 = __ldcg(rp), r1 = __ldcg(rp + 1);  // L2, not a stale L1 line
-            a.x += r0.x;
-            a.y += r0.y;
-            a.z += r1.x;
-            a.w += r1.y;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if (kk[q] == kNone) break;
+            const Dbl4 r = raw[kk[q]];
+            a.x += r.x;
+            a.y += r.y;
+            a.z += r.z;
+            a.w += r.w;
         }
         raw[p] = a;
-        cur = p;
     }
 }
 
-void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint8_t *nchild,
-                    uint32_t *ctr, const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw,
-                    cudaStream_t s)
+void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
+                    const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw, uint32_t *lvl,
+                    uint32_t *inodes, cudaStream_t s, int nsm)
 {
-    k_moments<<<(node_cap + 255) / 256, 256, 0, s>>>(nodes, n_nodes, node_cap, nchild, ctr, xs, ys, zs, ms, raw);
-    g_launches++;
+    cudaMemsetAsync(lvl, 0, 96 * sizeof(uint32_t), s);
+    const unsigned grid = (node_cap + 255) / 256;
+    k_moments_leaf<<<grid, 256, 0, s>>>(nodes, n_nodes, node_cap, xs, ys, zs, ms, raw, lvl);
+    k_level_scan<<<1, 32, 0, s>>>(lvl);
+    k_level_scatter<<<grid, 256, 0, s>>>(nodes, n_nodes, node_cap, lvl, inodes);
+    g_launches += 3;
+    for (int level = kMaxLevel - 1; level >= 0; level--) {
+        k_moments_level<<<nsm * 4, 256, 0, s>>>(level, lvl, inodes, kids, raw);
+        g_launches++;
+    }
 }
 
 // Each particle's offset from the centre of its leaf cell (level K_i) in eta units: the
