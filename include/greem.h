@@ -179,6 +179,22 @@ int greem_autotune(greem_ctx *ctx, const double *pos, const float *mass, int64_t
 int greem_pair_force_f32(greem_ctx *ctx, const double *x_g, const double *x_i, const double *x_j, const float *m_j,
                          int64_t npairs, double r_cut, double eps, float *acc);
 
+/* The pairwise FP32 force of greem_pair_force_f32 for callers that cannot allocate
+ * device memory (a library whose allocator policy forbids driver allocations, work that
+ * must not synchronise the way cudaMalloc/cudaFree can, a process whose free memory
+ * belongs to another allocator).  The paper has no counterpart: it is a deployment
+ * variant.  It allocates nothing: its scratch is a file-scope device array sized for at
+ * most 32768 pairs (about 6.5 MB, held on every GPU that loads the library until exit).
+ * The caller passes inputs and output as for greem_pair_force_f32, plus the stream to
+ * run on (NULL = legacy default stream); the call waits for that stream.  The first
+ * call on each device looks up the array's device address and should come before any
+ * stream capture.  All calls on a device share the array (it keeps the last call's
+ * contents); calls that overlap on the GPU race, so serialise them.
+ * Errors: INVALID_ARG (npairs < 1 or > 32768, r_cut <= 0, eps < 0, NULL pointer), CUDA,
+ * TIMEOUT. */
+int greem_pair_force_f32_noalloc(const double *x_g, const double *x_i, const double *x_j, const float *m_j,
+                                 int64_t npairs, double r_cut, double eps, float *acc, void *cuda_stream);
+
 /* Measured arithmetic peak of this GPU: which = 0 FP32 FMA, 1 FP64 FMA; *tflops gets
  * the rate (2 flops per FMA) of an FMA-chain microbenchmark over all SMs, at whatever
  * clock the GPU runs at the time.  Errors: INVALID_ARG, CUDA. */
