@@ -40,12 +40,28 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-crit", type=int, default=0, help="skip autotuning and use this n_crit")
+    ap.add_argument("--no-extras", action="store_true", help="skip the graph, theta-scan and batched lines")
     return ap.parse_args()
 
 
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def across_ranks(ms_local: float, n_local: int, dist=None, device=None):
+    """Whole-job numbers for N independent replicas (weak scaling): the step time is
+    the slowest rank's, and the particle count is every rank's.  Returns
+    (ms_per_step, particles_per_s).  With dist=None this is one rank."""
+    if dist is None:
+        return ms_local, n_local / (ms_local * 1e-3)
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    n = torch.tensor([float(n_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return ms, float(n.item()) / (ms * 1e-3)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -186,6 +202,82 @@ def traffic_per_launch(list_entries):
         return None
 
 
+def extras(ctx, P, M, p, prm, acc, stream):
+    """Context numbers beside the headline: CUDA-graph replay of the same step, the
+    opening-angle scan, and the 64-box batched workload (one call vs per-box calls)."""
+    import torch
+    from paper_0910_0121_gb300 import greem, synth
+    out = {}
+    N = P.shape[0]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # graph replay of the whole step
+    ctx.graph_capture(P, M, greem.params(L=p.L, r_cut=p.r_cut, theta=p.theta, n_crit=p.n_crit, n_leaf=p.n_leaf,
+                                         list_chunk=p.list_chunk, block_shape=p.block_shape), acc)
+    for _ in range(2):
+        ctx.graph_launch()
+    a, b = ev(), ev()
+    a.record(stream)
+    reps = 5
+    for _ in range(reps):
+        rc = ctx.graph_launch()
+        if rc != greem.OK:
+            raise greem.GreemError(rc, "greem_graph_launch")
+    b.record(stream)
+    torch.cuda.synchronize()
+    gms = a.elapsed_time(b) / reps
+    out["graph_replay"] = {"ms_per_step": gms, "particles_per_s": N / (gms * 1e-3)}
+    # opening-angle scan at the tuned n_crit
+    scan = {}
+    for th in (0.3, 0.5, 0.7):
+        q = greem.params(L=p.L, r_cut=p.r_cut, theta=th, n_crit=p.n_crit, n_leaf=p.n_leaf, list_chunk=p.list_chunk,
+                         block_shape=p.block_shape, flags=greem.FLAG_STAGE_TIMES)
+        ctx.short_force(P, M, q, acc)
+        a, b = ev(), ev()
+        a.record(stream)
+        ctx.short_force(P, M, q, acc)
+        b.record(stream)
+        torch.cuda.synchronize()
+        s = ctx.stats()
+        scan[str(th)] = {"ms_per_step": a.elapsed_time(b), "N_int": s["n_interactions"] / N,
+                         "force_tflops": FLOPS_PER_INTERACTION * s["n_interactions"] / (s["ms_force"] * 1e-3) / 1e12}
+    out["theta_scan"] = scan
+    # 64 independent boxes: one batched call vs one call per box (FP32) and per-box FP64 calls
+    bpos, bmass, boff, bprm = synth.config_batched()
+    BP = torch.from_numpy(bpos).cuda()
+    BM = torch.from_numpy(bmass).cuda()
+    per = [greem.params(L=q["L"], r_cut=q["r_cut"], theta=q["theta"], n_crit=p.n_crit, n_leaf=10,
+                        list_chunk=p.list_chunk, block_shape=p.block_shape) for q in bprm]
+    bacc = ctx.short_force_batched(BP, BM, boff, per)
+    a, b = ev(), ev()
+    a.record(stream)
+    ctx.short_force_batched(BP, BM, boff, per, bacc)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_batched = a.elapsed_time(b)
+    views = [(BP[boff[k]:boff[k + 1]], BM[boff[k]:boff[k + 1]]) for k in range(len(per))]
+    for (vp, vm), q in zip(views, per):
+        ctx.short_force(vp, vm, q)
+    a.record(stream)
+    for (vp, vm), q in zip(views, per):
+        ctx.short_force(vp, vm, q)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_single = a.elapsed_time(b)
+    per64 = [greem.params(L=q.L, r_cut=q.r_cut, theta=q.theta, n_crit=q.n_crit, n_leaf=10, precision=greem.F64)
+             for q in per]
+    a.record(stream)
+    for (vp, vm), q in zip(views, per64):
+        ctx.short_force(vp, vm, q)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t64 = a.elapsed_time(b)
+    NB = int(boff[-1])
+    out["batched64"] = {"N": NB, "boxes": len(per), "batched_ms": t_batched, "per_box_fp32_ms": t_single,
+                        "per_box_fp64_ms": t64, "batched_particles_per_s": NB / (t_batched * 1e-3),
+                        "speedup_vs_per_box_fp32": t_single / t_batched, "speedup_vs_per_box_fp64": t64 / t_batched}
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def gpu_arm(args, rank, world, local):
     import torch
@@ -243,11 +335,7 @@ def gpu_arm(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = across_ranks(e0.elapsed_time(e1) / args.steps, N, dist, "cuda")
     clocks = clk.summary()
 
     # ---- end to end through the public API with host buffers
@@ -271,11 +359,7 @@ def gpu_arm(args, rank, world, local):
         hacc.copy_(acc, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = f0.elapsed_time(f1) / e2
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e, value_e2e = across_ranks(f0.elapsed_time(f1) / e2, N, dist, "cuda")
 
     # ---- FP64 form on the same lists, and the measured FP32 FMA peak
     p64 = greem.params(L=p.L, r_cut=p.r_cut, theta=p.theta, n_crit=p.n_crit, n_leaf=p.n_leaf,
@@ -298,7 +382,6 @@ def gpu_arm(args, rank, world, local):
     peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     traffic = traffic_per_launch(st["n_list_entries"])
 
-    value = world * N / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -321,11 +404,13 @@ def gpu_arm(args, rank, world, local):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_force_f32", "work_per_launch": f"{inter} interactions x 42 flops",
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz"},
-        "e2e": {"value": world * N / (ms_e2e * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": N * (24 + 4),
+        "e2e": {"value": value_e2e, "unit": "particles/s", "h2d_bytes_per_step": N * (24 + 4),
                 "d2h_bytes_per_step": N * 12},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if not args.no_extras:
+        line["extras"] = extras(ctx, P, M, p, prm, acc, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, desc, nth = oracle_sample(pos, mass, prm, n_crit=p.n_crit)
         line["cpu_baseline"] = {"value": N / t_cpu, "unit": "particles/s", "cores": nth, "kind": "oracle",

@@ -164,6 +164,16 @@ int greem_get_stats(greem_ctx *ctx, greem_stats *out);
  * Errors: INVALID_ARG (unknown what, no previous call, cap too small -> *len_bytes set). */
 int greem_debug_dump(greem_ctx *ctx, int what, void *host_buf, int64_t cap_bytes, int64_t *len_bytes);
 
+/* The interaction lists of selected groups only (for sampled checks at sizes where the
+ * whole list dump would not fit in host memory).  groups: HOST int64 [ngroups] group
+ * indices (0 <= g < n_groups of the last force call, which must have used
+ * GREEM_FLAG_INDEX_LISTS).  offsets: HOST int64 [ngroups+1] CSR offsets (written);
+ * entries: HOST int64 [cap_entries, 5] as GREEM_DUMP_LISTS, each list in preorder.
+ * *n_entries always gets the total.  Errors: INVALID_ARG (no lists, bad group index,
+ * cap_entries too small), CUDA. */
+int greem_debug_dump_group_lists(greem_ctx *ctx, const int64_t *groups, int64_t ngroups, int64_t *offsets,
+                                 int64_t *entries, int64_t cap_entries, int64_t *n_entries);
+
 /* Picks n_crit from candidates[0..ncand) (ncand = 0 -> 32, 48, 64, 96, 128, 192, 256, 384,
  * 512), then list_chunk and block_shape, by timing the whole force on these inputs; writes
  * the best parameters to *best (a copy of *p with those three fields set).  acc is scratch

@@ -162,6 +162,7 @@ static int derive_box(const greem_params &p, uint32_t pb, uint32_t pe, BoxPar &b
     bp.inv_eta = 1.0 / bp.eta;
     bp.eps = p.eps;
     bp.k_f = (float)(bp.u / bp.eta);
+    bp.k52_f = (float)(std::ldexp(p.L, -52) / bp.eta);
     bp.inv_eta2 = (float)(bp.inv_eta * bp.inv_eta);
     bp.eps2 = (float)((p.eps / bp.eta) * (p.eps / bp.eta));
     bp.soft = p.eps > 0 ? 1 : 0;
@@ -827,6 +828,64 @@ int greem_debug_dump(greem_ctx *c, int what, void *host_buf, int64_t cap_bytes, 
     default:
         return GREEM_ERR_INVALID_ARG;
     }
+}
+
+int greem_debug_dump_group_lists(greem_ctx *c, const int64_t *groups, int64_t ngroups, int64_t *offsets,
+                                 int64_t *entries, int64_t cap_entries, int64_t *n_entries)
+{
+    if (!c || !groups || !offsets || !n_entries || ngroups < 0) return GREEM_ERR_INVALID_ARG;
+    *n_entries = 0;
+    if (!c->have_lists || !c->have_index) return GREEM_ERR_INVALID_ARG;
+    const int64_t G = c->stats.n_groups;
+    if (!cuda_ok(cudaStreamSynchronize(c->stream))) return GREEM_ERR_CUDA;
+    std::vector<uint32_t> raw(ngroups);
+    std::vector<unsigned long long> off(ngroups);
+    std::vector<Group> grp(ngroups);
+    int64_t tot = 0;
+    for (int64_t k = 0; k < ngroups; k++) {
+        const int64_t g = groups[k];
+        if (g < 0 || g >= G) return GREEM_ERR_INVALID_ARG;
+        if (!cuda_ok(cudaMemcpy(&raw[k], c->lraw.p + g, 4, cudaMemcpyDeviceToHost)) ||
+            !cuda_ok(cudaMemcpy(&off[k], c->loff.p + g, 8, cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        offsets[k] = tot;
+        tot += raw[k];
+    }
+    offsets[ngroups] = tot;
+    *n_entries = tot;
+    if (!entries || cap_entries < tot) return tot ? GREEM_ERR_INVALID_ARG : GREEM_OK;
+    auto dec = [](unsigned v) -> int64_t { return v == 1u ? 1 : (v == 2u ? -1 : 0); };
+    std::vector<unsigned long long> buf;
+    int64_t e = 0;
+    for (int64_t k = 0; k < ngroups; k++) {
+        buf.resize(raw[k]);
+        if (raw[k] && !cuda_ok(cudaMemcpy(buf.data(), c->ilist.p + off[k], (size_t)raw[k] * 8, cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        // first particle of each entry (node begin for nodes) gives preorder
+        std::vector<std::pair<uint64_t, unsigned long long>> keyed(raw[k]);
+        for (uint32_t t = 0; t < raw[k]; t++) {
+            const unsigned long long v = buf[t];
+            uint64_t first = (uint32_t)v;
+            if ((v >> 32) & 1ull) {
+                Node nd;
+                if (!cuda_ok(cudaMemcpy(&nd, c->nodes.p + (uint32_t)v, sizeof(Node), cudaMemcpyDeviceToHost)))
+                    return GREEM_ERR_CUDA;
+                first = nd.begin;
+            }
+            keyed[t] = {first, v};
+        }
+        std::sort(keyed.begin(), keyed.end());
+        for (uint32_t t = 0; t < raw[k]; t++, e++) {
+            const unsigned long long v = keyed[t].second;
+            const unsigned code = (unsigned)(v >> 33) & 63u;
+            entries[5 * e + 0] = (int64_t)((v >> 32) & 1ull);
+            entries[5 * e + 1] = (int64_t)(uint32_t)v;
+            entries[5 * e + 2] = dec(code & 3u);
+            entries[5 * e + 3] = dec((code >> 2) & 3u);
+            entries[5 * e + 4] = dec((code >> 4) & 3u);
+        }
+    }
+    return GREEM_OK;
 }
 
 int greem_autotune(greem_ctx *c, const double *pos, const float *mass, int64_t N, const greem_params *p,

@@ -45,9 +45,9 @@ static_assert(sizeof(Group) == 32, "Group must be 32 bytes");
 struct BoxPar {
     double L, inv_L, u, eta, inv_eta, eps;
     float k_f;             // u/eta rounded to float: cell offsets -> eta units
+    float k52_f;           // (L/2^52)/eta rounded to float: fixed52 offsets -> eta units
     float inv_eta2;        // 1/eta^2: eta-unit accelerations -> physical
     float eps2;            // (eps/eta)^2
-    float pad0;
     long long T_prune;     // prune a node iff S_gap > T_prune (exact form of the r_cut test)
     long long A[22];       // accept a node of level k iff S_d > A[k] (exact form of the theta test)
     uint32_t p_begin, p_end;
@@ -86,6 +86,44 @@ constexpr int kListBlocksPerSM = 4;
 
 // Kernel launches made by the current host thread (reported in greem_stats).
 extern thread_local long long g_launches;
+
+// x in [0, L) with L = 2^e: floor(x 2^(52-e)), i.e. x in units of L/2^52, read from the
+// bits of x with integer operations (exact for x >= L/2, truncated below 2^-52 L for
+// smaller x).  Cell centres are exact in these units, so an offset from a centre is one
+// integer subtraction.
+__device__ __forceinline__ long long fixed52(double x, int e)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return 0;
+    const unsigned long long mant = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = (ex - 1023) - e;  // x 2^(52-e) = mant 2^sh
+    if (sh >= 0) return sh > 10 ? (1ll << 62) : (long long)(mant << sh);
+    return -sh >= 64 ? 0 : (long long)(mant >> (-sh));
+}
+
+// Periodic wrap into [0, L): r = x - L floor(x/L); r < 0 -> r + L; r >= L -> r - L;
+// anything still outside [0, L) -> 0.  Each FP64 step is rounded separately (no FMA).
+__device__ __forceinline__ double wrap_pos(double x, double L)
+{
+    // x in [0, L) already: floor(x/L) = 0 and the formula returns x unchanged
+    if (x >= 0.0 && x < L) return x;
+    double f = floor(__ddiv_rn(x, L));
+    double r = __dsub_rn(x, __dmul_rn(L, f));
+    if (r < 0.0) r = __dadd_rn(r, L);
+    if (r >= L) r = __dsub_rn(r, L);
+    if (!(r >= 0.0 && r < L)) r = 0.0;
+    return r;
+}
+
+// Wrap with the in-range test done on the bit pattern (non-negative doubles order like
+// their bits): x in [0, L) returns x unchanged; anything else takes the FP64 formula.
+__device__ __forceinline__ double wrap_pos_fast(double x, double L)
+{
+    const long long bx = __double_as_longlong(x), bl = __double_as_longlong(L);
+    if (bx >= 0 && bx < bl) return x;
+    return wrap_pos(x, L);
+}
 
 // Box of sorted/input particle i: box_off holds nbox+1 increasing offsets.
 __device__ __forceinline__ int box_of(uint32_t i, const uint32_t *__restrict__ box_off, int nbox)

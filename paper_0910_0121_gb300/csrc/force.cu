@@ -70,6 +70,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Largest number of i-particles a lane holds in one pass, and the launch bounds of the
+// force kernel (registers per thread follow from them).
+#ifndef GREEM_FORCE_IMAX
+#define GREEM_FORCE_IMAX 6
+#endif
+#ifndef GREEM_FORCE_THREADS
+#define GREEM_FORCE_THREADS 512
+#endif
+#ifndef GREEM_FORCE_MINB
+#define GREEM_FORCE_MINB 1
+#endif
+#ifndef GREEM_FORCE_UNROLL
+#define GREEM_FORCE_UNROLL 2
+#endif
+constexpr int kImax = GREEM_FORCE_IMAX;
+constexpr int kUnroll = GREEM_FORCE_UNROLL;
+
 // ------------------------------------------------------------------ Eq. 2 constants
 constexpr float kC3 = 1.6f;                     // (8/35) * 7
 constexpr float kC2 = 5.028571428571428571f;    // (8/35) * 22
@@ -143,18 +160,18 @@ __device__ __forceinline__ void interact(const float4 j, const float (&xi)[I], c
 // then shared by more pairs.
 __device__ __forceinline__ void choose_layout(uint32_t n, int &S, int &I)
 {
-    if (n > 256u) {
+    if (n > 32u * kImax) {
         S = 1;
-        I = 8;
+        I = kImax;
         return;
     }
-    int bs = 1, bi = 8;
+    int bs = 1, bi = kImax;
     uint32_t best = 0xffffffffu;
 #pragma unroll
     for (int s = 32; s >= 1; s >>= 1) {
         const uint32_t li = 32u / s;
         const uint32_t ii = (n + li - 1) / li;
-        if (ii > 8) continue;
+        if (ii > (uint32_t)kImax) continue;
         const uint32_t slots = li * ii;
         if (slots < best) {
             best = slots;
@@ -168,7 +185,7 @@ __device__ __forceinline__ void choose_layout(uint32_t n, int &S, int &I)
         for (int s = 32; s >= 1; s >>= 1) {
             const uint32_t li = 32u / s;
             uint32_t ii = n / li;
-            ii = ii > 8u ? 8u : ii;
+            ii = ii > (uint32_t)kImax ? (uint32_t)kImax : ii;
             if (ii >= 1 && li * ii > lo) {
                 lo = li * ii;
                 bs = s;
@@ -247,7 +264,7 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
                 interact<I, SOFT>(j, xi, yi, zi, ax, ay, az, eps2);
             }
         } else {
-#pragma unroll 2
+#pragma unroll(kUnroll)
             for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
                 const float4 j = buf[t];
                 interact<I, SOFT>(j, xi, yi, zi, ax, ay, az, eps2);
@@ -280,7 +297,7 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
 }
 
 template <bool SOFT>
-__global__ void __launch_bounds__(512) k_force_f32(ForceArgs a)
+__global__ void __launch_bounds__(GREEM_FORCE_THREADS, GREEM_FORCE_MINB) k_force_f32(ForceArgs a)
 {
     extern __shared__ __align__(128) float4 sm[];
     __shared__ __align__(8) uint64_t bars[16][2];
@@ -321,10 +338,19 @@ __global__ void __launch_bounds__(512) k_force_f32(ForceArgs a)
             case 2: ok = group_pass<2, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
             case 3: ok = group_pass<3, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
             case 4: ok = group_pass<4, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+#if GREEM_FORCE_IMAX >= 5
             case 5: ok = group_pass<5, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+#endif
+#if GREEM_FORCE_IMAX >= 6
             case 6: ok = group_pass<6, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+#endif
+#if GREEM_FORCE_IMAX >= 7
             case 7: ok = group_pass<7, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
-            default: ok = group_pass<8, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+#endif
+#if GREEM_FORCE_IMAX >= 8
+            case 8: ok = group_pass<8, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+#endif
+            default: ok = false; break;  // not reachable: choose_layout never exceeds kImax
             }
             const uint32_t slots = (uint32_t)(32 / S) * (uint32_t)I;
             evals += (unsigned long long)slots * len;
@@ -344,7 +370,7 @@ __global__ void __launch_bounds__(512) k_force_f32(ForceArgs a)
 // (one instruction-cache footprint) and the cheapest groups come last.
 __device__ __forceinline__ int layout_bin(uint32_t n)
 {
-    if (n > 256u) return 0;
+    if (n > 32u * kImax) return 0;
     int S, I;
     choose_layout(n, S, I);
     return (8 - I) * 6 + (31 - __clz(S));
@@ -385,8 +411,19 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const Group *__restrict__ g
                                                      uint32_t *__restrict__ bins, uint32_t *__restrict__ order)
 {
     const uint32_t G = *n_groups;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
-        order[atomicAdd(&bins[64 + layout_bin(groups[g].count)], 1u)] = g;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // whole warps iterate together so that the bin atomics can be aggregated per warp
+    for (uint32_t g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < G; g0 += stride) {
+        const uint32_t g = g0 + lane;
+        const uint32_t key = g < G ? (uint32_t)layout_bin(groups[g].count) : 1024u;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (g < G && lane == leader) base = atomicAdd(&bins[64 + key], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (g < G) order[base + __popc(peers & ((1u << lane) - 1u))] = g;
+    }
 }
 
 void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t *bins, uint32_t *order,

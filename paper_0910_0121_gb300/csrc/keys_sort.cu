@@ -9,18 +9,6 @@
 
 namespace greem {
 
-__device__ __forceinline__ double wrap_pos(double x, double L)
-{
-    // x in [0, L) already: floor(x/L) = 0 and the formula returns x unchanged
-    if (x >= 0.0 && x < L) return x;
-    double f = floor(__ddiv_rn(x, L));
-    double r = __dsub_rn(x, __dmul_rn(L, f));
-    if (r < 0.0) r = __dadd_rn(r, L);
-    if (r >= L) r = __dsub_rn(r, L);
-    if (!(r >= 0.0 && r < L)) r = 0.0;
-    return r;
-}
-
 // floor((r/L) 2^21) clamped to [0, 2^21-1].  r * (1/L) differs from the rounded
 // quotient by at most 3 ulp, i.e. by < 1e-9 after the scaling, so its floor is the same
 // unless the scaled value lies within 1e-6 of an integer; only then is the exact
@@ -64,15 +52,6 @@ __device__ __forceinline__ uint32_t cell21_pow2(double r, int e)
     else i = -sh >= 64 ? 0 : (long long)(mant >> (-sh));
     i = i > 2097151 ? 2097151 : i;
     return (uint32_t)i;
-}
-
-// Wrap with the in-range test done on the bit pattern (non-negative doubles order like
-// their bits): x in [0, L) returns x unchanged; anything else takes the FP64 formula.
-__device__ __forceinline__ double wrap_pos_fast(double x, double L)
-{
-    const long long bx = __double_as_longlong(x), bl = __double_as_longlong(L);
-    if (bx >= 0 && bx < bl) return x;
-    return wrap_pos(x, L);
 }
 
 __global__ void __launch_bounds__(256) k_keys(const double *__restrict__ pos, uint32_t N,
@@ -183,12 +162,17 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *__res
     uint32_t v[kRsItems], dg[kRsItems], rk[kRsItems];
     const uint32_t wbase = blockIdx.x * kRsTile + w * (kRsItems * 32);
     const unsigned lt = (1u << lane) - 1u;
+    // all of this thread's loads are issued before the ranking, which is serialised
+    // through shared memory
 #pragma unroll
     for (int t = 0; t < kRsItems; t++) {
-        uint32_t i = wbase + t * 32 + lane;
-        bool valid = i < n;
-        k[t] = valid ? kin[i] : 0ull;
-        v[t] = valid ? (vin ? vin[i] : i) : 0u;
+        const uint32_t i = wbase + t * 32 + lane;
+        k[t] = i < n ? kin[i] : 0ull;
+        v[t] = i < n ? (vin ? vin[i] : i) : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < kRsItems; t++) {
+        const bool valid = wbase + t * 32 + lane < n;
         uint32_t d = valid ? rs_digit<SRC>(k[t], v[t], shift, box_off, nbox) : 256u;
         dg[t] = d;
         unsigned peers = __match_any_sync(0xffffffffu, d);

@@ -246,9 +246,17 @@ __global__ void __launch_bounds__(256) k_level_scatter(const Node *__restrict__ 
 {
     const uint32_t nn = node_count(n_nodes, node_cap);
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= nn) return;
-    const uint32_t l = nodes[n].lvl;
-    if (!(l & 256u)) inodes[atomicAdd(&lvl[64 + (l & 255u)], 1u)] = n;
+    const uint32_t l = n < nn ? nodes[n].lvl : 256u;
+    const bool internal = !(l & 256u);
+    const uint32_t key = internal ? (l & 255u) : 1024u;
+    // one atomic per distinct level per warp
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (internal && lane == leader) base = atomicAdd(&lvl[64 + key], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (internal) inodes[base + __popc(peers & ((1u << lane) - 1u))] = n;
 }
 
 __global__ void __launch_bounds__(256) k_moments_level(int level, const uint32_t *__restrict__ lvl,
@@ -306,10 +314,19 @@ __global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict
     const uint32_t h = 1u << (kMaxLevel - k);
     const uint32_t mask = ~(h - 1u);
     const uint64_t key = keys[i];
+    const uint32_t cx = 2u * (compact3(key >> 2) & mask) + h, cy = 2u * (compact3(key >> 1) & mask) + h,
+                   cz = 2u * (compact3(key) & mask) + h;
+    if (bp.pow2_e != kNotPow2) {
+        // integer offsets in units of L/2^52 (centre = c_u * 2^30), one rounding to FP32
+        const int e = bp.pow2_e;
+        const float s = bp.k52_f;
+        poff[i] = make_float4(__ll2float_rn(fixed52(xs[i], e) - ((long long)cx << 30)) * s,
+                              __ll2float_rn(fixed52(ys[i], e) - ((long long)cy << 30)) * s,
+                              __ll2float_rn(fixed52(zs[i], e) - ((long long)cz << 30)) * s, ms[i]);
+        return;
+    }
     const double u = bp.u, ie = bp.inv_eta;
-    const double cxa = __dmul_rn((double)(2u * (compact3(key >> 2) & mask) + h), u);
-    const double cya = __dmul_rn((double)(2u * (compact3(key >> 1) & mask) + h), u);
-    const double cza = __dmul_rn((double)(2u * (compact3(key) & mask) + h), u);
+    const double cxa = __dmul_rn((double)cx, u), cya = __dmul_rn((double)cy, u), cza = __dmul_rn((double)cz, u);
     poff[i] = make_float4((float)__dmul_rn(__dsub_rn(xs[i], cxa), ie), (float)__dmul_rn(__dsub_rn(ys[i], cya), ie),
                           (float)__dmul_rn(__dsub_rn(zs[i], cza), ie), ms[i]);
 }
@@ -350,8 +367,17 @@ __global__ void __launch_bounds__(256) k_node_finish(const Node *__restrict__ no
             cz = r.z * inv;
         }
         mom64[n] = make_dbl4(cx, cy, cz, r.w);
-        noff[n] = make_float4((float)__dmul_rn(__dsub_rn(cx, cxa), ie), (float)__dmul_rn(__dsub_rn(cy, cya), ie),
-                              (float)__dmul_rn(__dsub_rn(cz, cza), ie), (float)r.w);
+        if (bp.pow2_e != kNotPow2) {
+            const int e = bp.pow2_e;
+            const float s = bp.k52_f;
+            const long long sh = 30;
+            noff[n] = make_float4(__ll2float_rn(fixed52(cx, e) - ((long long)(2u * nd.ix + h) << sh)) * s,
+                                  __ll2float_rn(fixed52(cy, e) - ((long long)(2u * nd.iy + h) << sh)) * s,
+                                  __ll2float_rn(fixed52(cz, e) - ((long long)(2u * nd.iz + h) << sh)) * s, (float)r.w);
+        } else {
+            noff[n] = make_float4((float)__dmul_rn(__dsub_rn(cx, cxa), ie), (float)__dmul_rn(__dsub_rn(cy, cya), ie),
+                                  (float)__dmul_rn(__dsub_rn(cz, cza), ie), (float)r.w);
+        }
     }
 }
 

@@ -86,6 +86,7 @@ def _lib():
             L.greem_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
             L.greem_debug_dump.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
             L.greem_autotune.argtypes = [vp, vp, vp, i64, P, vp, i32, vp, P]
+            L.greem_debug_dump_group_lists.argtypes = [vp, vp, i64, vp, vp, i64, ctypes.POINTER(i64)]
             L.greem_pair_force_f32.argtypes = [vp, vp, vp, vp, vp, i64, dbl, dbl, vp]
             L.greem_peak_tflops.argtypes = [vp, i32, ctypes.POINTER(dbl)]
             L.greem_strerror.argtypes = [i32]
@@ -93,7 +94,7 @@ def _lib():
             for f in ("greem_create", "greem_build_tree", "greem_short_force", "greem_short_force_ex",
                       "greem_short_force_batched", "greem_pm_force", "greem_graph_capture", "greem_graph_launch",
                       "greem_get_stats", "greem_debug_dump", "greem_autotune", "greem_pair_force_f32",
-                      "greem_peak_tflops"):
+                      "greem_peak_tflops", "greem_debug_dump_group_lists"):
                 getattr(L, f).restype = i32
             _L = L
     return _L
@@ -233,6 +234,22 @@ class Context:
         s = Stats()
         _check(_lib().greem_get_stats(self._h, ctypes.byref(s)), "greem_get_stats")
         return {n: getattr(s, n) for n, _ in Stats._fields_}
+
+    def dump_group_lists(self, groups):
+        """(offsets [n+1], entries [E,5]) of the selected groups' lists, each in preorder."""
+        g = np.ascontiguousarray(groups, dtype=np.int64)
+        off = np.zeros(g.shape[0] + 1, np.int64)
+        n = ctypes.c_int64()
+        vp = ctypes.c_void_p
+        rc = _lib().greem_debug_dump_group_lists(self._h, g.ctypes.data_as(vp), g.shape[0], off.ctypes.data_as(vp),
+                                                None, 0, ctypes.byref(n))
+        if rc != OK and n.value == 0:
+            raise GreemError(rc, "greem_debug_dump_group_lists")
+        ent = np.zeros((max(n.value, 1), 5), np.int64)
+        _check(_lib().greem_debug_dump_group_lists(self._h, g.ctypes.data_as(vp), g.shape[0], off.ctypes.data_as(vp),
+                                                   ent.ctypes.data_as(vp), n.value, ctypes.byref(n)),
+               "greem_debug_dump_group_lists")
+        return off, ent[: n.value]
 
     def dump(self, what: int) -> np.ndarray:
         n = ctypes.c_int64()
