@@ -54,6 +54,13 @@ extern "C" {
 #define GREEM_FLAG_INDEX_LISTS 1u  /* also keep the interaction lists as (kind, index, image)
                                       entries so that greem_debug_dump(GREEM_DUMP_LISTS) works */
 #define GREEM_FLAG_STAGE_TIMES 2u  /* record per-stage device times in greem_stats */
+#define GREEM_FLAG_ADD_PM 4u       /* add the PM (long-range) force of greem_pm_force, on n_pm^3 with
+                                      the assign scheme, to acc in the same call (single box, FP32):
+                                      the full TreePM force, Sec. 2.1 */
+
+/* PM mass assignment schemes (greem_pm_force, greem_params.assign). */
+#define GREEM_ASSIGN_CIC 0
+#define GREEM_ASSIGN_TSC 1         /* the paper's choice (Sec. 2.2 step 1) */
 
 typedef struct greem_params {
     double L;        /* periodic box side, > 0 */
@@ -68,6 +75,8 @@ typedef struct greem_params {
                         two in [64, 2048] */
     int block_shape; /* warps per force-kernel block: 0 = default (8); 1..16 */
     unsigned flags;  /* GREEM_FLAG_* */
+    int n_pm;        /* PM grid points per side for GREEM_FLAG_ADD_PM (8..1024) */
+    int assign;      /* GREEM_ASSIGN_CIC or GREEM_ASSIGN_TSC for GREEM_FLAG_ADD_PM */
 } greem_params;
 
 /* Fills defaults: L 1, r_cut 3/32, theta 0.5, eps 0, n_crit 64, n_leaf 10 (Sec. 3.1.2),
@@ -114,8 +123,15 @@ int greem_short_force_ex(greem_ctx *ctx, const double *pos, const float *mass, i
 int greem_short_force_batched(greem_ctx *ctx, int nbox, const int64_t *offsets, const double *pos,
                               const float *mass, const greem_params *per_box, void *acc);
 
-/* PM (long-range) part: CIC/TSC assignment, Green's function and interpolation
- * (Sec. 2.2 step 1).  Not part of this build: returns GREEM_ERR_NOT_IMPLEMENTED. */
+/* PM (long-range) part of the TreePM split (Sec. 2.1; Sec. 2.2 step 1; Table 2): mass
+ * assigned to an n_pm^3 periodic grid (points at j L/n_pm) with CIC or TSC, FFT (cuFFT,
+ * FP32), convolution with G(k) = -4 pi S(k eta)^2 / (k^2 W(k)^2) where S is the transform
+ * of the S2 cloud of radius eta = r_cut/2 (so that PP of Eq. 1-2 plus PM is Newton's law)
+ * and W the assignment window (deconvolved twice), k = 0 removed, spectral gradient,
+ * interpolation with the same weights.  pos/mass/acc_pm as for the short-range calls
+ * (device, input order); acc_pm is float32 [N,3] and is overwritten.  Errors:
+ * INVALID_ARG (N < 1, L <= 0, n_pm outside 8..1024, r_cut outside (0, L/2), unknown
+ * assign), CUDA, OOM. */
 int greem_pm_force(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, double L, int n_pm,
                    double r_cut, int assign, float *acc_pm);
 

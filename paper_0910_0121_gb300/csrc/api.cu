@@ -10,8 +10,12 @@
 #include <new>
 #include <vector>
 
+#include <cufft.h>
+
 #include "common.cuh"
 #include "greem.h"
+
+#include "pm.cuh"
 
 namespace greem {
 thread_local long long g_launches = 0;
@@ -69,6 +73,13 @@ struct greem_ctx {
     int last_nbox = 0;
     bool have_tree = false, have_lists = false, have_index = false;
     greem_stats stats;
+
+    // PM
+    PmPlan pm;
+    DBuf<float> pm_grid, pm_table;
+    DBuf<cufftComplex> pm_spec, pm_tmp;
+    int pm_tab_n = 0, pm_tab_scheme = -1;
+    double pm_tab_L = 0, pm_tab_rc = 0;
 
     // graph
     cudaGraphExec_t exec = nullptr;
@@ -188,7 +199,43 @@ static int check_common(const greem_params &p)
     if (p.list_chunk != 0 && (p.list_chunk < 64 || p.list_chunk > 2048 || (p.list_chunk & (p.list_chunk - 1))))
         return GREEM_ERR_INVALID_ARG;
     if (p.block_shape < 0 || p.block_shape > 16) return GREEM_ERR_INVALID_ARG;
+    if (p.flags & GREEM_FLAG_ADD_PM) {
+        if (p.precision != GREEM_F32_REL || p.n_pm < 8 || p.n_pm > 1024) return GREEM_ERR_INVALID_ARG;
+        if (p.assign != GREEM_ASSIGN_CIC && p.assign != GREEM_ASSIGN_TSC) return GREEM_ERR_INVALID_ARG;
+    }
     return GREEM_OK;
+}
+
+// ------------------------------------------------------------------ PM buffers
+static int pm_prepare(greem_ctx *c, int n, double L, double r_cut, int scheme)
+{
+    int rc;
+    const size_t cells = (size_t)n * n * n, half = (size_t)n * n * (n / 2 + 1), h = (size_t)(n / 2 + 1);
+    if ((rc = ensure(c, c->pm_grid, cells)) || (rc = ensure(c, c->pm_spec, half)) ||
+        (rc = ensure(c, c->pm_tmp, half)) || (rc = ensure(c, c->pm_table, h * h * h)))
+        return rc;
+    if (!(c->pm.have && c->pm.n == n)) {
+        if (c->capturing) return GREEM_ERR_CAPACITY;
+        if (pm_plan(c->pm, n, c->stream)) return GREEM_ERR_CUDA;
+    } else {
+        pm_plan(c->pm, n, c->stream);
+    }
+    if (c->pm_tab_n != n || c->pm_tab_L != L || c->pm_tab_rc != r_cut || c->pm_tab_scheme != scheme) {
+        if (c->capturing) return GREEM_ERR_CAPACITY;
+        launch_pm_table(n, L, r_cut, scheme, c->pm_table.p, c->stream, c->nsm);
+        c->pm_tab_n = n;
+        c->pm_tab_L = L;
+        c->pm_tab_rc = r_cut;
+        c->pm_tab_scheme = scheme;
+    }
+    return GREEM_OK;
+}
+
+static int pow2_exponent(double L)
+{
+    int e = 0;
+    const double mfrac = std::frexp(L, &e);
+    return (mfrac == 0.5 && e - 1 > -900 && e - 1 < 900) ? e - 1 : kNotPow2;
 }
 
 // ------------------------------------------------------------------ pipeline
@@ -205,6 +252,9 @@ struct RunCfg {
     bool timing;
     int chunk;
     int warps;
+    bool add_pm;
+    int n_pm;
+    int assign;
 };
 
 static int host_boxes(greem_ctx *c, int nbox)
@@ -376,6 +426,15 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
         fa.warps = r.warps;
         if (r.precision == GREEM_F64) launch_force_f64(fa, s, nsm);
         else launch_force_f32(fa, s, nsm, r.soft);
+        if (r.add_pm) {
+            const BoxPar &b0 = c->bps_host[0];
+            if ((rc = pm_prepare(c, r.n_pm, b0.L, 2.0 * b0.eta, r.assign))) return rc;
+            // input order: Morton-sorted particles of dense halos make consecutive lanes hit the
+            // same cells and serialise the assignment atomics
+            if (run_pm(c->pm, r.pos, nullptr, nullptr, nullptr, r.mass, nullptr, N, b0.L, r.n_pm, r.assign, b0.pow2_e,
+                       c->pm_table.p, c->pm_grid.p, c->pm_spec.p, c->pm_tmp.p, (float *)r.acc, 1, s, nsm))
+                return GREEM_ERR_CUDA;
+        }
         ev_record(c, r, ev, 6);
     }
     cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
@@ -496,6 +555,9 @@ static RunCfg make_cfg(const greem_params &p, const double *pos, const float *ma
     r.timing = (p.flags & GREEM_FLAG_STAGE_TIMES) != 0;
     r.chunk = p.list_chunk ? p.list_chunk : 256;
     r.warps = p.block_shape ? p.block_shape : 8;
+    r.add_pm = (p.flags & GREEM_FLAG_ADD_PM) != 0;
+    r.n_pm = p.n_pm;
+    r.assign = p.assign;
     return r;
 }
 
@@ -543,6 +605,8 @@ void greem_destroy(greem_ctx *c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     if (c->exec) cudaGraphExecDestroy(c->exec);
+    pm_plan_destroy(c->pm);
+    release(c->pm_grid); release(c->pm_table); release(c->pm_spec); release(c->pm_tmp);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     release(c->k0); release(c->k1); release(c->v0); release(c->v1); release(c->hist); release(c->scratch);
     release(c->xs); release(c->ys); release(c->zs); release(c->ms);
@@ -628,9 +692,22 @@ int greem_short_force_batched(greem_ctx *c, int nbox, const int64_t *offsets, co
     return run(c, r);
 }
 
-int greem_pm_force(greem_ctx *, const double *, const float *, int64_t, double, int, double, int, float *)
+int greem_pm_force(greem_ctx *c, const double *pos, const float *mass, int64_t N, double L, int n_pm, double r_cut,
+                   int assign, float *acc_pm)
 {
-    return GREEM_ERR_NOT_IMPLEMENTED;
+    if (!c || !pos || !mass || !acc_pm || N < 1 || N >= (int64_t)0x7FFFFFF0) return GREEM_ERR_INVALID_ARG;
+    if (!(L > 0) || !std::isfinite(L) || !(r_cut > 0) || !(r_cut < 0.5 * L)) return GREEM_ERR_INVALID_ARG;
+    if (n_pm < 8 || n_pm > 1024 || (assign != GREEM_ASSIGN_CIC && assign != GREEM_ASSIGN_TSC))
+        return GREEM_ERR_INVALID_ARG;
+    int rc = pm_prepare(c, n_pm, L, r_cut, assign);
+    if (rc) return rc;
+    greem::g_launches = 0;
+    if (run_pm(c->pm, pos, nullptr, nullptr, nullptr, mass, nullptr, (uint32_t)N, L, n_pm, assign, pow2_exponent(L),
+               c->pm_table.p, c->pm_grid.p, c->pm_spec.p, c->pm_tmp.p, acc_pm, 0, c->stream, c->nsm))
+        return GREEM_ERR_CUDA;
+    if (!cuda_ok(cudaGetLastError()) || !cuda_ok(cudaStreamSynchronize(c->stream))) return GREEM_ERR_CUDA;
+    c->stats.kernel_launches = greem::g_launches;
+    return GREEM_OK;
 }
 
 int greem_graph_capture(greem_ctx *c, const double *pos, const float *mass, int64_t N, const greem_params *p, void *acc)

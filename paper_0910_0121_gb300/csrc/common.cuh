@@ -237,4 +237,7 @@ void launch_pair_setup(const double *xg, const double *xi, const double *xj, con
                        uint32_t *llen, uint32_t *lraw, uint32_t *perm, uint32_t *n_groups, cudaStream_t s);
 double peak_tflops(int which, int nsm, cudaStream_t s, int *err);
 
+// PM (pm.cu)
+void launch_pm_table(int n, double L, double r_cut, int scheme, float *table, cudaStream_t s, int nsm);
+
 }  // namespace greem

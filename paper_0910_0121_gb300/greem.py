@@ -27,6 +27,9 @@ F32_REL = 0
 F64 = 1
 FLAG_INDEX_LISTS = 1
 FLAG_STAGE_TIMES = 2
+FLAG_ADD_PM = 4
+ASSIGN_CIC = 0
+ASSIGN_TSC = 1
 
 DUMP_KEYS, DUMP_PERM, DUMP_NODES, DUMP_MOMENTS, DUMP_GROUPS, DUMP_LIST_OFFSETS, DUMP_LISTS = range(7)
 
@@ -42,7 +45,7 @@ class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("r_cut", ctypes.c_double), ("theta", ctypes.c_double),
                 ("eps", ctypes.c_double), ("n_crit", ctypes.c_int), ("n_leaf", ctypes.c_int),
                 ("precision", ctypes.c_int), ("list_chunk", ctypes.c_int), ("block_shape", ctypes.c_int),
-                ("flags", ctypes.c_uint)]
+                ("flags", ctypes.c_uint), ("n_pm", ctypes.c_int), ("assign", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -124,12 +127,13 @@ def _dev(t, dtype, shape=None, name="tensor"):
 
 
 def params(L=1.0, r_cut=3.0 / 32, theta=0.5, n_crit=64, n_leaf=10, eps=0.0, precision=F32_REL, list_chunk=0,
-           block_shape=0, flags=0) -> Params:
+           block_shape=0, flags=0, n_pm=0, assign=ASSIGN_TSC) -> Params:
     p = Params()
     _lib().greem_params_default(ctypes.byref(p))
     p.L, p.r_cut, p.theta, p.eps = float(L), float(r_cut), float(theta), float(eps)
     p.n_crit, p.n_leaf, p.precision = int(n_crit), int(n_leaf), int(precision)
     p.list_chunk, p.block_shape, p.flags = int(list_chunk), int(block_shape), int(flags)
+    p.n_pm, p.assign = int(n_pm), int(assign)
     return p
 
 
@@ -188,6 +192,17 @@ class Context:
                                                 _dev(pos, torch.float64, (N, 3), "pos"),
                                                 _dev(mass, torch.float32, (N,), "mass"), arr,
                                                 _dev(acc, dt, (N, 3), "acc")), "greem_short_force_batched")
+        return acc
+
+    def pm_force(self, pos, mass, L, n_pm, r_cut, assign=ASSIGN_TSC, acc=None):
+        """greem_pm_force: the PM (long-range) acceleration, float32 [N,3], input order."""
+        import torch
+        N = pos.shape[0]
+        if acc is None:
+            acc = torch.empty((N, 3), dtype=torch.float32, device=pos.device)
+        _check(_lib().greem_pm_force(self._h, _dev(pos, torch.float64, (N, 3), "pos"),
+                                     _dev(mass, torch.float32, (N,), "mass"), N, float(L), int(n_pm), float(r_cut),
+                                     int(assign), _dev(acc, torch.float32, (N, 3), "acc")), "greem_pm_force")
         return acc
 
     def graph_capture(self, pos, mass, p: Params, acc):

@@ -277,7 +277,7 @@ def test_invalid_inputs_are_errors(ctx):
             gpu_force(ctx, pos, mass, prm)
     # the context is still usable afterwards
     gpu_force(ctx, pos, mass, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=8))
-    assert greem.lib().greem_pm_force(ctx._h, None, None, 0, 1.0, 32, 0.1, 0, None) == greem.ERR_NOT_IMPLEMENTED
+    assert greem.lib().greem_pm_force(ctx._h, None, None, 0, 1.0, 32, 0.1, 0, None) == greem.ERR_INVALID_ARG
 
 
 # --------------------------------------------------------------------------- pairwise error (Sec. 3.1.1)
