@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-crit", type=int, default=0, help="skip autotuning and use this n_crit")
     ap.add_argument("--no-extras", action="store_true", help="skip the graph, theta-scan and batched lines")
+    ap.add_argument("--config5", action="store_true",
+                    help="time the 512^3 full TreePM step (PP + TSC PM on 512^3) in one CUDA graph instead")
     return ap.parse_args()
 
 
@@ -422,9 +424,63 @@ def gpu_arm(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def config5_arm(args):
+    """512^3 Zel'dovich (rms 1 spacing) + 20000 NFW halos, theta = 0.5, r_cut = 3/512: the
+    whole TreePM force (short-range tree force plus PM with TSC on 512^3) as one graph."""
+    import torch
+    from paper_0910_0121_gb300 import build as _build
+    from paper_0910_0121_gb300 import greem, synth
+
+    _build.build()
+    t0 = time.time()
+    pos, mass, prm = synth.config_zel512()
+    gen_s = time.time() - t0
+    N = len(pos)
+    P = torch.from_numpy(pos).cuda()
+    M = torch.from_numpy(mass).cuda()
+    del pos
+    acc = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = greem.Context(stream)
+    nc = args.n_crit or 192
+    p = greem.params(L=1.0, r_cut=prm["r_cut"], theta=0.5, n_crit=nc, flags=greem.FLAG_ADD_PM, n_pm=512,
+                     assign=greem.ASSIGN_TSC)
+    ctx.graph_capture(P, M, p, acc)
+    st = ctx.stats()
+    for _ in range(max(3, args.warmup)):
+        ctx.graph_launch()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            rc = ctx.graph_launch()
+            if rc != greem.OK:
+                raise greem.GreemError(rc, "greem_graph_launch")
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    s = ctx.stats()
+    line = {"metric": "full TreePM step particles/s (short-range tree force + PM)", "value": N / (ms * 1e-3),
+            "unit": "particles/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "zeldovich512+20000nfw_theta0.5_pm512_tsc", "N": N, "r_cut": prm["r_cut"],
+                       "theta": 0.5, "n_crit": nc, "n_pm": 512, "assign": "TSC", "graph": True},
+            "N_int": s["n_interactions"] / N, "n_groups": s["n_groups"], "n_nodes": s["n_nodes"],
+            "list_capacity_entries": s["list_capacity"], "kernel_launches_per_step": st["kernel_launches"],
+            "device_mem_gb": torch.cuda.mem_get_info()[1] / 1e9 - torch.cuda.mem_get_info()[0] / 1e9,
+            "generation_s": gen_s, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.config5:
+        config5_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args, rank, world)
     else:

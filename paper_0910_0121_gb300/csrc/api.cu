@@ -501,12 +501,13 @@ static void grow_caps(greem_ctx *c)
 static int run(greem_ctx *c, RunCfg r)
 {
     c->have_tree = c->have_lists = c->have_index = false;
-    if (c->node_cap < (size_t)r.N + 4096u * r.nbox) c->node_cap = (size_t)(r.N * 1.25) + 4096u * r.nbox;
+    // first guesses; an overflow grows them and the call is retried
+    if (c->node_cap < (size_t)(r.N * 0.5) + 4096u * r.nbox) c->node_cap = (size_t)(r.N * 0.75) + 4096u * r.nbox;
     uint32_t pg = choose_page(r.N, c->nsm);
     if (pg > c->page) c->page = pg;
     if (r.lists_force) {
         const size_t warps = (size_t)c->nsm * kListBlocksPerSM * kListWarps;
-        c->list_cap = std::max<size_t>(c->list_cap, (size_t)r.N * 48 + warps * c->page);
+        c->list_cap = std::max<size_t>(c->list_cap, (size_t)r.N * 32 + warps * c->page);
     }
     cudaEvent_t ev[7] = {};
     if (r.timing)

@@ -81,8 +81,11 @@ enum : unsigned {
 
 // Launch shape of the list builder (warps per block, blocks per SM): every warp may
 // hold one partly used page of the list pool.
+#ifndef GREEM_LIST_BLOCKS
+#define GREEM_LIST_BLOCKS 6
+#endif
 constexpr int kListWarps = 8;
-constexpr int kListBlocksPerSM = 4;
+constexpr int kListBlocksPerSM = GREEM_LIST_BLOCKS;
 
 // Kernel launches made by the current host thread (reported in greem_stats).
 extern thread_local long long g_launches;

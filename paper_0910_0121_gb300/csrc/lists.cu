@@ -189,7 +189,7 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const BoxPar 
     return cnt;
 }
 
-__global__ void __launch_bounds__(kListWarps * 32) k_lists(ListArgs a)
+__global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(ListArgs a)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
