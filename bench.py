@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the graph, theta-scan and batched lines")
     ap.add_argument("--config5", action="store_true",
                     help="time the 512^3 full TreePM step (PP + TSC PM on 512^3) in one CUDA graph instead")
+    ap.add_argument("--profile-case", choices=["nfw128", "zel256"], default=None,
+                    help="run --steps short-force calls on this workload (n_crit from --n-crit, else 128) "
+                         "and print the stats; no timing (the small case for profiler captures)")
     return ap.parse_args()
 
 
@@ -475,9 +478,34 @@ def config5_arm(args):
     ctx.close()
 
 
+def profile_case(args):
+    """A bare call sequence for profiler captures: the workload's short-range force,
+    --steps times, with nothing else on the device."""
+    import torch
+    from paper_0910_0121_gb300 import build as _build
+    from paper_0910_0121_gb300 import greem, synth
+
+    _build.build()
+    pos, mass, prm = synth.config_nfw128() if args.profile_case == "nfw128" else synth.config_zel256()
+    P = torch.from_numpy(pos).cuda()
+    M = torch.from_numpy(mass).cuda()
+    ctx = greem.Context()
+    acc = torch.empty((len(pos), 3), dtype=torch.float32, device="cuda")
+    p = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=args.n_crit or 128,
+                     n_leaf=prm["n_leaf"])
+    for _ in range(args.steps):
+        ctx.short_force(P, M, p, acc)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "n_crit": p.n_crit, **ctx.stats()}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.config5:
         config5_arm(args)
         return

@@ -36,7 +36,11 @@
  *     (2i+1)*2^(21-k) and half side 2^(21-k); the period is 2^22.
  *   - node-to-group offset wrapped into [-2^21, 2^21).
  *   - prune iff (double)S_gap * (u*u) > r_cut*r_cut, S_gap = sum of squared per-axis
- *     box-box gaps (exact integers).
+ *     gaps (exact integers) between the node's cell and the group's particle box: the
+ *     smallest box of finest-level (level 21) cells that holds every particle of the
+ *     group.  A particle of an opened leaf is tested the same way with its own finest
+ *     cell and is left out when the test holds.  Either way the left-out mass lies
+ *     farther than r_cut from every particle of the group, where Eq. 2 is exactly 0.
  *   - accept iff level >= l_min and (double)(l*l) < (theta*theta) * (double)S_d,
  *     l = node side, S_d = squared distance from node centre to the nearest point of
  *     the group cell (both in u).  Prune is tested first.
@@ -418,9 +422,25 @@ void or_tree_get_groups(const or_tree *t, int64_t *out)
 /* Step 5: interaction list of one group, DFS preorder over the tree. */
 typedef struct {
     or_tree *t;
-    int64_t cg[3], hg; /* group centre and half side, units of u */
+    int64_t cg[3], hg; /* group cell centre and half side, units of u */
+    int64_t cb[3], hb[3]; /* centre and half sides of the group's particle box, units of u */
     double uu, rc2, th2;
 } walk_t;
+
+/* r_cut test of a box (centre d relative to the group cell centre, already the image
+ * to use; half side h, all in u) against the group's particle box. */
+static int beyond_rcut(const walk_t *W, const int64_t d[3], int64_t h)
+{
+    int64_t sgap = 0;
+    for (int c = 0; c < 3; c++) {
+        int64_t e = d[c] - (W->cb[c] - W->cg[c]);
+        if (e < 0) e = -e;
+        int64_t gap = e - h - W->hb[c];
+        if (gap < 0) gap = 0;
+        sgap += gap * gap;
+    }
+    return (double)sgap * W->uu > W->rc2;
+}
 
 static int push_entry(or_tree *t, int kind, int64_t idx, const int sh[3])
 {
@@ -451,28 +471,32 @@ static int walk_rec(walk_t *W, int64_t n)
     int64_t hn = (int64_t)1 << (21 - k);
     int64_t cn[3] = {(2 * t->ix[n] + 1) * hn, (2 * t->iy[n] + 1) * hn, (2 * t->iz[n] + 1) * hn};
     const int64_t P = (int64_t)1 << 22, H = (int64_t)1 << 21;
-    int64_t sgap = 0, sd = 0;
+    int64_t sd = 0, dn[3];
     int sh[3];
     for (int c = 0; c < 3; c++) {
         int64_t d = cn[c] - W->cg[c];
         sh[c] = 0;
         if (d >= H) { d -= P; sh[c] = -1; }
         else if (d < -H) { d += P; sh[c] = 1; }
+        dn[c] = d;
         int64_t ad = d < 0 ? -d : d;
-        int64_t gap = ad - hn - W->hg;
-        if (gap < 0) gap = 0;
         int64_t e = ad - W->hg;
         if (e < 0) e = 0;
-        sgap += gap * gap;
         sd += e * e;
     }
-    /* r_cut pruning: the whole node lies farther than r_cut from the group cell */
-    if ((double)sgap * W->uu > W->rc2) return 0;
-    /* opening criterion (Barnes-Hut on cell side) */
+    /* r_cut pruning: the whole node lies farther than r_cut from the group's particles */
+    if (beyond_rcut(W, dn, hn)) return 0;
+    /* opening criterion (Barnes-Hut on cell side, distance to the group cell) */
     int64_t l = 2 * hn;
     if (k >= t->lmin && (double)(l * l) < W->th2 * (double)sd) return push_entry(t, 1, n, sh);
     if (t->leaf[n]) {
         for (int64_t j = t->beg[n]; j < t->end[n]; j++) {
+            /* the particle's finest cell, in the node's image */
+            int64_t dj[3] = {2 * or_cell_index(t->x[j], t->L) + 1 - W->cg[0],
+                             2 * or_cell_index(t->y[j], t->L) + 1 - W->cg[1],
+                             2 * or_cell_index(t->z[j], t->L) + 1 - W->cg[2]};
+            for (int c = 0; c < 3; c++) dj[c] += (int64_t)sh[c] * P;
+            if (beyond_rcut(W, dj, 1)) continue;
             int rc = push_entry(t, 0, j, sh);
             if (rc) return rc;
         }
@@ -511,6 +535,20 @@ int or_lists_build(or_tree *t, double theta, const int64_t *gsel, int64_t ns)
         W.cg[0] = (2 * t->ix[n] + 1) * W.hg;
         W.cg[1] = (2 * t->iy[n] + 1) * W.hg;
         W.cg[2] = (2 * t->iz[n] + 1) * W.hg;
+        {
+            const double *xs[3] = {t->x, t->y, t->z};
+            for (int c = 0; c < 3; c++) {
+                int64_t lo = 2097151, hi = 0;
+                for (int64_t j = t->beg[n]; j < t->end[n]; j++) {
+                    int64_t q = or_cell_index(xs[c][j], t->L);
+                    if (q < lo) lo = q;
+                    if (q > hi) hi = q;
+                }
+                /* finest cells lo..hi span [2 lo, 2 hi + 2] in u */
+                W.cb[c] = lo + hi + 1;
+                W.hb[c] = hi - lo + 1;
+            }
+        }
         t->lgrp[s] = g;
         t->loff[s] = t->nent;
         int rc = walk_rec(&W, 0);

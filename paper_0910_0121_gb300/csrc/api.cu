@@ -47,6 +47,8 @@ struct greem_ctx {
     DBuf<Dbl4> raw, mom64;
     DBuf<float4> noff, poff, irel;
     DBuf<Group> groups;
+    DBuf<unsigned long long> pcell;
+    DBuf<int4> gbox;
     // S5-S6
     DBuf<float4> flist;
     DBuf<unsigned long long> ilist, loff;
@@ -304,6 +306,7 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
     ENS(own, N);
     ENS(base, N + 1);
     ENS(poff, N);
+    ENS(pcell, N);
     ENS(irel, N);
     const size_t nc = c->node_cap;
     ENS(nodes, nc);
@@ -315,6 +318,7 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
     ENS(gflag, nc);
     ENS(gidx, nc + 1);
     ENS(groups, nc);
+    ENS(gbox, nc * 2);
     ENS(kids, nc * 8);
     ENS(lvl, 96);
     ENS(bps, (size_t)r.nbox);
@@ -369,7 +373,8 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     launch_tree_links(c->nodes.p, n_nodes, ncap, c->nchild.p, c->kids.p, s, nsm);
     launch_moments(c->nodes.p, n_nodes, ncap, c->kids.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p, c->lvl.p,
                    c->ctr.p, s, nsm);
-    launch_leaf_offsets(ks, c->K8.p, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->poff.p, s);
+    launch_leaf_offsets(ks, c->K8.p, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->poff.p,
+                        c->pcell.p, s);
     launch_node_finish(c->nodes.p, n_nodes, ncap, c->raw.p, c->box_off.p, nbox, c->bps.p, c->mom64.p, c->noff.p, s,
                        nsm);
     ev_record(c, r, ev, 3);
@@ -377,6 +382,7 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     scan_u32(c->gflag.p, c->gidx.p, ncap, c->scratch.p, s);
     const uint32_t *n_groups = c->gidx.p + ncap;
     launch_group_fill(c->nodes.p, n_nodes, ncap, c->gflag.p, c->gidx.p, c->box_off.p, nbox, c->groups.p, s, nsm);
+    launch_group_box(c->groups.p, n_groups, c->pcell.p, c->gbox.p, s, nsm);
     launch_record_counts(n_nodes, n_groups, c->st.p, ncap, s);
     ev_record(c, r, ev, 4);
     if (r.lists_force) {
@@ -391,6 +397,8 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
         la.stack_cap = c->stack_cap;
         la.poff = c->poff.p;
         la.noff = c->noff.p;
+        la.pcell = c->pcell.p;
+        la.gbox = c->gbox.p;
         la.flist = c->flist.p;
         la.ilist = r.index_lists ? c->ilist.p : nullptr;
         la.irel = c->irel.p;
@@ -613,7 +621,8 @@ void greem_destroy(greem_ctx *c)
     release(c->xs); release(c->ys); release(c->zs); release(c->ms);
     release(c->d8); release(c->K8); release(c->nchild); release(c->own); release(c->base); release(c->ctr);
     release(c->gflag); release(c->gidx); release(c->nodes); release(c->raw); release(c->mom64); release(c->noff);
-    release(c->poff); release(c->irel); release(c->groups); release(c->flist); release(c->ilist); release(c->loff);
+    release(c->poff); release(c->pcell); release(c->irel); release(c->groups); release(c->gbox);
+    release(c->flist); release(c->ilist); release(c->loff);
     release(c->llen); release(c->lraw); release(c->kids); release(c->stack); release(c->order); release(c->bins);
     release(c->lvl); release(c->bps); release(c->box_off); release(c->small); release(c->st);
     if (c->st_host) cudaFreeHost(c->st_host);

@@ -82,7 +82,7 @@ enum : unsigned {
 // Launch shape of the list builder (warps per block, blocks per SM): every warp may
 // hold one partly used page of the list pool.
 #ifndef GREEM_LIST_BLOCKS
-#define GREEM_LIST_BLOCKS 6
+#define GREEM_LIST_BLOCKS 4
 #endif
 constexpr int kListWarps = 8;
 constexpr int kListBlocksPerSM = GREEM_LIST_BLOCKS;
@@ -173,7 +173,7 @@ void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_ca
                     uint32_t *inodes, cudaStream_t s, int nsm);
 void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
                          const BoxPar *bps, const double *xs, const double *ys, const double *zs, const float *ms,
-                         float4 *poff, cudaStream_t s);
+                         float4 *poff, unsigned long long *pcell, cudaStream_t s);
 void launch_node_finish(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const Dbl4 *raw,
                         const uint32_t *box_off, int nbox, const BoxPar *bps, Dbl4 *mom64, float4 *noff,
                         cudaStream_t s, int nsm);
@@ -182,6 +182,8 @@ void launch_group_flags(const Node *nodes, const uint32_t *n_nodes, uint32_t nod
 void launch_group_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *flag,
                        const uint32_t *gidx, const uint32_t *box_off, int nbox, Group *groups, cudaStream_t s,
                        int nsm);
+void launch_group_box(const Group *groups, const uint32_t *n_groups, const unsigned long long *pcell, int4 *gbox,
+                      cudaStream_t s, int nsm);
 void launch_record_counts(const uint32_t *n_nodes, const uint32_t *n_groups, DevStatus *st, uint32_t node_cap,
                           cudaStream_t s);
 
@@ -197,6 +199,8 @@ struct ListArgs {
     uint32_t stack_cap;        // entries per warp stack
     const float4 *poff;        // per sorted particle: offset from its leaf centre (eta units), mass
     const float4 *noff;        // per node: COM offset from its cell centre (eta units), mass
+    const unsigned long long *pcell;  // per sorted particle: finest cell, x | y << 21 | z << 42
+    const int4 *gbox;          // per group: particle box centre minus cell centre, then half sides (u)
     float4 *flist;             // list pool, FP32 relative entries
     unsigned long long *ilist; // list pool, index entries (may be null)
     float4 *irel;              // per sorted particle: its own relative position in its group's frame

@@ -3,13 +3,15 @@
 // One warp per group walks its box's tree from the root with a per-warp stack of node
 // indices: each step pops up to 32 nodes, one per lane, and each lane decides, in
 // this order:
-//   prune  -- the node's cell is farther than r_cut from the group's cell (periodic
+//   prune  -- the node's cell is farther than r_cut from the group's particle box (the
+//             box of finest-level cells that holds the group's particles; periodic
 //             box-to-box distance), so none of its particles can act (Eq. 2 is 0);
 //   accept -- level >= l_min and the opening criterion holds: cell side l and the
 //             distance d from the node's cell centre to the nearest point of the group
 //             cell satisfy l < theta d; the node enters the list as one particle at its
 //             centre of mass (Sec. 3.1.2);
-//   leaf   -- an opened leaf puts all of its particles into the list;
+//   leaf   -- an opened leaf puts its particles into the list, each but those whose
+//             finest cell passes the prune test (the same integer test at level 21);
 //   open   -- the node's children (child table, up to 8) are pushed.
 // Every popped node is one the recursive walk visits, so no lane tests a node inside a
 // pruned or accepted subtree.  The entries are the same set as the recursive walk's;
@@ -63,8 +65,9 @@ __device__ __forceinline__ Node load_node(const Node *p)
 
 // Walks one group's list; writes entries [pos0, pos0+total) clipped at lim; returns
 // total.  stk is this warp's stack (a.stack_cap entries); an overflow sets the status.
-__device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const BoxPar &bp, uint32_t root,
-                               uint32_t *__restrict__ stk, unsigned long long pos0, unsigned long long lim, int lane)
+__device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb, const int4 th, const BoxPar &bp,
+                               uint32_t root, uint32_t *__restrict__ stk, unsigned long long pos0,
+                               unsigned long long lim, int lane)
 {
     const unsigned FULL = 0xffffffffu;
     const uint32_t gend = gr.begin + gr.count;
@@ -97,11 +100,18 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const BoxPar 
         const int dy = wrap_delta(2 * (int)nd.iy + h - gr.cy, sy);
         const int dz = wrap_delta(2 * (int)nd.iz + h - gr.cz, sz);
         const int ax = abs(dx), ay = abs(dy), az = abs(dz);
-        const int gx = max(0, ax - h - gr.hg), gy = max(0, ay - h - gr.hg), gz = max(0, az - h - gr.hg);
+        const int gx = max(0, abs(dx - tb.x) - h - th.x), gy = max(0, abs(dy - tb.y) - h - th.y),
+                  gz = max(0, abs(dz - tb.z) - h - th.z);
         const int ex = max(0, ax - gr.hg), ey = max(0, ay - gr.hg), ez = max(0, az - gr.hg);
         const long long Sg = (long long)gx * gx + (long long)gy * gy + (long long)gz * gz;
         const long long Sd = (long long)ex * ex + (long long)ey * ey + (long long)ez * ez;
         const bool prune = Sg > Tp;
+        // an opened leaf whose whole cell lies within r_cut of the particle box keeps every
+        // particle (each particle's finest cell is inside the leaf's cell), so its particles
+        // skip the per-particle test
+        const int fx = max(0, abs(dx - tb.x) + h - th.x), fy = max(0, abs(dy - tb.y) + h - th.y),
+                  fz = max(0, abs(dz - tb.z) + h - th.z);
+        const bool test_each = (long long)fx * fx + (long long)fy * fy + (long long)fz * fz > Tp;
         const bool accept = !prune && k >= lmin && Sd > bp.A[k];
         const bool open = valid && !prune && !accept && !leaf;
         uint32_t ne = (valid && !prune) ? (accept ? 1u : (leaf ? nd.end - nd.begin : 0u)) : 0u;
@@ -146,7 +156,7 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const BoxPar 
         if (tot) {
             const float bx = __fmul_rn((float)dx, kf), by = __fmul_rn((float)dy, kf), bz = __fmul_rn((float)dz, kf);
             const uint32_t src = accept ? (m | 0x80000000u) : nd.begin;
-            const unsigned shc = shift_code(sx, sy, sz);
+            const unsigned shc = shift_code(sx, sy, sz) | ((test_each && !accept) ? 64u : 0u);
             for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
                 const uint32_t t = t0 + lane;
                 int s = 0;
@@ -160,10 +170,13 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const BoxPar 
                 const float bx_s = __shfl_sync(FULL, bx, s), by_s = __shfl_sync(FULL, by, s),
                             bz_s = __shfl_sync(FULL, bz, s);
                 const unsigned sh_s = __shfl_sync(FULL, shc, s);
+                bool keep = false;
+                float4 e;
+                unsigned long long ie = 0;
                 if (t < tot) {
                     float4 v;
-                    unsigned long long ie;
                     uint32_t j = kNone;
+                    keep = true;
                     if (src_s & 0x80000000u) {
                         const uint32_t nn = src_s & 0x7fffffffu;
                         v = __ldg(a.noff + nn);
@@ -173,17 +186,33 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const BoxPar 
                         v = __ldg(a.poff + j);
                         ie = (unsigned long long)j;
                     }
-                    const float4 e = make_float4(__fadd_rn(bx_s, v.x), __fadd_rn(by_s, v.y), __fadd_rn(bz_s, v.z), v.w);
-                    const unsigned long long p = pos0 + cnt + t;
-                    if (p < lim) {
-                        a.flist[p] = e;
-                        if (a.ilist) a.ilist[p] = ie | ((unsigned long long)sh_s << 33);
+                    if (sh_s & 64u) {
+                        // the particle's finest cell, in its leaf's image, against the particle box
+                        const unsigned long long c = __ldg(a.pcell + j);
+                        const int px = 2 * (int)((uint32_t)c & 0x1fffffu) + 1 - gr.cx - tb.x +
+                                       ((sh_s & 1u) ? kPeriod : ((sh_s & 2u) ? -kPeriod : 0));
+                        const int py = 2 * (int)((uint32_t)(c >> 21) & 0x1fffffu) + 1 - gr.cy - tb.y +
+                                       ((sh_s & 4u) ? kPeriod : ((sh_s & 8u) ? -kPeriod : 0));
+                        const int pz = 2 * (int)(uint32_t)(c >> 42) + 1 - gr.cz - tb.z +
+                                       ((sh_s & 16u) ? kPeriod : ((sh_s & 32u) ? -kPeriod : 0));
+                        const int qx = max(0, abs(px) - 1 - th.x), qy = max(0, abs(py) - 1 - th.y),
+                                  qz = max(0, abs(pz) - 1 - th.z);
+                        keep = (long long)qx * qx + (long long)qy * qy + (long long)qz * qz <= Tp;
                     }
+                    e = make_float4(__fadd_rn(bx_s, v.x), __fadd_rn(by_s, v.y), __fadd_rn(bz_s, v.z), v.w);
                     if (j >= gr.begin && j < gend) a.irel[j] = e;
                 }
+                const unsigned kb = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const unsigned long long p = pos0 + cnt + __popc(kb & ((1u << lane) - 1u));
+                    if (p < lim) {
+                        a.flist[p] = e;
+                        if (a.ilist) a.ilist[p] = ie | ((unsigned long long)(sh_s & 63u) << 33);
+                    }
+                }
+                cnt += __popc(kb);
             }
         }
-        cnt += tot;
     }
     __syncwarp();
     return cnt;
@@ -205,9 +234,10 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
         if (gi >= G) break;
         const uint32_t g = (uint32_t)gi;
         const Group gr = a.groups[g];
+        const int4 tb = a.gbox[2 * (size_t)g], th = a.gbox[2 * (size_t)g + 1];
         const BoxPar &bp = a.bps[gr.box];
         const uint32_t root = a.base[bp.p_begin];
-        const uint32_t len = walk_group(a, gr, bp, root, stk, page_cur, page_end, lane);
+        const uint32_t len = walk_group(a, gr, tb, th, bp, root, stk, page_cur, page_end, lane);
         const uint32_t padded = (len + 7u) & ~7u;
         if (lane == 0) atomicAdd(&a.st->sum_padded, (unsigned long long)padded);
         if (exhausted) {
@@ -237,7 +267,7 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
             }
             page_cur = first * a.page;
             page_end = (first + np) * a.page;
-            walk_group(a, gr, bp, root, stk, page_cur, page_end, lane);
+            walk_group(a, gr, tb, th, bp, root, stk, page_cur, page_end, lane);
         }
         for (uint32_t t = len + lane; t < padded; t += 32) {
             a.flist[page_cur + t] = make_float4(16.f, 16.f, 16.f, 0.f);

@@ -305,7 +305,8 @@ __global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict
                                                       uint32_t N, const uint32_t *__restrict__ box_off, int nbox,
                                                       const BoxPar *__restrict__ bps, const double *__restrict__ xs,
                                                       const double *__restrict__ ys, const double *__restrict__ zs,
-                                                      const float *__restrict__ ms, float4 *__restrict__ poff)
+                                                      const float *__restrict__ ms, float4 *__restrict__ poff,
+                                                      unsigned long long *__restrict__ pcell)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -314,8 +315,9 @@ __global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict
     const uint32_t h = 1u << (kMaxLevel - k);
     const uint32_t mask = ~(h - 1u);
     const uint64_t key = keys[i];
-    const uint32_t cx = 2u * (compact3(key >> 2) & mask) + h, cy = 2u * (compact3(key >> 1) & mask) + h,
-                   cz = 2u * (compact3(key) & mask) + h;
+    const uint32_t fx = compact3(key >> 2), fy = compact3(key >> 1), fz = compact3(key);
+    pcell[i] = (unsigned long long)fx | ((unsigned long long)fy << 21) | ((unsigned long long)fz << 42);
+    const uint32_t cx = 2u * (fx & mask) + h, cy = 2u * (fy & mask) + h, cz = 2u * (fz & mask) + h;
     if (bp.pow2_e != kNotPow2) {
         // integer offsets in units of L/2^52 (centre = c_u * 2^30), one rounding to FP32
         const int e = bp.pow2_e;
@@ -333,9 +335,9 @@ __global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict
 
 void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
                          const BoxPar *bps, const double *xs, const double *ys, const double *zs, const float *ms,
-                         float4 *poff, cudaStream_t s)
+                         float4 *poff, unsigned long long *pcell, cudaStream_t s)
 {
-    k_leaf_offsets<<<(N + 255) / 256, 256, 0, s>>>(keys, K8, N, box_off, nbox, bps, xs, ys, zs, ms, poff);
+    k_leaf_offsets<<<(N + 255) / 256, 256, 0, s>>>(keys, K8, N, box_off, nbox, bps, xs, ys, zs, ms, poff, pcell);
     g_launches++;
 }
 
@@ -451,6 +453,53 @@ void launch_group_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t node
                        const uint32_t *gidx, const uint32_t *box_off, int nbox, Group *groups, cudaStream_t s, int nsm)
 {
     k_group_fill<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, flag, gidx, box_off, nbox, groups);
+    g_launches++;
+}
+
+// The box of finest-level cells that holds a group's particles, one warp per group:
+// centre minus the group's cell centre and half sides, in u (cells lo..hi span
+// [2 lo, 2 hi + 2]).  The list builder prunes against it (Eq. 2 vanishes beyond r_cut).
+__global__ void __launch_bounds__(256) k_group_box(const Group *__restrict__ groups,
+                                                   const uint32_t *__restrict__ n_groups,
+                                                   const unsigned long long *__restrict__ pcell,
+                                                   int4 *__restrict__ gbox)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t G = *n_groups;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
+        const Group gr = groups[g];
+        uint32_t lo[3] = {0x1fffffu, 0x1fffffu, 0x1fffffu}, hi[3] = {0u, 0u, 0u};
+        for (uint32_t j = gr.begin + lane; j < gr.begin + gr.count; j += 32) {
+            const unsigned long long c = pcell[j];
+            const uint32_t q[3] = {(uint32_t)c & 0x1fffffu, (uint32_t)(c >> 21) & 0x1fffffu, (uint32_t)(c >> 42)};
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                lo[a] = min(lo[a], q[a]);
+                hi[a] = max(hi[a], q[a]);
+            }
+        }
+        int b[3], h[3];
+        const int gc[3] = {gr.cx, gr.cy, gr.cz};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int l = (int)__reduce_min_sync(FULL, lo[a]);
+            const int u = (int)__reduce_max_sync(FULL, hi[a]);
+            b[a] = l + u + 1 - gc[a];
+            h[a] = u - l + 1;
+        }
+        if (lane == 0) {
+            gbox[2 * (size_t)g] = make_int4(b[0], b[1], b[2], 0);
+            gbox[2 * (size_t)g + 1] = make_int4(h[0], h[1], h[2], 0);
+        }
+    }
+}
+
+void launch_group_box(const Group *groups, const uint32_t *n_groups, const unsigned long long *pcell, int4 *gbox,
+                      cudaStream_t s, int nsm)
+{
+    k_group_box<<<nsm * 8, 256, 0, s>>>(groups, n_groups, pcell, gbox);
     g_launches++;
 }
 

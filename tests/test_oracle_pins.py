@@ -322,6 +322,61 @@ def test_list_completeness_and_disjointness():
         assert np.all(cov[near] == 1)
 
 
+def _box_distance(alo, ahi, blo, bhi, L):
+    """Distance between two axis-aligned boxes [alo, ahi) and [blo, bhi) in a periodic
+    cube of side L: per axis the interval gap minimised over the images -L, 0, +L."""
+    g2 = 0.0
+    for c in range(3):
+        best = np.inf
+        for s in (-L, 0.0, L):
+            best = np.minimum(best, np.maximum(0.0, np.maximum(alo[..., c] + s - bhi[c], blo[c] - ahi[..., c] - s)))
+        g2 = g2 + best * best
+    return np.sqrt(g2)
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.6])
+def test_list_entries_lie_within_rcut_of_the_group(theta):
+    """Entries are kept iff their cell (a node's cell; a particle's finest cell) comes
+    within r_cut of the box of finest cells holding the group's particles.  At theta = 0
+    no node is accepted, so the list is exactly that set of particles; anything farther
+    adds nothing to the force (Eq. 2 is 0 beyond R = 2)."""
+    N = 900
+    pos, m = _clustered(N, 5)
+    L, rc = 1.0, 0.11
+    t = oracle.Tree(pos, m, L, rc, n_crit=14)
+    t.build_lists(theta)
+    off, kind, idx, sh = t.lists()
+    nodes = t.nodes()
+    _, _, xyz, _ = t.sorted()
+    grp = t.groups()
+    c = L / 2 ** 21
+    cell = np.floor(xyz / c)
+    nontrivial = False
+    for gi in range(len(grp)):
+        b, e_ = nodes[grp[gi], 4], nodes[grp[gi], 5]
+        blo, bhi = cell[b:e_].min(0) * c, (cell[b:e_].max(0) + 1) * c
+        ents = slice(off[gi], off[gi + 1])
+        if theta == 0.0:
+            assert np.all(kind[ents] == 0)
+            dist = _box_distance(cell * c, (cell + 1) * c, blo, bhi, L)
+            want = np.flatnonzero(dist <= rc)
+            assert np.array_equal(np.sort(idx[ents]), want)
+            near = np.zeros(N, bool)
+            d = xyz[None, :, :] - xyz[b:e_, None, :]
+            d -= np.rint(d / L) * L
+            near[(np.sqrt((d * d).sum(-1)) < rc).any(0)] = True
+            nontrivial |= bool(np.any(~near[want]) or len(want) < N)
+        else:
+            k, j = kind[ents], idx[ents]
+            nj = np.where(k == 1, j, 0)
+            side = L / 2.0 ** nodes[nj, 0]
+            lo = np.where(k[:, None] == 0, cell[np.where(k == 0, j, 0)] * c, nodes[nj, 1:4] * side[:, None])
+            hi = np.where(k[:, None] == 0, lo + c, lo + side[:, None])
+            nontrivial |= bool(np.any(k == 1))  # here: some node was accepted
+            assert np.all(_box_distance(lo, hi, blo, bhi, L) <= rc)
+    assert nontrivial
+
+
 def test_list_shift_is_min_image_for_near_pairs():
     """The per-entry image shift equals the per-pair minimum image for every pair in range."""
     N = 600
