@@ -38,7 +38,8 @@ extern "C" {
 
 /* Status codes. */
 #define GREEM_OK 0
-#define GREEM_ERR_INVALID_ARG -1   /* bad size/parameter, or a NaN/Inf position seen on the device */
+#define GREEM_ERR_INVALID_ARG -1   /* bad size/parameter, or a NaN/Inf position or a mass that is
+                                      NaN or of magnitude >= 2^38 seen on the device */
 #define GREEM_ERR_CUDA -2          /* a CUDA runtime call failed */
 #define GREEM_ERR_OOM -3           /* device or host allocation failed */
 #define GREEM_ERR_CAPACITY -4      /* a device buffer overflowed (only from graph replays; direct
@@ -98,7 +99,9 @@ void greem_destroy(greem_ctx *ctx);
  * the groups of at most n_crit particles (Sec. 2.2 step 5).  The tree lives in the
  * context until the next build or force call and can be read with greem_debug_dump.
  * Errors: INVALID_ARG (N < 1, N >= 2^31, L <= 0, r_cut outside (0, L/2), theta < 0,
- * eps < 0, n_crit < 1, n_leaf < 1, a NaN/Inf position), CUDA, OOM. */
+ * eps < 0, n_crit < 1, n_leaf < 1, a NaN/Inf position, a mass that is NaN or of
+ * magnitude >= 2^38: the FP32 force keeps the zero-distance pair of a particle with
+ * itself finite only below that), CUDA, OOM. */
 int greem_build_tree(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, const greem_params *p);
 
 /* The whole short-range force (S1-S6) with default settings: n_leaf 10, eps 0, FP32

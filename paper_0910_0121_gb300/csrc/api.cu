@@ -364,7 +364,8 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     uint32_t *perm = nullptr;
     radix_sort(c->k0.p, c->k1.p, c->v0.p, c->v1.p, N, 8, box_passes, c->box_off.p, nbox, c->hist.p, c->scratch.p, &ks,
                &perm, s);
-    launch_gather(r.pos, r.mass, perm, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, s);
+    launch_gather(r.pos, r.mass, perm, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->st.p,
+                  s);
     ev_record(c, r, ev, 2);
     launch_tree_prep(ks, N, c->box_off.p, nbox, c->bps.p, c->d8.p, c->K8.p, c->own.p, s);
     scan_u32(c->own.p, c->base.p, N, c->scratch.p, s);

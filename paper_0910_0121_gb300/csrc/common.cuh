@@ -158,7 +158,8 @@ void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t
                 int box_passes, const uint32_t *box_off, int nbox, uint32_t *hist, uint32_t *scan_scratch,
                 uint64_t **k_out, uint32_t **v_out, cudaStream_t s);
 void launch_gather(const double *pos, const float *mass, const uint32_t *perm, uint32_t N, const uint32_t *box_off,
-                   int nbox, const BoxPar *bps, double *xs, double *ys, double *zs, float *ms, cudaStream_t s);
+                   int nbox, const BoxPar *bps, double *xs, double *ys, double *zs, float *ms, DevStatus *st,
+                   cudaStream_t s);
 
 // S3-S4 (tree.cu)
 void launch_tree_prep(const uint64_t *keys, uint32_t N, const uint32_t *box_off, int nbox, const BoxPar *bps,

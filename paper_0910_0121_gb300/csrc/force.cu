@@ -10,12 +10,19 @@
 //   g(R) = v^5 C(R) + u^6 P(R),  C = (8/35)(7R^3 + 22R^2 + 10R + 4),  P = (7R^2 + 18R + 3)/35,
 // a sum of two non-negative terms for every R >= 0 that is exactly 0 for R >= 2.  The
 // relative error of g therefore stays at a few ulp even where g -> 0 near the cutoff.
-// A pair with r^2 = 0 (the particle itself, or a coincident one) is selected out.
+//
+// Two forms of the pair loop.  With an even number I of i-particles per lane, pairs of
+// i-particles share the sm_100-family packed FP32x2 instructions (two FP32 operations
+// per instruction: half the issue slots, the FP32 pipe is then the limit); r^2 gets a
+// floor of 2^-60 eta^2, so a pair at distance 0 (the particle itself, a coincident one)
+// adds exactly 0 without a select.  With odd I the scalar loop runs and such a pair is
+// selected out.
 //
 // Layout.  A persistent grid; each warp takes one group at a time from an atomic
-// queue.  The warp's 32 lanes are split into S parts (S in 1, 2, 4, 8) of 32/S lanes;
+// queue.  The warp's 32 lanes are split into S parts (S in 1, 2, ..., 32) of 32/S lanes;
 // each lane holds I i-particles in registers and each part runs over every S-th list
 // entry, so small groups do not idle lanes; the parts are summed by shuffles at the end.
+// The layout of each pass comes from a table built at compile time from a cost model.
 // The group's list streams through a per-warp double buffer in shared memory filled by
 // 1-D bulk asynchronous copies (cp.async.bulk, the TMA engine) that complete on an
 // mbarrier; every entry is read by the part's lanes as one broadcast 16-byte load.
@@ -125,6 +132,105 @@ __device__ __forceinline__ float g_p3m(float R)
     return fmaf(u6, p, v5 * c);
 }
 
+// ------------------------------------------------------------------ packed FP32 pairs
+// sm_100-family FP32x2 instructions: one instruction does the same operation on two FP32
+// values held in a 64-bit register pair.  The FP32 pipe still takes two cycles for it,
+// so the peak is unchanged, but the interaction needs half the issue slots and the FP32
+// pipe, not instruction issue, becomes the limit.  Two i-particles share each packed
+// value; the list entry is broadcast into both halves.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// max(x, 0) of both halves as a signed-integer max on the bit patterns (a negative float
+// is a negative integer; the result is +0), on the integer pipe instead of the FP32 pipe
+__device__ __forceinline__ f32x2 relu2(f32x2 v)
+{
+    f32x2 d;
+    asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmax.s32 lo, lo, 0;\n\tmax.s32 hi, hi, 0;\n\t"
+        "mov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(d)
+        : "l"(v));
+    return d;
+}
+__device__ __forceinline__ f32x2 rsqrt2(f32x2 v)
+{
+    float lo, hi;
+    upk(v, lo, hi);
+    asm("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(lo));
+    asm("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(hi));
+    return pk(lo, hi);
+}
+// r^2 gets 2^-60 (in eta^2) before the square root.  That is far below what FP32
+// coordinates relative to the group centre resolve (~1e-7 eta), and it keeps 1/r^3
+// below 2^90, so a pair with D = 0 (the particle itself, a coincident particle) adds
+// exactly 0 without a select; masses must stay below 2^38 for that (checked on input).
+constexpr float kR2Floor = 8.673617379884035e-19f;  // 2^-60
+
+// Packed form of interact() for I = 2H i-particles: (xi[2h], xi[2h+1]) in xi2[h].
+template <int H, bool SOFT>
+__device__ __forceinline__ void interact2(const float4 j, const f32x2 (&xi)[H], const f32x2 (&yi)[H],
+                                          const f32x2 (&zi)[H], f32x2 (&ax)[H], f32x2 (&ay)[H], f32x2 (&az)[H],
+                                          const f32x2 eps2)
+{
+    const f32x2 jx = pk(j.x, j.x), jy = pk(j.y, j.y), jz = pk(j.z, j.z), jm = pk(j.w, j.w);
+    const f32x2 k[11] = {pk(kR2Floor, kR2Floor), pk(1.0f, 1.0f), pk(-0.5f, -0.5f), pk(-1.0f, -1.0f), pk(kC3, kC3),
+                         pk(kC2, kC2),           pk(kC1, kC1),   pk(kC0, kC0),     pk(kP2, kP2),     pk(kP1, kP1),
+                         pk(kP0, kP0)};
+#pragma unroll
+    for (int h = 0; h < H; h++) {
+        const f32x2 dx = sub2(jx, xi[h]), dy = sub2(jy, yi[h]), dz = sub2(jz, zi[h]);
+        const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, k[0])));
+        const f32x2 rinv = rsqrt2(r2);
+        const f32x2 R = mul2(r2, rinv);
+        const f32x2 v = relu2(fma2(R, k[2], k[1]));
+        const f32x2 u = relu2(fma2(R, k[3], k[1]));
+        const f32x2 c = fma2(fma2(fma2(R, k[4], k[5]), R, k[6]), R, k[7]);
+        const f32x2 p = fma2(fma2(R, k[8], k[9]), R, k[10]);
+        const f32x2 v2 = mul2(v, v), v5 = mul2(mul2(v2, v2), v);
+        const f32x2 u2 = mul2(u, u), u6 = mul2(mul2(u2, u2), u2);
+        const f32x2 g = fma2(u6, p, mul2(v5, c));
+        f32x2 ri3;
+        if (!SOFT) {
+            ri3 = mul2(mul2(rinv, rinv), rinv);
+        } else {
+            // Plummer softening: 1/(r^2+eps^2)^(3/2), g at the unsoftened R
+            const f32x2 rs = rsqrt2(fma2(k[1], eps2, r2));
+            ri3 = mul2(mul2(rs, rs), rs);
+        }
+        const f32x2 sc = mul2(mul2(jm, g), ri3);
+        ax[h] = fma2(sc, dx, ax[h]);
+        ay[h] = fma2(sc, dy, ay[h]);
+        az[h] = fma2(sc, dz, az[h]);
+    }
+}
+
 template <int I, bool SOFT>
 __device__ __forceinline__ void interact(const float4 j, const float (&xi)[I], const float (&yi)[I],
                                          const float (&zi)[I], float (&ax)[I], float (&ay)[I], float (&az)[I],
@@ -152,12 +258,59 @@ __device__ __forceinline__ void interact(const float4 j, const float (&xi)[I], c
     }
 }
 
-// Lane layout of one pass: S parts of li = 32/S lanes, I i-particles per lane.  The pass
-// covering the n remaining particles is the one with the fewest slots li*I >= n; when that
-// wastes more than n/8 slots and n > 32, the pass instead takes the largest slot count
-// <= n and leaves the rest to another pass over the same list.  Ties go to more parts
-// (fewer lanes per part, more i per lane): each list entry's load and loop overhead is
-// then shared by more pairs.
+// Lane layout of one pass: S parts of li = 32/S lanes, I i-particles per lane; the pass
+// covers li*I of the group's remaining particles.  Cost model of a pass over a list of
+// len entries, in warp cycles: each lane takes len/S entries at I*w + o cycles each (w =
+// cycles per pair: packed path for even I, scalar path for odd I; o = the entry's load
+// and loop overhead), the list streams through shared memory once per pass (cs cycles
+// per entry), and the S parts are summed by 3*I*log2(S) shuffle-adds (cr cycles each).
+// For n <= 32*kImax remaining particles the first pass of the cheapest sequence of
+// passes covering n (at a typical list length) is tabulated at compile time by dynamic
+// programming over n; larger groups take the widest layout (S = 1, I = kImax).
+#ifndef GREEM_LAYOUT_W_EVEN
+#define GREEM_LAYOUT_W_EVEN 29
+#endif
+#ifndef GREEM_LAYOUT_W_ODD
+#define GREEM_LAYOUT_W_ODD 39
+#endif
+#ifndef GREEM_LAYOUT_O
+#define GREEM_LAYOUT_O 8
+#endif
+#ifndef GREEM_LAYOUT_CS
+#define GREEM_LAYOUT_CS 2
+#endif
+struct LayoutTable {
+    uint8_t v[32 * kImax + 1];  // log2(S) in bits 4-6, I in bits 0-3
+};
+
+constexpr LayoutTable make_layout_table()
+{
+    constexpr long len = 512, cr = 3;
+    LayoutTable t{};
+    long cost[32 * kImax + 1] = {};
+    for (int n = 1; n <= 32 * kImax; n++) {
+        long best = -1;
+        for (int ls = 5; ls >= 0; ls--) {      // more parts first: they win ties
+            const int li = 32 >> ls;
+            for (int I = 1; I <= kImax; I++) {
+                const long w = (I % 2 == 0) ? GREEM_LAYOUT_W_EVEN : GREEM_LAYOUT_W_ODD;
+                const int rest = n - li * I;
+                const long pass = (len * li * (I * w + GREEM_LAYOUT_O)) / 32 +
+                                  len * GREEM_LAYOUT_CS + 3L * I * ls * cr;
+                const long c = pass + cost[rest > 0 ? rest : 0];
+                if (best < 0 || c < best) {
+                    best = c;
+                    t.v[n] = (uint8_t)((ls << 4) | I);
+                }
+            }
+        }
+        cost[n] = best;
+    }
+    return t;
+}
+
+__constant__ LayoutTable c_layout = make_layout_table();
+
 __device__ __forceinline__ void choose_layout(uint32_t n, int &S, int &I)
 {
     if (n > 32u * kImax) {
@@ -165,36 +318,9 @@ __device__ __forceinline__ void choose_layout(uint32_t n, int &S, int &I)
         I = kImax;
         return;
     }
-    int bs = 1, bi = kImax;
-    uint32_t best = 0xffffffffu;
-#pragma unroll
-    for (int s = 32; s >= 1; s >>= 1) {
-        const uint32_t li = 32u / s;
-        const uint32_t ii = (n + li - 1) / li;
-        if (ii > (uint32_t)kImax) continue;
-        const uint32_t slots = li * ii;
-        if (slots < best) {
-            best = slots;
-            bs = s;
-            bi = (int)ii;
-        }
-    }
-    if (n > 32u && best - n > n / 8u) {
-        uint32_t lo = 0;
-#pragma unroll
-        for (int s = 32; s >= 1; s >>= 1) {
-            const uint32_t li = 32u / s;
-            uint32_t ii = n / li;
-            ii = ii > (uint32_t)kImax ? (uint32_t)kImax : ii;
-            if (ii >= 1 && li * ii > lo) {
-                lo = li * ii;
-                bs = s;
-                bi = (int)ii;
-            }
-        }
-    }
-    S = bs;
-    I = bi;
+    const uint32_t v = c_layout.v[n];
+    S = 1 << (v >> 4);
+    I = (int)(v & 15u);
 }
 
 struct WarpPipe {
@@ -238,6 +364,19 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
         zi[s] = v.z;
         ax[s] = ay[s] = az[s] = 0.f;
     }
+    constexpr bool kPacked = (I % 2) == 0;
+    constexpr int H = kPacked ? I / 2 : 1;
+    f32x2 xi2[H], yi2[H], zi2[H], ax2[H], ay2[H], az2[H];
+    const f32x2 eps2x2 = pk(eps2, eps2);
+    if constexpr (kPacked) {
+#pragma unroll
+        for (int h = 0; h < H; h++) {
+            xi2[h] = pk(xi[2 * h], xi[2 * h + 1]);
+            yi2[h] = pk(yi[2 * h], yi[2 * h + 1]);
+            zi2[h] = pk(zi[2 * h], zi[2 * h + 1]);
+            ax2[h] = ay2[h] = az2[h] = pk(0.f, 0.f);
+        }
+    }
     const uint32_t nch = (len + (uint32_t)a.chunk - 1) / (uint32_t)a.chunk;
     if (nch) issue_chunk(a, wp, 0, lo, 0, len, lane);
     bool ok = true;
@@ -257,7 +396,13 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
         }
         const float4 *buf = wp.buf[b];
         const uint32_t nj = min((uint32_t)a.chunk, len - c * (uint32_t)a.chunk);
-        if constexpr (I <= 2) {
+        if constexpr (kPacked) {
+#pragma unroll(kUnroll)
+            for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
+                const float4 j = buf[t];
+                interact2<H, SOFT>(j, xi2, yi2, zi2, ax2, ay2, az2, eps2x2);
+            }
+        } else if constexpr (I <= 2) {
 #pragma unroll 4
             for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
                 const float4 j = buf[t];
@@ -271,6 +416,14 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
             }
         }
         __syncwarp();
+    }
+    if constexpr (kPacked) {
+#pragma unroll
+        for (int h = 0; h < H; h++) {
+            upk(ax2[h], ax[2 * h], ax[2 * h + 1]);
+            upk(ay2[h], ay[2 * h], ay[2 * h + 1]);
+            upk(az2[h], az[2 * h], az[2 * h + 1]);
+        }
     }
 #pragma unroll
     for (int s = 0; s < I; s++) {

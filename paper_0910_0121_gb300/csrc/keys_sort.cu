@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) k_gather(const double *__restrict__ pos, 
                                                 const uint32_t *__restrict__ box_off, int nbox,
                                                 const BoxPar *__restrict__ bps, double *__restrict__ xs,
                                                 double *__restrict__ ys, double *__restrict__ zs,
-                                                float *__restrict__ ms)
+                                                float *__restrict__ ms, DevStatus *st)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -277,13 +277,17 @@ __global__ void __launch_bounds__(256) k_gather(const double *__restrict__ pos, 
     xs[i] = wrap_pos_fast(pos[3 * (size_t)j], L);
     ys[i] = wrap_pos_fast(pos[3 * (size_t)j + 1], L);
     zs[i] = wrap_pos_fast(pos[3 * (size_t)j + 2], L);
-    ms[i] = mass[j];
+    const float m = mass[j];
+    ms[i] = m;
+    // the FP32 force keeps a pair at distance 0 finite only for |m| < 2^38 (and NaN fails too)
+    if (!(fabsf(m) < 274877906944.0f)) atomicOr(&st->flags, ST_NONFINITE);
 }
 
 void launch_gather(const double *pos, const float *mass, const uint32_t *perm, uint32_t N, const uint32_t *box_off,
-                   int nbox, const BoxPar *bps, double *xs, double *ys, double *zs, float *ms, cudaStream_t s)
+                   int nbox, const BoxPar *bps, double *xs, double *ys, double *zs, float *ms, DevStatus *st,
+                   cudaStream_t s)
 {
-    k_gather<<<(N + 255) / 256, 256, 0, s>>>(pos, mass, perm, N, box_off, nbox, bps, xs, ys, zs, ms);
+    k_gather<<<(N + 255) / 256, 256, 0, s>>>(pos, mass, perm, N, box_off, nbox, bps, xs, ys, zs, ms, st);
     g_launches++;
 }
 

@@ -271,6 +271,14 @@ def test_invalid_inputs_are_errors(ctx):
     with pytest.raises(greem.GreemError) as ei:
         gpu_force(ctx, bad, mass, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=8))
     assert ei.value.code == greem.ERR_INVALID_ARG
+    # masses the FP32 force cannot take (NaN, or so large that a particle's zero-distance
+    # pair with itself would overflow) are refused too
+    for mbad in (np.nan, 2.0 ** 38, -(2.0 ** 39)):
+        m2 = mass.copy()
+        m2[42] = mbad
+        with pytest.raises(greem.GreemError) as ei:
+            gpu_force(ctx, pos, m2, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=8))
+        assert ei.value.code == greem.ERR_INVALID_ARG
     for prm in (dict(L=1.0, r_cut=0.5, theta=0.5, n_crit=8), dict(L=1.0, r_cut=0.1, theta=-1.0, n_crit=8),
                 dict(L=0.0, r_cut=0.1, theta=0.5, n_crit=8), dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=0)):
         with pytest.raises(greem.GreemError):
