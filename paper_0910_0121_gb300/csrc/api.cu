@@ -38,6 +38,7 @@ struct greem_ctx {
     // S1-S2
     DBuf<uint64_t> k0, k1;
     DBuf<uint32_t> v0, v1, hist, scratch;
+    DBuf<unsigned long long> rs_status;
     DBuf<double> xs, ys, zs;
     DBuf<float> ms;
     // S3-S4
@@ -295,7 +296,8 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
     ENS(v0, N);
     ENS(v1, N);
     ENS(hist, radix_hist_elems((uint32_t)N));
-    const size_t big = std::max<size_t>(N + 1, std::max<size_t>(c->node_cap + 1, radix_hist_elems((uint32_t)N)));
+    ENS(rs_status, radix_status_elems((uint32_t)N));
+    const size_t big = std::max<size_t>(N + 1, c->node_cap + 1);
     ENS(scratch, scan_scratch_elems(big) + 64);
     ENS(xs, N);
     ENS(ys, N);
@@ -362,8 +364,8 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     const int box_passes = nbox <= 1 ? 0 : (nbox <= 256 ? 1 : 2);
     uint64_t *ks = nullptr;
     uint32_t *perm = nullptr;
-    radix_sort(c->k0.p, c->k1.p, c->v0.p, c->v1.p, N, 8, box_passes, c->box_off.p, nbox, c->hist.p, c->scratch.p, &ks,
-               &perm, s);
+    radix_sort(c->k0.p, c->k1.p, c->v0.p, c->v1.p, N, 8, box_passes, c->box_off.p, nbox, c->hist.p, c->rs_status.p,
+               c->st.p, &ks, &perm, s, nsm);
     launch_gather(r.pos, r.mass, perm, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->st.p,
                   s);
     ev_record(c, r, ev, 2);
@@ -619,6 +621,7 @@ void greem_destroy(greem_ctx *c)
     release(c->pm_grid); release(c->pm_table); release(c->pm_spec); release(c->pm_tmp);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     release(c->k0); release(c->k1); release(c->v0); release(c->v1); release(c->hist); release(c->scratch);
+    release(c->rs_status);
     release(c->xs); release(c->ys); release(c->zs); release(c->ms);
     release(c->d8); release(c->K8); release(c->nchild); release(c->own); release(c->base); release(c->ctr);
     release(c->gflag); release(c->gidx); release(c->nodes); release(c->raw); release(c->mom64); release(c->noff);

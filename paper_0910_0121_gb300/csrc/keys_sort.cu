@@ -94,12 +94,36 @@ void launch_keys(const double *pos, uint32_t N, const uint32_t *box_off, int nbo
 }
 
 // ------------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (key, index) pairs, 8-bit digits, one kernel per digit in the
+// single-pass ("onesweep") form of decoupled look-back (Merrill & Garland 2016; Adinets
+// & Merrill 2022): one pass over the keys histograms every digit at once, then each
+// digit pass reads and writes the pairs once.  A block takes the next tile by ticket,
+// ranks its pairs, publishes its per-digit counts, and adds up its predecessors' counts
+// per digit by looking back through their published words until it meets a published
+// inclusive prefix; the tile is then written out in digit order through shared memory.
+// Tickets make every block wait only on blocks that started before it.  Each wait has an
+// iteration limit, after which the status records a timeout (the call then fails).
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 12;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 3072 pairs per block
+#ifndef GREEM_RS_ITEMS
+#define GREEM_RS_ITEMS 12
+#endif
+#ifndef GREEM_RS_MINB
+#define GREEM_RS_MINB 3
+#endif
+constexpr int kRsItems = GREEM_RS_ITEMS;
+constexpr int kRsTile = kRsThreads * kRsItems;  // pairs per tile
+constexpr int kRsMaxPasses = 10;                // 8 key digits + up to 2 box digits
+constexpr int kRsLook = 8;                      // predecessors loaded at once in the look-back
+constexpr unsigned long long kRsAgg = 1ull << 62, kRsPrefix = 2ull << 62, kRsValue = (1ull << 62) - 1;
+constexpr size_t kRsSmem = (size_t)kRsTile * (sizeof(uint64_t) + sizeof(uint32_t));
 
-size_t radix_hist_elems(uint32_t n) { return (size_t)256 * ((n + kRsTile - 1) / kRsTile) + 1; }
+static inline uint32_t rs_tiles(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
+
+// u32 words: [passes][256] digit counts, [passes][256] digit starts, [passes] tickets
+size_t radix_hist_elems(uint32_t) { return (size_t)kRsMaxPasses * 512 + kRsMaxPasses; }
+// u64 look-back words: [passes][tiles][256]
+size_t radix_status_elems(uint32_t n) { return (size_t)kRsMaxPasses * rs_tiles(n) * 256; }
 
 // SRC 0: digit = key bits [shift, shift+8); SRC 1: digit = bits of the box of the value.
 template <int SRC>
@@ -109,145 +133,254 @@ __device__ __forceinline__ uint32_t rs_digit(uint64_t k, uint32_t v, int shift, 
     return ((uint32_t)box_of(v, box_off, nbox) >> shift) & 255u;
 }
 
-template <int SRC>
-__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t *__restrict__ key,
-                                                         const uint32_t *__restrict__ val, uint32_t n, int shift,
-                                                         uint32_t nblk, uint32_t *__restrict__ hist,
-                                                         const uint32_t *__restrict__ box_off, int nbox)
+// Lanes of the warp whose 8-bit digit equals this lane's (d < 256; lanes with d = 256,
+// out of range, match only each other): one ballot per digit bit.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d)
 {
-    __shared__ uint32_t h[kRsWarps][256];
-    for (int d = threadIdx.x; d < kRsWarps * 256; d += kRsThreads) (&h[0][0])[d] = 0;
+    unsigned peers = __ballot_sync(0xffffffffu, d >= 256u) ^ (d >= 256u ? 0u : 0xffffffffu);
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bb : ~bb;
+    }
+    return peers;
+}
+
+// All digit histograms in one pass over the unsorted keys (the box digits from the box
+// of each input index).  A warp whose lanes share a digit adds it with one shared
+// atomic (the usual case for the high digits of spatially ordered input); otherwise
+// every lane adds its own.
+__global__ void __launch_bounds__(256) k_rs_hist_all(const uint64_t *__restrict__ key, uint32_t n, int key_passes,
+                                                     int box_passes, const uint32_t *__restrict__ box_off, int nbox,
+                                                     uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t h[kRsMaxPasses][256];
+    const int passes = key_passes + box_passes;
+    for (int d = threadIdx.x; d < passes * 256; d += blockDim.x) (&h[0][0])[d] = 0;
     __syncthreads();
-    const int w = threadIdx.x >> 5;
-    const uint32_t base = blockIdx.x * kRsTile;
-#pragma unroll 4
-    for (int t = 0; t < kRsItems; t++) {
-        uint32_t i = base + t * kRsThreads + threadIdx.x;
-        if (i < n) {
-            uint32_t v = val ? val[i] : i;
-            atomicAdd(&h[w][rs_digit<SRC>(key[i], v, shift, box_off, nbox)], 1u);
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint32_t i = i0 + (uint32_t)lane;
+        const bool ok = i < n;
+        const uint64_t k = ok ? key[i] : 0ull;
+        const uint32_t b = (ok && box_passes) ? (uint32_t)box_of(i, box_off, nbox) : 0u;
+        for (int p = 0; p < passes; p++) {
+            const uint32_t d = ok ? (p < key_passes ? (uint32_t)(k >> (8 * p)) & 255u : (b >> (8 * (p - key_passes))) & 255u)
+                                  : 256u;
+            const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+            if (__all_sync(0xffffffffu, d == d0)) {
+                if (lane == 0 && d0 < 256u) atomicAdd(&h[p][d0], 32u);
+            } else if (ok) {
+                atomicAdd(&h[p][d], 1u);
+            }
         }
     }
     __syncthreads();
-    uint32_t s = 0;
-#pragma unroll
-    for (int ww = 0; ww < kRsWarps; ww++) s += h[ww][threadIdx.x];
-    hist[(size_t)threadIdx.x * nblk + blockIdx.x] = s;
+    for (int d = threadIdx.x; d < passes * 256; d += blockDim.x)
+        if ((&h[0][0])[d]) atomicAdd(&hist[d], (&h[0][0])[d]);
 }
 
-// Stable scatter.  Warp w of a block ranks the pairs [w*kRsItems*32, (w+1)*kRsItems*32)
-// of the tile in input order (rounds of 32 consecutive pairs, lanes in order), the block
-// places the tile in shared memory in digit order, and the tile is written out in
-// contiguous runs per digit.
-template <int SRC>
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *__restrict__ kin,
-                                                            const uint32_t *__restrict__ vin,
-                                                            uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                            uint32_t n, int shift, uint32_t nblk,
-                                                            const uint32_t *__restrict__ off,
-                                                            const uint32_t *__restrict__ box_off, int nbox)
+// Exclusive scan of each pass's 256 counts into its digit starts (one warp per pass).
+__global__ void k_rs_digit_starts(uint32_t *hist, int passes)
 {
+    const int p = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (p >= passes) return;
+    const uint32_t *c = hist + p * 256;
+    uint32_t *o = hist + kRsMaxPasses * 256 + p * 256;
+    uint32_t carry = 0;
+    for (int b = 0; b < 256; b += 32) {
+        const uint32_t v = c[b + lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int q = 1; q < 32; q <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
+            if (lane >= q) x += y;
+        }
+        o[b + lane] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int SRC>
+__global__ void __launch_bounds__(kRsThreads, GREEM_RS_MINB) k_rs_onesweep(const uint64_t *__restrict__ kin,
+                                                             const uint32_t *__restrict__ vin,
+                                                             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                             uint32_t n, int shift, const uint32_t *__restrict__ dstart,
+                                                             unsigned long long *status, uint32_t *ticket,
+                                                             const uint32_t *__restrict__ box_off, int nbox,
+                                                             DevStatus *st)
+{
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(rs_smem);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(rs_smem + (size_t)kRsTile * sizeof(uint64_t));
     __shared__ uint32_t wcnt[kRsWarps][256];
-    __shared__ uint32_t dstart[256];
+    __shared__ uint32_t lstart[256];
     __shared__ uint32_t gbase[256];
     __shared__ uint32_t wsum[kRsWarps];
-    __shared__ uint64_t sk[kRsTile];
-    __shared__ uint32_t sv[kRsTile];
+    __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     for (int d = tid; d < kRsWarps * 256; d += kRsThreads) (&wcnt[0][0])[d] = 0;
-    gbase[tid] = off[(size_t)tid * nblk + blockIdx.x];
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
+    const uint32_t tile = s_tile;
 
     uint64_t k[kRsItems];
-    uint32_t v[kRsItems], dg[kRsItems], rk[kRsItems];
-    const uint32_t wbase = blockIdx.x * kRsTile + w * (kRsItems * 32);
+    uint32_t v[kRsItems], rk[kRsItems];
+    const uint32_t wbase = tile * kRsTile + w * (kRsItems * 32);
     const unsigned lt = (1u << lane) - 1u;
-    // all of this thread's loads are issued before the ranking, which is serialised
-    // through shared memory
 #pragma unroll
     for (int t = 0; t < kRsItems; t++) {
         const uint32_t i = wbase + t * 32 + lane;
         k[t] = i < n ? kin[i] : 0ull;
         v[t] = i < n ? (vin ? vin[i] : i) : 0u;
     }
+    // rank within the warp's run of pairs, in input order
 #pragma unroll
     for (int t = 0; t < kRsItems; t++) {
         const bool valid = wbase + t * 32 + lane < n;
-        uint32_t d = valid ? rs_digit<SRC>(k[t], v[t], shift, box_off, nbox) : 256u;
-        dg[t] = d;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = d < 256u ? wcnt[w][d] : 0u;
+        const uint32_t d = valid ? rs_digit<SRC>(k[t], v[t], shift, box_off, nbox) : 256u;
+        const unsigned peers = digit_peers(d);
+        const uint32_t before = d < 256u ? wcnt[w][d] : 0u;
         __syncwarp();
         if (d < 256u && (peers & lt) == 0u) wcnt[w][d] = before + __popc(peers);
         __syncwarp();
-        rk[t] = before + __popc(peers & lt);
+        rk[t] = valid ? before + __popc(peers & lt) : 0xffffffffu;
     }
     __syncthreads();
-    // per digit: exclusive offsets of the warps, and the tile total
+    // thread d: warp-exclusive offsets of digit d and the tile's count of d
     uint32_t tot = 0;
 #pragma unroll
     for (int ww = 0; ww < kRsWarps; ww++) {
-        uint32_t c = wcnt[ww][tid];
+        const uint32_t c = wcnt[ww][tid];
         wcnt[ww][tid] = tot;
         tot += c;
     }
-    // exclusive scan of the 256 digit totals -> tile-local digit starts
+    // publish this tile's count at once, so that later tiles need not wait for it
+    unsigned long long *my = status + (size_t)tile * 256 + tid;
+    if (tile == 0) st_relaxed_u64(my, kRsPrefix | tot);
+    else st_relaxed_u64(my, kRsAgg | tot);
+    // tile-local digit starts
     uint32_t x = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) wsum[w] = x;
     __syncthreads();
     uint32_t wb = 0;
     for (int ww = 0; ww < w; ww++) wb += wsum[ww];
-    dstart[tid] = wb + x - tot;
+    lstart[tid] = wb + x - tot;
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < kRsItems; t++) {
-        if (dg[t] < 256u) {
-            uint32_t lp = dstart[dg[t]] + wcnt[w][dg[t]] + rk[t];
+        if (rk[t] != 0xffffffffu) {
+            const uint32_t d = rs_digit<SRC>(k[t], v[t], shift, box_off, nbox);
+            const uint32_t lp = lstart[d] + wcnt[w][d] + rk[t];
             sk[lp] = k[t];
             sv[lp] = v[t];
         }
     }
     __syncthreads();
-    const uint32_t tbase = blockIdx.x * kRsTile;
+    // the tile sits in shared memory in digit order; look back for the exclusive prefix
+    // of each digit over the earlier tiles
+    if (tile == 0) {
+        gbase[tid] = dstart[tid];
+    } else {
+        // look back over windows of up to kRsLook predecessors, loaded together: add
+        // published counts from the nearest one backwards until a published prefix (done)
+        // or a tile that has not published yet (wait for it, then go on from there)
+        unsigned long long excl = 0;
+        int j = (int)tile - 1;
+        bool done = false, timeout = false;
+        while (!done && !timeout) {
+            unsigned long long sw[kRsLook];
+#pragma unroll
+            for (int q = 0; q < kRsLook; q++)
+                sw[q] = j - q >= 0 ? ld_relaxed_u64(status + (size_t)(j - q) * 256 + tid) : kRsPrefix;
+            int q = 0;
+            for (; q < kRsLook; q++) {
+                if ((sw[q] >> 62) == 0ull) break;  // not published yet
+                excl += sw[q] & kRsValue;
+                if ((sw[q] >> 62) == 2ull) {
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+            j -= q;
+            if (q < kRsLook) {
+                // wait for tile j to publish (bounded)
+                const unsigned long long *w8 = status + (size_t)j * 256 + tid;
+                uint32_t it = 0;
+                while ((ld_relaxed_u64(w8) >> 62) == 0ull) {
+                    if (++it >= (1u << 22)) {
+                        atomicOr(&st->flags, ST_TIMEOUT);
+                        timeout = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+        }
+        st_relaxed_u64(my, kRsPrefix | (excl + tot));
+        gbase[tid] = dstart[tid] + (uint32_t)excl;
+    }
+    __syncthreads();
+    const uint32_t tbase = tile * kRsTile;
     const uint32_t cnt = min((uint32_t)kRsTile, n - tbase);
     for (uint32_t j = tid; j < cnt; j += kRsThreads) {
-        uint64_t kk = sk[j];
-        uint32_t vv = sv[j];
-        uint32_t d = rs_digit<SRC>(kk, vv, shift, box_off, nbox);
-        uint32_t gp = gbase[d] + (j - dstart[d]);
+        const uint64_t kk = sk[j];
+        const uint32_t vv = sv[j];
+        const uint32_t d = rs_digit<SRC>(kk, vv, shift, box_off, nbox);
+        const uint32_t gp = gbase[d] + (j - lstart[d]);
         kout[gp] = kk;
         vout[gp] = vv;
     }
 }
 
 void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t n, int key_passes, int box_passes,
-                const uint32_t *box_off, int nbox, uint32_t *hist, uint32_t *scan_scratch, uint64_t **k_out,
-                uint32_t **v_out, cudaStream_t s)
+                const uint32_t *box_off, int nbox, uint32_t *hist, unsigned long long *status, DevStatus *st,
+                uint64_t **k_out, uint32_t **v_out, cudaStream_t s, int nsm)
 {
-    const uint32_t nblk = (n + kRsTile - 1) / kRsTile;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_rs_onesweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem);
+        cudaFuncSetAttribute(k_rs_onesweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem);
+        attr_set = true;
+    }
+    const uint32_t ntile = rs_tiles(n);
+    const int passes = key_passes + box_passes;
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * radix_hist_elems(n), s);
+    cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)passes * ntile * 256, s);
+    k_rs_hist_all<<<nsm * 4, 256, 0, s>>>(k0, n, key_passes, box_passes, box_off, nbox, hist);
+    k_rs_digit_starts<<<1, 32 * passes, 0, s>>>(hist, passes);
+    g_launches += 2;
     uint64_t *ki = k0, *ko = k1;
     uint32_t *vi = nullptr, *vo = v1;  // first pass generates the identity values
     uint32_t *vfree = v0;
-    const int passes = key_passes + box_passes;
     for (int p = 0; p < passes; p++) {
         const bool boxp = p >= key_passes;
         const int shift = boxp ? 8 * (p - key_passes) : 8 * p;
+        const uint32_t *ds = hist + kRsMaxPasses * 256 + p * 256;
+        uint32_t *tk = hist + kRsMaxPasses * 512 + p;
+        unsigned long long *sw = status + (size_t)p * ntile * 256;
         if (boxp) {
-            k_rs_hist<1><<<nblk, kRsThreads, 0, s>>>(ki, vi, n, shift, nblk, hist, box_off, nbox);
+            k_rs_onesweep<1><<<ntile, kRsThreads, kRsSmem, s>>>(ki, vi, ko, vo, n, shift, ds, sw, tk, box_off, nbox, st);
         } else {
-            k_rs_hist<0><<<nblk, kRsThreads, 0, s>>>(ki, vi, n, shift, nblk, hist, box_off, nbox);
-        }
-        g_launches++;
-        scan_u32(hist, hist, (size_t)256 * nblk, scan_scratch, s);
-        if (boxp) {
-            k_rs_scatter<1><<<nblk, kRsThreads, 0, s>>>(ki, vi, ko, vo, n, shift, nblk, hist, box_off, nbox);
-        } else {
-            k_rs_scatter<0><<<nblk, kRsThreads, 0, s>>>(ki, vi, ko, vo, n, shift, nblk, hist, box_off, nbox);
+            k_rs_onesweep<0><<<ntile, kRsThreads, kRsSmem, s>>>(ki, vi, ko, vo, n, shift, ds, sw, tk, box_off, nbox, st);
         }
         g_launches++;
         // ping-pong

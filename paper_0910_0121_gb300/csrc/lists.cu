@@ -1,8 +1,7 @@
 // S5 Barnes (1990) grouped interaction lists (Sec. 2.2 steps 3 and 5; Sec. 3.1.2).
 //
-// One warp per group walks its box's tree from the root with a per-warp stack of node
-// indices: each step pops up to 32 nodes, one per lane, and each lane decides, in
-// this order:
+// One warp per group walks its box's tree from the root with a per-warp stack.  Every
+// node the recursive walk visits is tested, in this order:
 //   prune  -- the node's cell is farther than r_cut from the group's particle box (the
 //             box of finest-level cells that holds the group's particles; periodic
 //             box-to-box distance), so none of its particles can act (Eq. 2 is 0);
@@ -12,11 +11,10 @@
 //             centre of mass (Sec. 3.1.2);
 //   leaf   -- an opened leaf puts its particles into the list, each but those whose
 //             finest cell passes the prune test (the same integer test at level 21);
-//   open   -- the node's children (child table, up to 8) are pushed.
-// Every popped node is one the recursive walk visits, so no lane tests a node inside a
-// pruned or accepted subtree.  The entries are the same set as the recursive walk's;
-// their order within a list is the order of the steps (the debug dump sorts each list
-// back into preorder, i.e. by first particle).
+//   open   -- the node's children are tested next.
+// No node inside a pruned or accepted subtree is tested.  The entries are the same set
+// as the recursive walk's; their order within a list is the order of the steps (the
+// debug dump sorts each list back into preorder, i.e. by first particle).
 // Every test is done in integer units u = L/2^22 against thresholds the host derives
 // from the FP64 comparisons (double)S*u*u > r_cut*r_cut and (double)l*l < theta*theta*S,
 // so the lists are exact and bit-identical to a sequential FP64 walk.
@@ -63,13 +61,72 @@ __device__ __forceinline__ Node load_node(const Node *p)
     return n;
 }
 
+// Geometry of a cell against the group: the offset of its centre from the group's cell
+// centre (u, wrapped to the nearest image, shift code of that image), the squared gap
+// to the group's particle box, and the squared distance from its centre to the group
+// cell (both in u^2).
+struct CellTest {
+    int dx, dy, dz;
+    unsigned shc;
+    long long Sg, Sd;
+};
+
+__device__ __forceinline__ CellTest cell_test(uint32_t ix, uint32_t iy, uint32_t iz, int h, const Group &gr,
+                                              const int4 tb, const int4 th)
+{
+    CellTest c;
+    int sx, sy, sz;
+    c.dx = wrap_delta(2 * (int)ix + h - gr.cx, sx);
+    c.dy = wrap_delta(2 * (int)iy + h - gr.cy, sy);
+    c.dz = wrap_delta(2 * (int)iz + h - gr.cz, sz);
+    c.shc = shift_code(sx, sy, sz);
+    const int gx = max(0, abs(c.dx - tb.x) - h - th.x), gy = max(0, abs(c.dy - tb.y) - h - th.y),
+              gz = max(0, abs(c.dz - tb.z) - h - th.z);
+    const int ex = max(0, abs(c.dx) - gr.hg), ey = max(0, abs(c.dy) - gr.hg), ez = max(0, abs(c.dz) - gr.hg);
+    c.Sg = (long long)gx * gx + (long long)gy * gy + (long long)gz * gz;
+    c.Sd = (long long)ex * ex + (long long)ey * ey + (long long)ez * ez;
+    return c;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// The lane s whose exclusive offset off is the largest one <= t (offsets non-decreasing).
+__device__ __forceinline__ int owner_lane(uint32_t off, uint32_t t)
+{
+    int s = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const uint32_t oc = __shfl_sync(0xffffffffu, off, s + step);
+        if (oc <= t) s += step;
+    }
+    return s;
+}
+
 // Walks one group's list; writes entries [pos0, pos0+total) clipped at lim; returns
 // total.  stk is this warp's stack (a.stack_cap entries); an overflow sets the status.
+//
+// The stack holds nodes that passed the prune test and failed the accept test: leaves,
+// whose particles are emitted, and nodes to open.  Each step pops up to 32 of them, one
+// per lane.  The children of the opened nodes are then spread over the lanes, 32 at a
+// time: a child's cell follows from its parent's cell and its octant (the parent's
+// child-octant mask), so prune and accept are decided without loading the child; an
+// accepted child is written as one entry at its centre of mass, and the others are
+// pushed.  Last, the particles of the popped leaves are spread over the lanes and each
+// goes through the per-particle r_cut test unless its whole leaf lies within r_cut.
 __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb, const int4 th, const BoxPar &bp,
                                uint32_t root, uint32_t *__restrict__ stk, unsigned long long pos0,
                                unsigned long long lim, int lane)
 {
     const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
     const uint32_t gend = gr.begin + gr.count;
     const long long Tp = bp.T_prune;
     const int lmin = bp.lmin;
@@ -78,8 +135,9 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
     uint32_t cnt = 0;
     if (lane == 0) stk[0] = root;
     uint32_t sp = 1;
+    bool overflow = false;
     __syncwarp();
-    while (sp > 0) {
+    while (sp > 0 && !overflow) {
         const uint32_t nb = min(sp, 32u);
         const uint32_t sbase = sp - nb;
         const bool valid = (uint32_t)lane < nb;
@@ -93,125 +151,123 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
             nd.ix = nd.iy = nd.iz = 0; nd.lvl = 0; nd.begin = nd.end = nd.skip = 0; nd.parent = 0;
         }
         const int k = nd.lvl & 255u;
-        const bool leaf = (nd.lvl & 256u) != 0;
-        const int h = 1 << (kMaxLevel - k);
-        int sx, sy, sz;
-        const int dx = wrap_delta(2 * (int)nd.ix + h - gr.cx, sx);
-        const int dy = wrap_delta(2 * (int)nd.iy + h - gr.cy, sy);
-        const int dz = wrap_delta(2 * (int)nd.iz + h - gr.cz, sz);
-        const int ax = abs(dx), ay = abs(dy), az = abs(dz);
-        const int gx = max(0, abs(dx - tb.x) - h - th.x), gy = max(0, abs(dy - tb.y) - h - th.y),
-                  gz = max(0, abs(dz - tb.z) - h - th.z);
-        const int ex = max(0, ax - gr.hg), ey = max(0, ay - gr.hg), ez = max(0, az - gr.hg);
-        const long long Sg = (long long)gx * gx + (long long)gy * gy + (long long)gz * gz;
-        const long long Sd = (long long)ex * ex + (long long)ey * ey + (long long)ez * ez;
-        const bool prune = Sg > Tp;
-        // an opened leaf whose whole cell lies within r_cut of the particle box keeps every
-        // particle (each particle's finest cell is inside the leaf's cell), so its particles
-        // skip the per-particle test
-        const int fx = max(0, abs(dx - tb.x) + h - th.x), fy = max(0, abs(dy - tb.y) + h - th.y),
-                  fz = max(0, abs(dz - tb.z) + h - th.z);
-        const bool test_each = (long long)fx * fx + (long long)fy * fy + (long long)fz * fz > Tp;
-        const bool accept = !prune && k >= lmin && Sd > bp.A[k];
-        const bool open = valid && !prune && !accept && !leaf;
-        uint32_t ne = (valid && !prune) ? (accept ? 1u : (leaf ? nd.end - nd.begin : 0u)) : 0u;
-        // push the children of opened nodes
-        uint4 k0 = make_uint4(kNone, kNone, kNone, kNone), k1 = k0;
-        uint32_t nch = 0;
-        if (open) {
-            const uint4 *kp = reinterpret_cast<const uint4 *>(a.kids + (size_t)m * 8);
-            k0 = __ldg(kp);
-            k1 = __ldg(kp + 1);
-            nch = (k0.x != kNone) + (k0.y != kNone) + (k0.z != kNone) + (k0.w != kNone) + (k1.x != kNone) +
-                  (k1.y != kNone) + (k1.z != kNone) + (k1.w != kNone);
-        }
-        uint32_t csum = nch;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(FULL, csum, o);
-            if (lane >= o) csum += y;
-        }
+        const bool leaf = valid && (nd.lvl & 256u) != 0;
+        const uint32_t mask = valid && !leaf ? (nd.lvl >> 16) & 255u : 0u;
+
+        // ---- children of the opened nodes: prune, accept (one entry), or push
+        const uint32_t nch = __popc(mask);
+        const uint32_t csum = warp_incl_scan(nch, lane);
+        const uint32_t coff = csum - nch;
         const uint32_t ctot = __shfl_sync(FULL, csum, 31);
-        if (sp + ctot > cap) {
-            if (lane == 0) atomicOr(&a.st->flags, ST_STACK);
-            break;  // the caller's list is incomplete; the call is retried with a larger stack
+        for (uint32_t c0 = 0; c0 < ctot; c0 += 32) {
+            const uint32_t t = c0 + lane;
+            const int s = owner_lane(coff, t);
+            const uint32_t o_s = __shfl_sync(FULL, coff, s);
+            const uint32_t pix = __shfl_sync(FULL, nd.ix, s), piy = __shfl_sync(FULL, nd.iy, s),
+                           piz = __shfl_sync(FULL, nd.iz, s), plvl = __shfl_sync(FULL, nd.lvl, s),
+                           pm = __shfl_sync(FULL, m, s);
+            bool acc = false, push = false;
+            uint32_t child = 0;
+            CellTest ct;
+            if (t < ctot) {
+                const uint32_t q = t - o_s;
+                const uint32_t oct = __fns((plvl >> 16) & 255u, 0, (int)q + 1);
+                const int kc = (int)(plvl & 255u) + 1;
+                const int hc = 1 << (kMaxLevel - kc);
+                ct = cell_test(pix + ((oct >> 2) & 1u) * (uint32_t)hc, piy + ((oct >> 1) & 1u) * (uint32_t)hc,
+                               piz + (oct & 1u) * (uint32_t)hc, hc, gr, tb, th);
+                if (ct.Sg <= Tp) {
+                    child = __ldg(a.kids + (size_t)pm * 8 + q);
+                    acc = kc >= lmin && ct.Sd > bp.A[kc];
+                    push = !acc;
+                }
+            }
+            const unsigned ab = __ballot_sync(FULL, acc);
+            if (acc) {
+                const unsigned long long p = pos0 + cnt + __popc(ab & lt);
+                const float4 v = __ldg(a.noff + child);
+                const float4 e = make_float4(__fadd_rn(__fmul_rn((float)ct.dx, kf), v.x),
+                                             __fadd_rn(__fmul_rn((float)ct.dy, kf), v.y),
+                                             __fadd_rn(__fmul_rn((float)ct.dz, kf), v.z), v.w);
+                if (p < lim) {
+                    a.flist[p] = e;
+                    if (a.ilist) a.ilist[p] = (unsigned long long)child | (1ull << 32) | ((unsigned long long)ct.shc << 33);
+                }
+            }
+            cnt += __popc(ab);
+            const unsigned pb = __ballot_sync(FULL, push);
+            if (sp + __popc(pb) > cap) {
+                if (lane == 0) atomicOr(&a.st->flags, ST_STACK);
+                overflow = true;  // the caller's list is incomplete; the call is retried with a larger stack
+                break;
+            }
+            if (push) stk[sp + __popc(pb & lt)] = child;
+            sp += __popc(pb);
         }
-        if (nch) {
-            uint32_t *d = stk + sp + (csum - nch);
-            const uint32_t kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                if ((uint32_t)q < nch) d[q] = kk[q];
-        }
-        sp += ctot;
         __syncwarp();
-        uint32_t isum = ne;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(FULL, isum, o);
-            if (lane >= o) isum += y;
+        if (overflow) break;
+
+        // ---- particles of the popped leaves
+        uint32_t ne = 0;
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        unsigned shc = 0;
+        if (leaf) {
+            const int h = 1 << (kMaxLevel - k);
+            const CellTest lc = cell_test(nd.ix, nd.iy, nd.iz, h, gr, tb, th);
+            // a leaf whose whole cell lies within r_cut of the particle box keeps every
+            // particle (each particle's finest cell is inside the leaf's cell)
+            const int fx = max(0, abs(lc.dx - tb.x) + h - th.x), fy = max(0, abs(lc.dy - tb.y) + h - th.y),
+                      fz = max(0, abs(lc.dz - tb.z) + h - th.z);
+            const bool test_each = (long long)fx * fx + (long long)fy * fy + (long long)fz * fz > Tp;
+            ne = nd.end - nd.begin;
+            bx = __fmul_rn((float)lc.dx, kf);
+            by = __fmul_rn((float)lc.dy, kf);
+            bz = __fmul_rn((float)lc.dz, kf);
+            shc = lc.shc | (test_each ? 64u : 0u);
         }
+        const uint32_t isum = warp_incl_scan(ne, lane);
         const uint32_t off = isum - ne;
         const uint32_t tot = __shfl_sync(FULL, isum, 31);
-        if (tot) {
-            const float bx = __fmul_rn((float)dx, kf), by = __fmul_rn((float)dy, kf), bz = __fmul_rn((float)dz, kf);
-            const uint32_t src = accept ? (m | 0x80000000u) : nd.begin;
-            const unsigned shc = shift_code(sx, sy, sz) | ((test_each && !accept) ? 64u : 0u);
-            for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
-                const uint32_t t = t0 + lane;
-                int s = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t oc = __shfl_sync(FULL, off, s + step);
-                    if (oc <= t) s += step;
+        for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            const int s = owner_lane(off, t);
+            const uint32_t o_s = __shfl_sync(FULL, off, s);
+            const uint32_t b_s = __shfl_sync(FULL, nd.begin, s);
+            const float bx_s = __shfl_sync(FULL, bx, s), by_s = __shfl_sync(FULL, by, s),
+                        bz_s = __shfl_sync(FULL, bz, s);
+            const unsigned sh_s = __shfl_sync(FULL, shc, s);
+            bool keep = false;
+            float4 e;
+            uint32_t j = kNone;
+            if (t < tot) {
+                j = b_s + (t - o_s);
+                const float4 v = __ldg(a.poff + j);
+                keep = true;
+                if (sh_s & 64u) {
+                    // the particle's finest cell, in its leaf's image, against the particle box
+                    const unsigned long long c = __ldg(a.pcell + j);
+                    const int px = 2 * (int)((uint32_t)c & 0x1fffffu) + 1 - gr.cx - tb.x +
+                                   ((sh_s & 1u) ? kPeriod : ((sh_s & 2u) ? -kPeriod : 0));
+                    const int py = 2 * (int)((uint32_t)(c >> 21) & 0x1fffffu) + 1 - gr.cy - tb.y +
+                                   ((sh_s & 4u) ? kPeriod : ((sh_s & 8u) ? -kPeriod : 0));
+                    const int pz = 2 * (int)(uint32_t)(c >> 42) + 1 - gr.cz - tb.z +
+                                   ((sh_s & 16u) ? kPeriod : ((sh_s & 32u) ? -kPeriod : 0));
+                    const int qx = max(0, abs(px) - 1 - th.x), qy = max(0, abs(py) - 1 - th.y),
+                              qz = max(0, abs(pz) - 1 - th.z);
+                    keep = (long long)qx * qx + (long long)qy * qy + (long long)qz * qz <= Tp;
                 }
-                const uint32_t o_s = __shfl_sync(FULL, off, s);
-                const uint32_t src_s = __shfl_sync(FULL, src, s);
-                const float bx_s = __shfl_sync(FULL, bx, s), by_s = __shfl_sync(FULL, by, s),
-                            bz_s = __shfl_sync(FULL, bz, s);
-                const unsigned sh_s = __shfl_sync(FULL, shc, s);
-                bool keep = false;
-                float4 e;
-                unsigned long long ie = 0;
-                if (t < tot) {
-                    float4 v;
-                    uint32_t j = kNone;
-                    keep = true;
-                    if (src_s & 0x80000000u) {
-                        const uint32_t nn = src_s & 0x7fffffffu;
-                        v = __ldg(a.noff + nn);
-                        ie = (unsigned long long)nn | (1ull << 32);
-                    } else {
-                        j = src_s + (t - o_s);
-                        v = __ldg(a.poff + j);
-                        ie = (unsigned long long)j;
-                    }
-                    if (sh_s & 64u) {
-                        // the particle's finest cell, in its leaf's image, against the particle box
-                        const unsigned long long c = __ldg(a.pcell + j);
-                        const int px = 2 * (int)((uint32_t)c & 0x1fffffu) + 1 - gr.cx - tb.x +
-                                       ((sh_s & 1u) ? kPeriod : ((sh_s & 2u) ? -kPeriod : 0));
-                        const int py = 2 * (int)((uint32_t)(c >> 21) & 0x1fffffu) + 1 - gr.cy - tb.y +
-                                       ((sh_s & 4u) ? kPeriod : ((sh_s & 8u) ? -kPeriod : 0));
-                        const int pz = 2 * (int)(uint32_t)(c >> 42) + 1 - gr.cz - tb.z +
-                                       ((sh_s & 16u) ? kPeriod : ((sh_s & 32u) ? -kPeriod : 0));
-                        const int qx = max(0, abs(px) - 1 - th.x), qy = max(0, abs(py) - 1 - th.y),
-                                  qz = max(0, abs(pz) - 1 - th.z);
-                        keep = (long long)qx * qx + (long long)qy * qy + (long long)qz * qz <= Tp;
-                    }
-                    e = make_float4(__fadd_rn(bx_s, v.x), __fadd_rn(by_s, v.y), __fadd_rn(bz_s, v.z), v.w);
-                    if (j >= gr.begin && j < gend) a.irel[j] = e;
-                }
-                const unsigned kb = __ballot_sync(FULL, keep);
-                if (keep) {
-                    const unsigned long long p = pos0 + cnt + __popc(kb & ((1u << lane) - 1u));
-                    if (p < lim) {
-                        a.flist[p] = e;
-                        if (a.ilist) a.ilist[p] = ie | ((unsigned long long)(sh_s & 63u) << 33);
-                    }
-                }
-                cnt += __popc(kb);
+                e = make_float4(__fadd_rn(bx_s, v.x), __fadd_rn(by_s, v.y), __fadd_rn(bz_s, v.z), v.w);
+                if (j >= gr.begin && j < gend) a.irel[j] = e;
             }
+            const unsigned kb = __ballot_sync(FULL, keep);
+            if (keep) {
+                const unsigned long long p = pos0 + cnt + __popc(kb & lt);
+                if (p < lim) {
+                    a.flist[p] = e;
+                    if (a.ilist) a.ilist[p] = (unsigned long long)j | ((unsigned long long)(sh_s & 63u) << 33);
+                }
+            }
+            cnt += __popc(kb);
         }
     }
     __syncwarp();

@@ -150,9 +150,11 @@ __device__ __forceinline__ uint32_t node_count(const uint32_t *n_nodes, uint32_t
     return n < cap ? n : cap;
 }
 
-// Parent links, child counts and the child table (up to 8 children per internal node,
-// unused slots kNone): the children of an internal node p are p+1 and then the skip
-// chain while it stays inside p's particle range.
+// Parent links, child counts, the child table (up to 8 children per internal node,
+// unused slots kNone) and each node's child-octant mask (bits 16-23 of lvl; octant =
+// x<<2 | y<<1 | z of the child's cell within the parent's): the children of an internal
+// node p are p+1 and then the skip chain while it stays inside p's particle range, in
+// Morton order, so slot q holds the child in the octant of the mask's (q+1)-th set bit.
 __global__ void __launch_bounds__(256) k_tree_links(Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
                                                     uint32_t node_cap, uint8_t *__restrict__ nchild,
                                                     uint32_t *__restrict__ kids)
@@ -163,17 +165,21 @@ __global__ void __launch_bounds__(256) k_tree_links(Node *__restrict__ nodes, co
         uint32_t slot[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) slot[k] = kNone;
-        uint32_t cnt = 0;
+        uint32_t cnt = 0, mask = 0;
         if (!(np.lvl & 256u)) {
+            const int sh = kMaxLevel - 1 - (int)(np.lvl & 255u);  // child side in finest cells = 1 << sh
             uint32_t c = p + 1;
             while (c < nn && nodes[c].begin < np.end && cnt < 8) {
+                const Node nc = nodes[c];
                 nodes[c].parent = p;
+                mask |= 1u << ((((nc.ix >> sh) & 1u) << 2) | (((nc.iy >> sh) & 1u) << 1) | ((nc.iz >> sh) & 1u));
 #pragma unroll
                 for (int k = 0; k < 8; k++)
                     if (k == (int)cnt) slot[k] = c;
                 cnt++;
-                c = nodes[c].skip;
+                c = nc.skip;
             }
+            nodes[p].lvl = np.lvl | (mask << 16);
         }
         nchild[p] = (uint8_t)cnt;
         uint4 *kp = reinterpret_cast<uint4 *>(kids + (size_t)p * 8);
