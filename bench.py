@@ -43,9 +43,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the graph, theta-scan and batched lines")
     ap.add_argument("--config5", action="store_true",
                     help="time the 512^3 full TreePM step (PP + TSC PM on 512^3) in one CUDA graph instead")
-    ap.add_argument("--profile-case", choices=["nfw128", "zel256"], default=None,
-                    help="run --steps short-force calls on this workload (n_crit from --n-crit, else 128) "
-                         "and print the stats; no timing (the small case for profiler captures)")
+    ap.add_argument("--profile-case", choices=["nfw128", "zel256", "zel256tree"], default=None,
+                    help="run --steps short-force calls on this workload (n_crit from --n-crit, else 128; "
+                         "zel256tree: tree builds only, about 2 GB on the device) and print the stats; no "
+                         "timing (the small cases for profiler captures)")
     return ap.parse_args()
 
 
@@ -494,7 +495,10 @@ def profile_case(args):
     p = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=args.n_crit or 128,
                      n_leaf=prm["n_leaf"])
     for _ in range(args.steps):
-        ctx.short_force(P, M, p, acc)
+        if args.profile_case == "zel256tree":
+            ctx.build_tree(P, M, p)
+        else:
+            ctx.short_force(P, M, p, acc)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile_case, "n_crit": p.n_crit, **ctx.stats()}), flush=True)
     ctx.close()
