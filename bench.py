@@ -210,7 +210,8 @@ def traffic_per_launch(list_entries):
 
 def extras(ctx, P, M, p, prm, acc, stream):
     """Context numbers beside the headline: CUDA-graph replay of the same step, the
-    opening-angle scan, and the 64-box batched workload (one call vs per-box calls)."""
+    opening-angle scan, the distance-dependent opening angle of Eq. 12, and the 64-box
+    batched workload (one call vs per-box calls)."""
     import torch
     from paper_0910_0121_gb300 import greem, synth
     out = {}
@@ -247,6 +248,19 @@ def extras(ctx, P, M, p, prm, acc, stream):
         scan[str(th)] = {"ms_per_step": a.elapsed_time(b), "N_int": s["n_interactions"] / N,
                          "force_tflops": FLOPS_PER_INTERACTION * s["n_interactions"] / (s["ms_force"] * 1e-3) / 1e12}
     out["theta_scan"] = scan
+    # distance-dependent opening angle of Eq. 12 (Sec. 4.1), theta0 = 0.25 capped at 0.7: on
+    # a 32^3 NFW mix it matches theta = 0.5's interaction count with a lower error tail
+    q = greem.params(L=p.L, r_cut=p.r_cut, theta=0.7, n_crit=p.n_crit, n_leaf=p.n_leaf, list_chunk=p.list_chunk,
+                     block_shape=p.block_shape, flags=greem.FLAG_STAGE_TIMES | greem.FLAG_THETA_EQ12, theta0=0.25)
+    ctx.short_force(P, M, q, acc)
+    a, b = ev(), ev()
+    a.record(stream)
+    ctx.short_force(P, M, q, acc)
+    b.record(stream)
+    torch.cuda.synchronize()
+    s = ctx.stats()
+    out["theta_eq12"] = {"theta0": 0.25, "theta_max": 0.7, "ms_per_step": a.elapsed_time(b),
+                         "N_int": s["n_interactions"] / N, "lists_ms": s["ms_lists"], "force_ms": s["ms_force"]}
     # 64 independent boxes: one batched call vs one call per box (FP32) and per-box FP64 calls
     bpos, bmass, boff, bprm = synth.config_batched()
     BP = torch.from_numpy(bpos).cuda()

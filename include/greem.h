@@ -58,6 +58,12 @@ extern "C" {
 #define GREEM_FLAG_ADD_PM 4u       /* add the PM (long-range) force of greem_pm_force, on n_pm^3 with
                                       the assign scheme, to acc in the same call (single box, FP32):
                                       the full TreePM force, Sec. 2.1 */
+#define GREEM_FLAG_THETA_EQ12 8u   /* distance-dependent opening angle of Sec. 4.1, Eq. 12: a node is
+                                      accepted iff l < theta(d) d with theta(d) = min(theta,
+                                      theta0 / sqrt(R g(R))), R = d/eta, g of Eq. 2 (theta(d) = theta
+                                      where R g(R) = 0); theta is then the upper limit the paper
+                                      calls for.  Per box in greem_short_force_batched (theta0 from
+                                      each box's parameters, the flag from per_box[0]). */
 
 /* PM mass assignment schemes (greem_pm_force, greem_params.assign). */
 #define GREEM_ASSIGN_CIC 0
@@ -78,10 +84,12 @@ typedef struct greem_params {
     unsigned flags;  /* GREEM_FLAG_* */
     int n_pm;        /* PM grid points per side for GREEM_FLAG_ADD_PM (8..1024) */
     int assign;      /* GREEM_ASSIGN_CIC or GREEM_ASSIGN_TSC for GREEM_FLAG_ADD_PM */
+    double theta0;   /* theta_0 of Eq. 12 for GREEM_FLAG_THETA_EQ12, > 0 (R in units of eta
+                        makes it dimensionless) */
 } greem_params;
 
 /* Fills defaults: L 1, r_cut 3/32, theta 0.5, eps 0, n_crit 64, n_leaf 10 (Sec. 3.1.2),
- * F32 precision, default chunk and block shape, no flags. */
+ * F32 precision, default chunk and block shape, no flags, theta0 0.25. */
 void greem_params_default(greem_params *p);
 
 typedef struct greem_ctx greem_ctx; /* opaque; owns all device workspace */

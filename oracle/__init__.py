@@ -77,6 +77,8 @@ def lib():
                 getattr(L, f).argtypes = [_vp, _vp]
             L.or_lists_build.restype = ctypes.c_int
             L.or_lists_build.argtypes = [_vp, _dbl, _vp, _i64]
+            L.or_lists_build_eq12.restype = ctypes.c_int
+            L.or_lists_build_eq12.argtypes = [_vp, _dbl, _dbl, _vp, _i64]
             L.or_lists_get.restype = None
             L.or_lists_get.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.or_list_force.restype = ctypes.c_int
@@ -210,10 +212,16 @@ class Tree:
         lib().or_tree_get_groups(self._h, _ptr(out))
         return out
 
-    def build_lists(self, theta: float, groups=None):
+    def build_lists(self, theta: float, groups=None, theta0=None):
+        """Lists with the constant opening angle theta, or, when theta0 is given, with the
+        distance-dependent angle of Eq. 12 (Sec. 4.1) capped at theta_max = theta."""
         sel = None if groups is None else np.ascontiguousarray(groups, dtype=np.int64)
-        rc = lib().or_lists_build(self._h, float(theta), None if sel is None else _ptr(sel),
-                                  0 if sel is None else sel.shape[0])
+        if theta0 is None:
+            rc = lib().or_lists_build(self._h, float(theta), None if sel is None else _ptr(sel),
+                                      0 if sel is None else sel.shape[0])
+        else:
+            rc = lib().or_lists_build_eq12(self._h, float(theta0), float(theta), None if sel is None else _ptr(sel),
+                                           0 if sel is None else sel.shape[0])
         if rc:
             raise ValueError(f"oracle list build failed ({rc})")
         self.theta = float(theta)

@@ -41,6 +41,10 @@
  *     group.  A particle of an opened leaf is tested the same way with its own finest
  *     cell and is left out when the test holds.  Either way the left-out mass lies
  *     farther than r_cut from every particle of the group, where Eq. 2 is exactly 0.
+ *   - distance-dependent opening angle (Sec. 4.1, Eq. 12), when selected: theta(d) =
+ *     min(theta_max, theta0 / sqrt(R g(R))) with R = d/eta (the distance in units of eta,
+ *     which makes theta0 dimensionless) and theta(d) = theta_max where R g(R) = 0; the
+ *     accept test below then uses theta(d)^2 in place of theta^2.
  *   - accept iff level >= l_min and (double)(l*l) < (theta*theta) * (double)S_d,
  *     l = node side, S_d = squared distance from node centre to the nearest point of
  *     the group cell (both in u).  Prune is tested first.
@@ -425,7 +429,21 @@ typedef struct {
     int64_t cg[3], hg; /* group cell centre and half side, units of u */
     int64_t cb[3], hb[3]; /* centre and half sides of the group's particle box, units of u */
     double uu, rc2, th2;
+    int eq12;              /* distance-dependent theta (Eq. 12) */
+    double t02, tmax2;     /* theta0^2, theta_max^2 */
+    double u_over_eta;
 } walk_t;
+
+/* theta^2 of the accept test at squared distance sd (units of u^2). */
+static double walk_theta2(const walk_t *W, int64_t sd)
+{
+    if (!W->eq12) return W->th2;
+    double R = sqrt((double)sd) * W->u_over_eta;
+    double rg = R * or_g_p3m(R);
+    if (!(rg > 0.0)) return W->tmax2;
+    double t2 = W->t02 / rg;
+    return t2 < W->tmax2 ? t2 : W->tmax2;
+}
 
 /* r_cut test of a box (centre d relative to the group cell centre, already the image
  * to use; half side h, all in u) against the group's particle box. */
@@ -488,7 +506,7 @@ static int walk_rec(walk_t *W, int64_t n)
     if (beyond_rcut(W, dn, hn)) return 0;
     /* opening criterion (Barnes-Hut on cell side, distance to the group cell) */
     int64_t l = 2 * hn;
-    if (k >= t->lmin && (double)(l * l) < W->th2 * (double)sd) return push_entry(t, 1, n, sh);
+    if (k >= t->lmin && (double)(l * l) < walk_theta2(W, sd) * (double)sd) return push_entry(t, 1, n, sh);
     if (t->leaf[n]) {
         for (int64_t j = t->beg[n]; j < t->end[n]; j++) {
             /* the particle's finest cell, in the node's image */
@@ -510,7 +528,22 @@ static int walk_rec(walk_t *W, int64_t n)
 }
 
 /* Build lists for groups gsel[0..ns) (all groups when gsel == NULL). */
+static int lists_build(or_tree *t, double theta, int eq12, double theta0, const int64_t *gsel, int64_t ns);
+
+/* Lists with the constant opening angle theta. */
 int or_lists_build(or_tree *t, double theta, const int64_t *gsel, int64_t ns)
+{
+    return lists_build(t, theta, 0, 0.0, gsel, ns);
+}
+
+/* Lists with the distance-dependent opening angle of Eq. 12 (theta0), capped at theta_max. */
+int or_lists_build_eq12(or_tree *t, double theta0, double theta_max, const int64_t *gsel, int64_t ns)
+{
+    if (!(theta0 >= 0)) return -1;
+    return lists_build(t, theta_max, 1, theta0, gsel, ns);
+}
+
+static int lists_build(or_tree *t, double theta, int eq12, double theta0, const int64_t *gsel, int64_t ns)
 {
     if (!(theta >= 0)) return -1;
     if (!gsel) ns = t->ng;
@@ -526,6 +559,10 @@ int or_lists_build(or_tree *t, double theta, const int64_t *gsel, int64_t ns)
     W.uu = t->u * t->u;
     W.rc2 = t->r_cut * t->r_cut;
     W.th2 = theta * theta;
+    W.eq12 = eq12;
+    W.t02 = theta0 * theta0;
+    W.tmax2 = theta * theta;
+    W.u_over_eta = t->u / t->eta;
     for (int64_t s = 0; s < ns; s++) {
         int64_t g = gsel ? gsel[s] : s;
         if (g < 0 || g >= t->ng) return -1;

@@ -144,7 +144,49 @@ static long long max_s_le(double coef, double bound)
     return S;
 }
 
-static int derive_box(const greem_params &p, uint32_t pb, uint32_t pe, BoxPar &bp)
+// Eq. 2 on the host, both branches as printed (only the opening-angle thresholds use it).
+static double host_g_p3m(double R)
+{
+    if (R < 0.0) R = -R;
+    const double R2 = R * R, R3 = R2 * R, R4 = R3 * R, R5 = R4 * R, R6 = R5 * R, R7 = R6 * R, R8 = R7 * R;
+    if (R < 1.0) return 1.0 - (224.0 * R3 - 224.0 * R5 + 70.0 * R6 + 48.0 * R7 - 21.0 * R8) / 140.0;
+    if (R < 2.0)
+        return 1.0 - (12.0 - 224.0 * R2 + 896.0 * R3 - 840.0 * R4 + 224.0 * R5 + 70.0 * R6 - 48.0 * R7 + 7.0 * R8) /
+                         140.0;
+    return 0.0;
+}
+
+// The accept test of Eq. 12 (Sec. 4.1) for a node of side l (u) at squared distance S
+// (u^2): (double)(l*l) < theta(d)^2 * (double)S, theta(d)^2 = min(theta_max^2,
+// theta0^2 / (R g(R))), R = sqrt(S) u / eta, theta_max^2 where R g(R) = 0.
+static bool eq12_accept(long long l, long long S, double t02, double tmax2, double u_over_eta)
+{
+    const double R = std::sqrt((double)S) * u_over_eta;
+    const double rg = R * host_g_p3m(R);
+    double t2 = tmax2;
+    if (rg > 0.0) {
+        const double q = t02 / rg;
+        if (q < t2) t2 = q;
+    }
+    return (double)(l * l) < t2 * (double)S;
+}
+
+// Largest S for which a node of side l is NOT accepted under Eq. 12.  theta(d) d grows
+// with d (R / g(R) and d both increase), so the test is false below a threshold and true
+// above it, and a bisection over the integers finds it; LLONG_MAX if never accepted.
+static long long eq12_threshold(long long l, double t02, double tmax2, double u_over_eta)
+{
+    long long lo = 0, hi = 1LL << 46;  // beyond any squared distance in a box (3 * 2^42)
+    if (!eq12_accept(l, hi, t02, tmax2, u_over_eta)) return LLONG_MAX;
+    while (hi - lo > 1) {  // invariant: accept(lo) false (S = 0 never accepts), accept(hi) true
+        const long long mid = lo + (hi - lo) / 2;
+        if (eq12_accept(l, mid, t02, tmax2, u_over_eta)) hi = mid;
+        else lo = mid;
+    }
+    return lo;
+}
+
+static int derive_box(const greem_params &p, uint32_t pb, uint32_t pe, BoxPar &bp, bool eq12)
 {
     if (!(p.L > 0) || !std::isfinite(p.L)) return GREEM_ERR_INVALID_ARG;
     if (!(p.r_cut > 0) || !(p.r_cut < 0.5 * p.L)) return GREEM_ERR_INVALID_ARG;
@@ -182,11 +224,15 @@ static int derive_box(const greem_params &p, uint32_t pb, uint32_t pe, BoxPar &b
     bp.soft = p.eps > 0 ? 1 : 0;
     // r_cut pruning: prune iff (double)S_gap * (u*u) > r_cut*r_cut
     bp.T_prune = max_s_le(bp.u * bp.u, p.r_cut * p.r_cut);
-    // opening: accept iff (double)(l*l) < (theta*theta) * (double)S_d, l = 2^(22-k) u
+    // opening: accept iff (double)(l*l) < (theta*theta) * (double)S_d, l = 2^(22-k) u;
+    // with Eq. 12 theta(d) replaces theta (p.theta is then its upper limit)
     const double th2 = p.theta * p.theta;
+    if (eq12 && !(p.theta0 > 0 && std::isfinite(p.theta0))) return GREEM_ERR_INVALID_ARG;
     for (int k = 0; k <= kMaxLevel; k++) {
         const long long l = 1LL << (22 - k);
-        bp.A[k] = th2 > 0 ? max_s_le(th2, (double)(l * l)) : LLONG_MAX;
+        if (th2 <= 0) bp.A[k] = LLONG_MAX;
+        else if (eq12) bp.A[k] = eq12_threshold(l, p.theta0 * p.theta0, th2, bp.u / bp.eta);
+        else bp.A[k] = max_s_le(th2, (double)(l * l));
     }
     bp.p_begin = pb;
     bp.p_end = pe;
@@ -545,7 +591,7 @@ static int setup_single(greem_ctx *c, int64_t N, const greem_params *p)
     int rc = check_common(*p);
     if (rc) return rc;
     if ((rc = host_boxes(c, 1))) return rc;
-    if ((rc = derive_box(*p, 0, (uint32_t)N, c->bps_host[0]))) return rc;
+    if ((rc = derive_box(*p, 0, (uint32_t)N, c->bps_host[0], (p->flags & GREEM_FLAG_THETA_EQ12) != 0))) return rc;
     c->box_off_host[0] = 0;
     c->box_off_host[1] = (uint32_t)N;
     return GREEM_OK;
@@ -587,6 +633,7 @@ void greem_params_default(greem_params *p)
     p->n_crit = 64;
     p->n_leaf = 10;
     p->precision = GREEM_F32_REL;
+    p->theta0 = 0.25;
 }
 
 int greem_create(greem_ctx **out, void *cuda_stream)
@@ -696,7 +743,9 @@ int greem_short_force_batched(greem_ctx *c, int nbox, const int64_t *offsets, co
     if ((rc = host_boxes(c, nbox))) return rc;
     bool soft = false;
     for (int b = 0; b < nbox; b++) {
-        if ((rc = derive_box(per_box[b], (uint32_t)offsets[b], (uint32_t)offsets[b + 1], c->bps_host[b]))) return rc;
+        if ((rc = derive_box(per_box[b], (uint32_t)offsets[b], (uint32_t)offsets[b + 1], c->bps_host[b],
+                             (per_box[0].flags & GREEM_FLAG_THETA_EQ12) != 0)))
+            return rc;
         c->box_off_host[b] = (uint32_t)offsets[b];
         soft = soft || per_box[b].eps > 0;
     }

@@ -28,6 +28,7 @@ F64 = 1
 FLAG_INDEX_LISTS = 1
 FLAG_STAGE_TIMES = 2
 FLAG_ADD_PM = 4
+FLAG_THETA_EQ12 = 8
 ASSIGN_CIC = 0
 ASSIGN_TSC = 1
 
@@ -45,7 +46,8 @@ class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("r_cut", ctypes.c_double), ("theta", ctypes.c_double),
                 ("eps", ctypes.c_double), ("n_crit", ctypes.c_int), ("n_leaf", ctypes.c_int),
                 ("precision", ctypes.c_int), ("list_chunk", ctypes.c_int), ("block_shape", ctypes.c_int),
-                ("flags", ctypes.c_uint), ("n_pm", ctypes.c_int), ("assign", ctypes.c_int)]
+                ("flags", ctypes.c_uint), ("n_pm", ctypes.c_int), ("assign", ctypes.c_int),
+                ("theta0", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -127,13 +129,15 @@ def _dev(t, dtype, shape=None, name="tensor"):
 
 
 def params(L=1.0, r_cut=3.0 / 32, theta=0.5, n_crit=64, n_leaf=10, eps=0.0, precision=F32_REL, list_chunk=0,
-           block_shape=0, flags=0, n_pm=0, assign=ASSIGN_TSC) -> Params:
+           block_shape=0, flags=0, n_pm=0, assign=ASSIGN_TSC, theta0=None) -> Params:
     p = Params()
     _lib().greem_params_default(ctypes.byref(p))
     p.L, p.r_cut, p.theta, p.eps = float(L), float(r_cut), float(theta), float(eps)
     p.n_crit, p.n_leaf, p.precision = int(n_crit), int(n_leaf), int(precision)
     p.list_chunk, p.block_shape, p.flags = int(list_chunk), int(block_shape), int(flags)
     p.n_pm, p.assign = int(n_pm), int(assign)
+    if theta0 is not None:
+        p.theta0 = float(theta0)
     return p
 
 

@@ -306,3 +306,39 @@ def test_pairwise_fp32_error_e1(ctx):
     assert np.median(err) < 1e-5
     assert np.quantile(err, 0.99) < 1e-4
     assert np.all(a[r >= rc] == 0)
+
+
+# --------------------------------------------------------------------------- Eq. 12 opening angle
+@pytest.mark.parametrize("name,theta0,theta_max", [("clustered", 0.2, 0.8), ("nfw24", 0.25, 0.7),
+                                                   ("boxL3", 0.3, 1.0)])
+def test_eq12_lists_bit_exact_and_force(ctx, name, theta0, theta_max):
+    """Distance-dependent opening angle of Sec. 4.1 (Eq. 12), capped at theta_max: the GPU
+    applies it through per-level integer distance thresholds, the oracle node by node;
+    the lists must be identical and the force within the FP32 bounds."""
+    pos, mass, prm = CASES[name]()
+    prm = dict(prm, theta=theta_max)
+    if not prm.get("n_crit"):
+        prm["n_crit"] = 64
+    acc = gpu_force(ctx, pos, mass, prm, flags=greem.FLAG_INDEX_LISTS | greem.FLAG_THETA_EQ12, theta0=theta0)
+    T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm.get("n_leaf", 10))
+    T.build_lists(theta_max, theta0=theta0)
+    off, kind, idx, sh = T.lists()
+    assert np.array_equal(ctx.dump(greem.DUMP_LIST_OFFSETS), off)
+    gl = ctx.dump(greem.DUMP_LISTS)
+    assert np.array_equal(gl[:, 0], kind.astype(np.int64))
+    assert np.array_equal(gl[:, 1], idx)
+    assert np.array_equal(gl[:, 2:], sh.astype(np.int64))
+    # the variant changes the lists (else this test would not test it)
+    T2 = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm.get("n_leaf", 10))
+    T2.build_lists(theta_max)
+    assert T2.lists()[0][-1] != off[-1]
+    e = rel_err(acc, T.list_force_input_order())
+    assert np.median(e) <= MED_BOUND and np.quantile(e, 0.999) <= P999_BOUND
+
+
+def test_eq12_needs_a_positive_theta0(ctx):
+    pos, mass = clustered(300, 3)
+    with pytest.raises(greem.GreemError) as ei:
+        gpu_force(ctx, pos, mass, dict(L=1.0, r_cut=0.1, theta=0.7, n_crit=16),
+                  flags=greem.FLAG_THETA_EQ12, theta0=0.0)
+    assert ei.value.code == greem.ERR_INVALID_ARG
