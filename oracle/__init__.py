@@ -50,6 +50,13 @@ def lib():
             L.or_g_p3m.argtypes = [_dbl]
             L.or_pair_accel.restype = None
             L.or_pair_accel.argtypes = [_vp, _dbl, _dbl, _dbl, _vp]
+            for f in ("or_g_p3m_d1", "or_g_p3m_d2"):
+                getattr(L, f).restype = _dbl
+                getattr(L, f).argtypes = [_dbl]
+            L.or_quad_accel.restype = None
+            L.or_quad_accel.argtypes = [_vp, _vp, _dbl, _vp]
+            L.or_list_force_quad.restype = ctypes.c_int
+            L.or_list_force_quad.argtypes = [_vp, _vp, ctypes.c_int]
             L.or_wrap.restype = _dbl
             L.or_wrap.argtypes = [_dbl, _dbl]
             L.or_cell_index.restype = _i64
@@ -72,7 +79,7 @@ def lib():
             L.or_tree_lmin.argtypes = [_vp]
             L.or_tree_get_sorted.restype = None
             L.or_tree_get_sorted.argtypes = [_vp, _vp, _vp, _vp, _vp]
-            for f in ("or_tree_get_nodes", "or_tree_get_moments", "or_tree_get_groups"):
+            for f in ("or_tree_get_nodes", "or_tree_get_moments", "or_tree_get_groups", "or_tree_get_quadrupoles"):
                 getattr(L, f).restype = None
                 getattr(L, f).argtypes = [_vp, _vp]
             L.or_lists_build.restype = ctypes.c_int
@@ -110,6 +117,26 @@ def _mass(mass) -> np.ndarray:
 def g_p3m(R: float) -> float:
     """Eq. 2 cutoff function."""
     return lib().or_g_p3m(float(R))
+
+
+def g_p3m_d1(R: float) -> float:
+    """dg/dR of Eq. 2."""
+    return lib().or_g_p3m_d1(float(R))
+
+
+def g_p3m_d2(R: float) -> float:
+    """d^2g/dR^2 of Eq. 2."""
+    return lib().or_g_p3m_d2(float(R))
+
+
+def quad_accel(d, q, eta: float) -> np.ndarray:
+    """Second-order (quadrupole) part of the acceleration from a mass distribution with
+    second moments q = (xx, yy, zz, xy, xz, yz) about its COM at d = COM - x (Sec. 4.1)."""
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    qq = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros(3)
+    lib().or_quad_accel(_ptr(dd), _ptr(qq), float(eta), _ptr(out))
+    return out
 
 
 def pair_accel(d, m: float, eta: float, eps: float = 0.0) -> np.ndarray:
@@ -207,6 +234,12 @@ class Tree:
         lib().or_tree_get_moments(self._h, _ptr(out))
         return out
 
+    def quadrupoles(self) -> np.ndarray:
+        """[n_nodes, 6] float64: second moments xx, yy, zz, xy, xz, yz about the COM."""
+        out = np.zeros((self.n_nodes, 6))
+        lib().or_tree_get_quadrupoles(self._h, _ptr(out))
+        return out
+
     def groups(self) -> np.ndarray:
         out = np.zeros(self.n_groups, np.int64)
         lib().or_tree_get_groups(self._h, _ptr(out))
@@ -237,14 +270,20 @@ class Tree:
         lib().or_lists_get(self._h, _ptr(off), _ptr(kind), _ptr(idx), _ptr(sh))
         return off, kind, idx, sh
 
-    def list_force(self, eps: float = 0.0, nthreads: int = 0) -> np.ndarray:
-        """FP64 list force in SORTED order ([N,3]; particles of groups without lists are 0)."""
+    def list_force(self, eps: float = 0.0, nthreads: int = 0, quad: bool = False) -> np.ndarray:
+        """FP64 list force in SORTED order ([N,3]; particles of groups without lists are 0);
+        quad adds the second-order terms of node entries (Sec. 4.1; eps must be 0)."""
         acc = np.zeros((self.N, 3))
-        lib().or_list_force(self._h, float(eps), _ptr(acc), int(nthreads))
+        if quad:
+            if eps != 0.0:
+                raise ValueError("the quadrupole terms are for eps = 0")
+            lib().or_list_force_quad(self._h, _ptr(acc), int(nthreads))
+        else:
+            lib().or_list_force(self._h, float(eps), _ptr(acc), int(nthreads))
         return acc
 
-    def list_force_input_order(self, eps: float = 0.0, nthreads: int = 0) -> np.ndarray:
-        a = self.list_force(eps, nthreads)
+    def list_force_input_order(self, eps: float = 0.0, nthreads: int = 0, quad: bool = False) -> np.ndarray:
+        a = self.list_force(eps, nthreads, quad)
         _, perm, _, _ = self.sorted()
         out = np.zeros_like(a)
         out[perm] = a

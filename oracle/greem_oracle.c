@@ -76,6 +76,55 @@ double or_g_p3m(double R)
     return 0.0;
 }
 
+/* First and second derivatives of Eq. 2 in R, term by term from the printed branches
+ * (the quadrupole terms of Sec. 4.1 need the cutoff function's derivatives). */
+double or_g_p3m_d1(double R)
+{
+    if (R < 0.0) R = -R;
+    double R2 = R * R, R3 = R2 * R, R4 = R3 * R, R5 = R4 * R, R6 = R5 * R, R7 = R6 * R;
+    if (R < 1.0) return -(3.0 * 224.0 * R2 - 5.0 * 224.0 * R4 + 6.0 * 70.0 * R5 + 7.0 * 48.0 * R6 - 8.0 * 21.0 * R7) / 140.0;
+    if (R < 2.0)
+        return -(-2.0 * 224.0 * R + 3.0 * 896.0 * R2 - 4.0 * 840.0 * R3 + 5.0 * 224.0 * R4 + 6.0 * 70.0 * R5 -
+                 7.0 * 48.0 * R6 + 8.0 * 7.0 * R7) / 140.0;
+    return 0.0;
+}
+
+double or_g_p3m_d2(double R)
+{
+    if (R < 0.0) R = -R;
+    double R2 = R * R, R3 = R2 * R, R4 = R3 * R, R5 = R4 * R, R6 = R5 * R;
+    if (R < 1.0)
+        return -(6.0 * 224.0 * R - 20.0 * 224.0 * R3 + 30.0 * 70.0 * R4 + 42.0 * 48.0 * R5 - 56.0 * 21.0 * R6) / 140.0;
+    if (R < 2.0)
+        return -(-2.0 * 224.0 + 6.0 * 896.0 * R - 12.0 * 840.0 * R2 + 20.0 * 224.0 * R3 + 30.0 * 70.0 * R4 -
+                 42.0 * 48.0 * R5 + 56.0 * 7.0 * R6) / 140.0;
+    return 0.0;
+}
+
+/* Quadrupole part of the acceleration from a mass distribution with second moments
+ * q = (xx, yy, zz, xy, xz, yz) about its COM at separation d = COM - x (Sec. 4.1).  With
+ * the pair force m f(r) d/r, f(r) = g(r/eta)/r^2, and Phi' = f, the second-order Taylor
+ * term of sum_j m_j grad Phi(d + s_j) is
+ *   1/2 B tr(Q) d + 1/2 C (d.Q.d) d + B Q d,
+ *   A = f/r, B = A'/r = g'/(eta r^4) - 3 g/r^5, C = B'/r = g''/(eta^2 r^5) - 7 g'/(eta r^6) + 15 g/r^7,
+ * which for g = 1 is the Newtonian quadrupole.  eps must be 0. */
+void or_quad_accel(const double d[3], const double q[6], double eta, double out[3])
+{
+    out[0] = out[1] = out[2] = 0.0;
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2 == 0.0) return;
+    double r = sqrt(r2), R = r / eta;
+    double g = or_g_p3m(R), g1 = or_g_p3m_d1(R) / eta, g2 = or_g_p3m_d2(R) / (eta * eta);
+    double r4 = r2 * r2, r5 = r4 * r, r6 = r4 * r2, r7 = r6 * r;
+    double B = g1 / r4 - 3.0 * g / r5;
+    double C = g2 / r5 - 7.0 * g1 / r6 + 15.0 * g / r7;
+    double Qd[3] = {q[0] * d[0] + q[3] * d[1] + q[4] * d[2], q[3] * d[0] + q[1] * d[1] + q[5] * d[2],
+                    q[4] * d[0] + q[5] * d[1] + q[2] * d[2]};
+    double dQd = d[0] * Qd[0] + d[1] * Qd[1] + d[2] * Qd[2];
+    double tr = q[0] + q[1] + q[2];
+    for (int c = 0; c < 3; c++) out[c] = 0.5 * B * tr * d[c] + 0.5 * C * dQd * d[c] + B * Qd[c];
+}
+
 /* Eq. 1: acceleration on the evaluation point from a particle of mass m at
  * separation d = x_j - x_i (already the image to use).  G = 1.  eta = r_cut/2. */
 void or_pair_accel(const double d[3], double m, double eta, double eps, double out[3])
@@ -197,6 +246,7 @@ typedef struct {
     int64_t *beg, *end, *skip;
     int8_t *leaf;
     double *M, *cx, *cy, *cz;
+    double *Q;  /* [nn][6] second moments about the COM: xx, yy, zz, xy, xz, yz (Sec. 4.1) */
     /* groups (node indices, preorder) */
     int64_t ng;
     int64_t *grp;
@@ -238,6 +288,11 @@ static int grow_nodes(or_tree *t)
     RE(lvl, int32_t); RE(ix, int64_t); RE(iy, int64_t); RE(iz, int64_t);
     RE(beg, int64_t); RE(end, int64_t); RE(skip, int64_t); RE(leaf, int8_t);
     RE(M, double); RE(cx, double); RE(cy, double); RE(cz, double);
+    {
+        void *q = realloc(t->Q, sizeof(double) * 6 * (size_t)nc);
+        if (!q) return -3;
+        t->Q = (double *)q;
+    }
 #undef RE
     t->ncap = nc;
     return 0;
@@ -275,6 +330,21 @@ static int build_rec(or_tree *t, int level, int64_t b, int64_t e, int64_t ix, in
         t->cx[n] = ((double)ix + 0.5) * side;
         t->cy[n] = ((double)iy + 0.5) * side;
         t->cz[n] = ((double)iz + 0.5) * side;
+    }
+    /* second moments about the COM, by their definition (Sec. 4.1: second-order terms) */
+    {
+        double q[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t j = b; j < e; j++) {
+            double mj = (double)t->m[j];
+            double dx = t->x[j] - t->cx[n], dy = t->y[j] - t->cy[n], dz = t->z[j] - t->cz[n];
+            q[0] += mj * dx * dx;
+            q[1] += mj * dy * dy;
+            q[2] += mj * dz * dz;
+            q[3] += mj * dx * dy;
+            q[4] += mj * dx * dz;
+            q[5] += mj * dy * dz;
+        }
+        for (int c = 0; c < 6; c++) t->Q[6 * n + c] = q[c];
     }
     int64_t cnt = e - b;
     int split = level < OR_MAXLEVEL && (level < t->lmin || cnt >= t->n_leaf);
@@ -321,7 +391,7 @@ void or_tree_free(or_tree *t)
     if (!t) return;
     free(t->x); free(t->y); free(t->z); free(t->m); free(t->key); free(t->perm);
     free(t->lvl); free(t->ix); free(t->iy); free(t->iz); free(t->beg); free(t->end);
-    free(t->skip); free(t->leaf); free(t->M); free(t->cx); free(t->cy); free(t->cz);
+    free(t->skip); free(t->leaf); free(t->M); free(t->cx); free(t->cy); free(t->cz); free(t->Q);
     free(t->grp); free(t->lgrp); free(t->loff); free(t->ekind); free(t->eidx); free(t->esh);
     free(t);
 }
@@ -415,6 +485,12 @@ void or_tree_get_moments(const or_tree *t, double *out)
     for (int64_t n = 0; n < t->nn; n++) {
         out[4 * n] = t->M[n]; out[4 * n + 1] = t->cx[n]; out[4 * n + 2] = t->cy[n]; out[4 * n + 3] = t->cz[n];
     }
+}
+
+/* second moments: [nn, 6] double = xx, yy, zz, xy, xz, yz about the COM */
+void or_tree_get_quadrupoles(const or_tree *t, double *out)
+{
+    for (int64_t n = 0; n < 6 * t->nn; n++) out[n] = t->Q[n];
 }
 
 void or_tree_get_groups(const or_tree *t, int64_t *out)
@@ -611,7 +687,20 @@ void or_lists_get(const or_tree *t, int64_t *offsets, int8_t *kind, int64_t *idx
 /* Step 6: FP64 force from the lists, Eq. 1-2, per-pair minimum image against the
  * entry position (particle or node centre of mass).  acc_sorted gets [N,3] in
  * sorted order; only particles of groups with lists are written (others zero). */
+static int list_force(const or_tree *t, double eps, int quad, double *acc_sorted, int nthreads);
+
 int or_list_force(const or_tree *t, double eps, double *acc_sorted, int nthreads)
+{
+    return list_force(t, eps, 0, acc_sorted, nthreads);
+}
+
+/* The same with the second-order terms of Sec. 4.1 added for node entries (eps = 0). */
+int or_list_force_quad(const or_tree *t, double *acc_sorted, int nthreads)
+{
+    return list_force(t, 0.0, 1, acc_sorted, nthreads);
+}
+
+static int list_force(const or_tree *t, double eps, int quad, double *acc_sorted, int nthreads)
 {
     memset(acc_sorted, 0, sizeof(double) * 3 * (size_t)t->N);
 #ifdef _OPENMP
@@ -639,6 +728,12 @@ int or_list_force(const or_tree *t, double eps, double *acc_sorted, int nthreads
                 a[0] += f[0];
                 a[1] += f[1];
                 a[2] += f[2];
+                if (quad && t->ekind[e] == 1) {
+                    or_quad_accel(d, t->Q + 6 * j, t->eta, f);
+                    a[0] += f[0];
+                    a[1] += f[1];
+                    a[2] += f[2];
+                }
             }
             acc_sorted[3 * i] = a[0];
             acc_sorted[3 * i + 1] = a[1];

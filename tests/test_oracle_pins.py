@@ -532,3 +532,67 @@ def test_eq12_lowers_the_error_tail_at_equal_cost():
     assert abs(n_v / n_c - 1) < 0.05, (n_c, n_v)
     assert p99_v < 0.85 * p99_c, (p99_c, p99_v)
     assert rms_v < rms_c, (rms_c, rms_v)
+
+
+def test_g_derivatives_match_finite_differences():
+    """g' and g'' (needed by the second-order terms, Sec. 4.1) against centred differences
+    of Eq. 2 itself, on both branches and across R = 1; both vanish at R = 2."""
+    for R in np.concatenate([np.linspace(0.01, 0.99, 23), np.linspace(1.01, 1.99, 23)]):
+        h = 1e-5
+        d1 = (oracle.g_p3m(R + h) - oracle.g_p3m(R - h)) / (2 * h)
+        d2 = (oracle.g_p3m(R + h) - 2 * oracle.g_p3m(R) + oracle.g_p3m(R - h)) / (h * h)
+        assert oracle.g_p3m_d1(R) == pytest.approx(d1, abs=1e-8)
+        assert oracle.g_p3m_d2(R) == pytest.approx(d2, abs=2e-4)
+    for R in (1.0 - 1e-12, 1.0 + 1e-12):
+        assert oracle.g_p3m_d1(R) == pytest.approx(-1.0, abs=1e-9)
+    assert abs(oracle.g_p3m_d1(2.0 - 1e-9)) < 1e-30 and abs(oracle.g_p3m_d2(2.0 - 1e-9)) < 1e-20
+
+
+@pytest.mark.parametrize("R0", [0.4, 1.0, 1.6])
+def test_quadrupole_term_converges_at_third_order(R0):
+    """A small cloud of particles at distance R0*eta: the monopole's error against the
+    brute-force sum falls as (s/r)^2 with the cloud size s; with the second-order terms
+    of Sec. 4.1 it falls as (s/r)^3."""
+    rng = np.random.default_rng(int(R0 * 10))
+    eta = 0.05
+    base = rng.standard_normal((12, 3))
+    mass = rng.uniform(0.5, 1.5, 12)
+    direction = np.array([0.48, -0.6, 0.64])
+    errs_m, errs_q = [], []
+    for s in (0.02, 0.01, 0.005):
+        off = base * s * eta
+        off -= (mass[:, None] * off).sum(0) / mass.sum()
+        com = R0 * eta * direction
+        pts = com + off
+        exact = sum(oracle.pair_accel(p, m, eta) for p, m in zip(pts, mass))
+        mono = oracle.pair_accel(com, mass.sum(), eta)
+        q = np.array([np.sum(mass * off[:, a] * off[:, b]) for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))])
+        quad = mono + oracle.quad_accel(com, q, eta)
+        errs_m.append(np.linalg.norm(mono - exact))
+        errs_q.append(np.linalg.norm(quad - exact))
+    for k in range(2):
+        assert errs_m[k] / errs_m[k + 1] == pytest.approx(4.0, rel=0.1)
+        assert errs_q[k] / errs_q[k + 1] == pytest.approx(8.0, rel=0.15)
+    assert errs_q[-1] < 0.05 * errs_m[-1]
+
+
+def test_quadrupole_lowers_the_tree_error():
+    """Sec. 4.1: the second-order terms improve the accuracy a lot.  On a clustered set at
+    theta = 0.7 the 99th percentile and the RMS of the relative error against the
+    brute-force sum drop by more than 3x with the same lists (most particles' lists hold
+    only particles, so the median is at rounding level either way)."""
+    pos, m = _clustered(3000, 31)
+    L, rc = 1.0, 0.1
+    ref = oracle.direct(pos, m, L, rc)
+    t = oracle.Tree(pos, m, L, rc, n_crit=24)
+    t.build_lists(0.7)
+
+    def err(a):
+        n = np.linalg.norm(ref, axis=1)
+        keep = n > 1e-6 * np.median(n)
+        e = np.linalg.norm(a - ref, axis=1)[keep] / n[keep]
+        return np.sqrt(np.mean(e * e)), np.quantile(e, 0.99)
+
+    r0, p0 = err(t.list_force_input_order())
+    r1, p1 = err(t.list_force_input_order(quad=True))
+    assert r1 < r0 / 3 and p1 < p0 / 3, (r0, r1, p0, p1)
