@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the graph, theta-scan and batched lines")
     ap.add_argument("--config5", action="store_true",
                     help="time the 512^3 full TreePM step (PP + TSC PM on 512^3) in one CUDA graph instead")
+    ap.add_argument("--quad", action="store_true",
+                    help="with --profile-case: add the second-order (quadrupole) terms, theta = 0.7")
     ap.add_argument("--profile-case", choices=["nfw128", "zel256", "zel256tree"], default=None,
                     help="run --steps short-force calls on this workload (n_crit from --n-crit, else 128; "
                          "zel256tree: tree builds only, about 2 GB on the device) and print the stats; no "
@@ -210,8 +212,8 @@ def traffic_per_launch(list_entries):
 
 def extras(ctx, P, M, p, prm, acc, stream):
     """Context numbers beside the headline: CUDA-graph replay of the same step, the
-    opening-angle scan, the distance-dependent opening angle of Eq. 12, and the 64-box
-    batched workload (one call vs per-box calls)."""
+    opening-angle scan, the distance-dependent opening angle of Eq. 12, the second-order
+    terms, and the 64-box batched workload (one call vs per-box calls)."""
     import torch
     from paper_0910_0121_gb300 import greem, synth
     out = {}
@@ -261,6 +263,20 @@ def extras(ctx, P, M, p, prm, acc, stream):
     s = ctx.stats()
     out["theta_eq12"] = {"theta0": 0.25, "theta_max": 0.7, "ms_per_step": a.elapsed_time(b),
                          "N_int": s["n_interactions"] / N, "lists_ms": s["ms_lists"], "force_ms": s["ms_force"]}
+    # second-order (quadrupole) terms of Sec. 4.1 at theta = 0.5 and 0.7
+    quad = {}
+    for th in (0.5, 0.7):
+        q = greem.params(L=p.L, r_cut=p.r_cut, theta=th, n_crit=p.n_crit, n_leaf=p.n_leaf, list_chunk=p.list_chunk,
+                         block_shape=p.block_shape, flags=greem.FLAG_STAGE_TIMES | greem.FLAG_QUADRUPOLE)
+        ctx.short_force(P, M, q, acc)
+        a, b = ev(), ev()
+        a.record(stream)
+        ctx.short_force(P, M, q, acc)
+        b.record(stream)
+        torch.cuda.synchronize()
+        s = ctx.stats()
+        quad[str(th)] = {"ms_per_step": a.elapsed_time(b), "N_int": s["n_interactions"] / N, "force_ms": s["ms_force"]}
+    out["quadrupole"] = quad
     # 64 independent boxes: one batched call vs one call per box (FP32) and per-box FP64 calls
     bpos, bmass, boff, bprm = synth.config_batched()
     BP = torch.from_numpy(bpos).cuda()
@@ -506,8 +522,9 @@ def profile_case(args):
     M = torch.from_numpy(mass).cuda()
     ctx = greem.Context()
     acc = torch.empty((len(pos), 3), dtype=torch.float32, device="cuda")
-    p = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=args.n_crit or 128,
-                     n_leaf=prm["n_leaf"])
+    p = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=0.7 if args.quad else prm["theta"],
+                     n_crit=args.n_crit or 128, n_leaf=prm["n_leaf"],
+                     flags=greem.FLAG_QUADRUPOLE if args.quad else 0)
     for _ in range(args.steps):
         if args.profile_case == "zel256tree":
             ctx.build_tree(P, M, p)

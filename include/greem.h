@@ -58,6 +58,12 @@ extern "C" {
 #define GREEM_FLAG_ADD_PM 4u       /* add the PM (long-range) force of greem_pm_force, on n_pm^3 with
                                       the assign scheme, to acc in the same call (single box, FP32):
                                       the full TreePM force, Sec. 2.1 */
+#define GREEM_FLAG_QUADRUPOLE 16u  /* add the second-order (quadrupole) terms of accepted nodes,
+                                      with the derivatives of the cutoff function (Sec. 4.1):
+                                      1/2 B tr(Q) d + 1/2 C (d.Q.d) d + B Q d, B = A'/r, C = B'/r,
+                                      A = g(r/eta)/r^3, Q the node's second moments about its COM
+                                      (FP32).  FP32 precision and eps = 0 only (INVALID_ARG
+                                      otherwise); keeps the index lists as INDEX_LISTS does. */
 #define GREEM_FLAG_THETA_EQ12 8u   /* distance-dependent opening angle of Sec. 4.1, Eq. 12: a node is
                                       accepted iff l < theta(d) d with theta(d) = min(theta,
                                       theta0 / sqrt(R g(R))), R = d/eta, g of Eq. 2 (theta(d) = theta
@@ -187,6 +193,8 @@ int greem_get_stats(greem_ctx *ctx, greem_stats *out);
 #define GREEM_DUMP_LISTS 6     /* int64 [n_entries, 5]: kind (0 particle, 1 node), index (sorted
                                   particle or node), image shift x, y, z in units of L (needs
                                   GREEM_FLAG_INDEX_LISTS on the force call) */
+#define GREEM_DUMP_QUADRUPOLES 7 /* float64 [n_nodes, 6]: second moments xx, yy, zz, xy, xz, yz about
+                                    the COM (after a call with GREEM_FLAG_QUADRUPOLE) */
 /* Copies the array into host_buf when cap_bytes suffices; *len_bytes always gets the size.
  * Errors: INVALID_ARG (unknown what, no previous call, cap too small -> *len_bytes set). */
 int greem_debug_dump(greem_ctx *ctx, int what, void *host_buf, int64_t cap_bytes, int64_t *len_bytes);

@@ -48,6 +48,9 @@ struct greem_ctx {
     DBuf<Dbl4> raw, mom64;
     DBuf<float4> noff, poff, irel;
     DBuf<Group> groups;
+    DBuf<float4> quad, qlist;
+    DBuf<uint32_t> qcnt, qoff;
+    size_t qcap = 0;  // quadrupole-list entries
     DBuf<unsigned long long> pcell;
     DBuf<int4> gbox;
     // S5-S6
@@ -74,7 +77,7 @@ struct greem_ctx {
     uint32_t *perm = nullptr;
     uint32_t last_N = 0;
     int last_nbox = 0;
-    bool have_tree = false, have_lists = false, have_index = false;
+    bool have_tree = false, have_lists = false, have_index = false, have_quad = false;
     greem_stats stats;
 
     // PM
@@ -248,6 +251,8 @@ static int check_common(const greem_params &p)
     if (p.list_chunk != 0 && (p.list_chunk < 64 || p.list_chunk > 2048 || (p.list_chunk & (p.list_chunk - 1))))
         return GREEM_ERR_INVALID_ARG;
     if (p.block_shape < 0 || p.block_shape > 16) return GREEM_ERR_INVALID_ARG;
+    if ((p.flags & GREEM_FLAG_QUADRUPOLE) && (p.precision != GREEM_F32_REL || p.eps != 0.0))
+        return GREEM_ERR_INVALID_ARG;
     if (p.flags & GREEM_FLAG_ADD_PM) {
         if (p.precision != GREEM_F32_REL || p.n_pm < 8 || p.n_pm > 1024) return GREEM_ERR_INVALID_ARG;
         if (p.assign != GREEM_ASSIGN_CIC && p.assign != GREEM_ASSIGN_TSC) return GREEM_ERR_INVALID_ARG;
@@ -304,6 +309,7 @@ struct RunCfg {
     bool add_pm;
     int n_pm;
     int assign;
+    bool quad;
 };
 
 static int host_boxes(greem_ctx *c, int nbox)
@@ -367,6 +373,12 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
     ENS(gidx, nc + 1);
     ENS(groups, nc);
     ENS(gbox, nc * 2);
+    if (r.quad) {
+        ENS(quad, nc * 2);
+        ENS(qcnt, nc);
+        ENS(qoff, nc + 1);
+        ENS(qlist, c->qcap * 3);
+    }
     ENS(kids, nc * 8);
     ENS(lvl, 96);
     ENS(bps, (size_t)r.nbox);
@@ -426,6 +438,9 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
                         c->pcell.p, s);
     launch_node_finish(c->nodes.p, n_nodes, ncap, c->raw.p, c->box_off.p, nbox, c->bps.p, c->mom64.p, c->noff.p, s,
                        nsm);
+    if (r.quad)
+        launch_quadrupoles(c->nodes.p, n_nodes, ncap, c->kids.p, c->poff.p, c->noff.p, c->lvl.p, c->ctr.p,
+                           c->box_off.p, nbox, c->bps.p, c->quad.p, s, nsm);
     ev_record(c, r, ev, 3);
     launch_group_flags(c->nodes.p, n_nodes, ncap, c->box_off.p, nbox, c->bps.p, c->gflag.p, s, nsm);
     scan_u32(c->gflag.p, c->gidx.p, ncap, c->scratch.p, s);
@@ -454,13 +469,15 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
         la.loff = c->loff.p;
         la.llen = c->llen.p;
         la.lraw = c->lraw.p;
+        la.qcnt = r.quad ? c->qcnt.p : nullptr;
+        if (r.quad) cudaMemsetAsync(c->qcnt.p, 0, sizeof(uint32_t) * ncap, s);
         la.cap = c->list_cap;
         la.page = c->page;
         la.st = c->st.p;
         launch_lists(la, s, nsm);
         ev_record(c, r, ev, 5);
         launch_force_order(c->groups.p, n_groups, c->bins.p, c->order.p, s, nsm);
-        ForceArgs fa;
+        ForceArgs fa = {};
         fa.groups = c->groups.p;
         fa.n_groups = n_groups;
         fa.order = c->order.p;
@@ -483,6 +500,14 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
         fa.warps = r.warps;
         if (r.precision == GREEM_F64) launch_force_f64(fa, s, nsm);
         else launch_force_f32(fa, s, nsm, r.soft);
+        if (r.quad) {
+            scan_u32(c->qcnt.p, c->qoff.p, ncap, c->scratch.p, s);
+            fa.qoff = c->qoff.p;
+            fa.qcnt = c->qcnt.p;
+            fa.qlist = c->qlist.p;
+            launch_qlist_fill(fa, c->quad.p, c->qcap, s, nsm);
+            launch_force_f32(fa, s, nsm, false, true);
+        }
         if (r.add_pm) {
             const BoxPar &b0 = c->bps_host[0];
             if ((rc = pm_prepare(c, r.n_pm, b0.L, 2.0 * b0.eta, r.assign))) return rc;
@@ -534,10 +559,11 @@ static int finish(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     c->last_nbox = r.nbox;
     if (h.flags & ST_NONFINITE) return GREEM_ERR_INVALID_ARG;
     if (h.flags & ST_TIMEOUT) return GREEM_ERR_TIMEOUT;
-    if (h.flags & (ST_NODE_CAP | ST_LIST_CAP | ST_STACK)) return GREEM_ERR_CAPACITY;
+    if (h.flags & (ST_NODE_CAP | ST_LIST_CAP | ST_STACK | ST_QLIST_CAP)) return GREEM_ERR_CAPACITY;
     c->have_tree = true;
     c->have_lists = r.lists_force;
     c->have_index = r.lists_force && r.index_lists;
+    c->have_quad = r.quad;
     return GREEM_OK;
 }
 
@@ -545,6 +571,7 @@ static void grow_caps(greem_ctx *c)
 {
     const DevStatus &h = *c->st_host;
     if (h.flags & ST_NODE_CAP) c->node_cap = (size_t)(h.n_nodes * 1.15) + 4096;
+    if (h.flags & ST_QLIST_CAP) c->qcap = std::max<size_t>(c->qcap * 2, (size_t)(h.sum_quad * 1.25) + 4096);
     if (h.flags & ST_STACK) c->stack_cap *= 4;
     if (h.flags & ST_LIST_CAP) {
         // every allocation abandons less than the list that did not fit, and every warp
@@ -557,7 +584,7 @@ static void grow_caps(greem_ctx *c)
 
 static int run(greem_ctx *c, RunCfg r)
 {
-    c->have_tree = c->have_lists = c->have_index = false;
+    c->have_tree = c->have_lists = c->have_index = c->have_quad = false;
     // first guesses; an overflow grows them and the call is retried
     if (c->node_cap < (size_t)(r.N * 0.5) + 4096u * r.nbox) c->node_cap = (size_t)(r.N * 0.75) + 4096u * r.nbox;
     uint32_t pg = choose_page(r.N, c->nsm);
@@ -565,6 +592,8 @@ static int run(greem_ctx *c, RunCfg r)
     if (r.lists_force) {
         const size_t warps = (size_t)c->nsm * kListBlocksPerSM * kListWarps;
         c->list_cap = std::max<size_t>(c->list_cap, (size_t)r.N * 32 + warps * c->page);
+        // accepted nodes are a minority of the entries: a first guess of 4 per particle
+        if (r.quad) c->qcap = std::max<size_t>(c->qcap, (size_t)r.N * 4 + 4096);
     }
     cudaEvent_t ev[7] = {};
     if (r.timing)
@@ -607,7 +636,8 @@ static RunCfg make_cfg(const greem_params &p, const double *pos, const float *ma
     r.N = N;
     r.nbox = nbox;
     r.precision = p.precision;
-    r.index_lists = (p.flags & GREEM_FLAG_INDEX_LISTS) || p.precision == GREEM_F64;
+    r.quad = (p.flags & GREEM_FLAG_QUADRUPOLE) != 0;
+    r.index_lists = (p.flags & GREEM_FLAG_INDEX_LISTS) || p.precision == GREEM_F64 || r.quad;
     r.lists_force = lists_force;
     r.soft = false;
     r.timing = (p.flags & GREEM_FLAG_STAGE_TIMES) != 0;
@@ -672,7 +702,7 @@ void greem_destroy(greem_ctx *c)
     release(c->xs); release(c->ys); release(c->zs); release(c->ms);
     release(c->d8); release(c->K8); release(c->nchild); release(c->own); release(c->base); release(c->ctr);
     release(c->gflag); release(c->gidx); release(c->nodes); release(c->raw); release(c->mom64); release(c->noff);
-    release(c->poff); release(c->pcell); release(c->irel); release(c->groups); release(c->gbox);
+    release(c->poff); release(c->pcell); release(c->irel); release(c->groups); release(c->gbox); release(c->quad);
     release(c->flist); release(c->ilist); release(c->loff);
     release(c->llen); release(c->lraw); release(c->kids); release(c->stack); release(c->order); release(c->bins);
     release(c->lvl); release(c->bps); release(c->box_off); release(c->small); release(c->st);
@@ -752,6 +782,7 @@ int greem_short_force_batched(greem_ctx *c, int nbox, const int64_t *offsets, co
     c->box_off_host[nbox] = (uint32_t)N;
     RunCfg r = make_cfg(per_box[0], pos, mass, acc, (uint32_t)N, nbox, true);
     r.soft = soft;
+    if (r.quad && soft) return GREEM_ERR_INVALID_ARG;
     return run(c, r);
 }
 
@@ -833,7 +864,7 @@ int greem_graph_launch(greem_ctx *c)
     c->stats.n_evaluated = (int64_t)h.sum_eval;
     if (h.flags & ST_NONFINITE) return GREEM_ERR_INVALID_ARG;
     if (h.flags & ST_TIMEOUT) return GREEM_ERR_TIMEOUT;
-    if (h.flags & (ST_NODE_CAP | ST_LIST_CAP | ST_STACK)) return GREEM_ERR_CAPACITY;
+    if (h.flags & (ST_NODE_CAP | ST_LIST_CAP | ST_STACK | ST_QLIST_CAP)) return GREEM_ERR_CAPACITY;
     return GREEM_OK;
 }
 
@@ -908,6 +939,30 @@ int greem_debug_dump(greem_ctx *c, int what, void *host_buf, int64_t cap_bytes, 
             return GREEM_ERR_CUDA;
         int64_t *o = (int64_t *)host_buf;
         for (uint32_t g = 0; g < G; g++) o[g] = h[g].node;
+        return GREEM_OK;
+    }
+    case GREEM_DUMP_QUADRUPOLES: {
+        if (!c->have_quad) return GREEM_ERR_INVALID_ARG;
+        *len_bytes = (int64_t)nn * 6 * 8;
+        if (!host_buf || cap_bytes < *len_bytes) return GREEM_ERR_INVALID_ARG;
+        std::vector<float4> h((size_t)nn * 2);
+        std::vector<Node> hn(nn);
+        if (nn && (!cuda_ok(cudaMemcpy(h.data(), c->quad.p, (size_t)nn * 2 * sizeof(float4), cudaMemcpyDeviceToHost)) ||
+                   !cuda_ok(cudaMemcpy(hn.data(), c->nodes.p, (size_t)nn * sizeof(Node), cudaMemcpyDeviceToHost))))
+            return GREEM_ERR_CUDA;
+        double *o = (double *)host_buf;
+        int b = 0;
+        for (uint32_t n = 0; n < nn; n++) {
+            while (b + 1 < c->last_nbox && hn[n].begin >= c->box_off_host[b + 1]) b++;
+            const double e2 = c->bps_host[b].eta * c->bps_host[b].eta;  // eta^2 units -> physical
+            const float4 q0 = h[2 * (size_t)n], q1 = h[2 * (size_t)n + 1];
+            o[6 * n + 0] = q0.x * e2;
+            o[6 * n + 1] = q0.y * e2;
+            o[6 * n + 2] = q0.z * e2;
+            o[6 * n + 3] = q0.w * e2;
+            o[6 * n + 4] = q1.x * e2;
+            o[6 * n + 5] = q1.y * e2;
+        }
         return GREEM_OK;
     }
     case GREEM_DUMP_LIST_OFFSETS:
@@ -1143,7 +1198,7 @@ int greem_pair_force_f32(greem_ctx *c, const double *x_g, const double *x_i, con
     launch_force_f32(fa, s, c->nsm, eps > 0);
     cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
     if (!cuda_ok(cudaStreamSynchronize(s))) return GREEM_ERR_CUDA;
-    c->have_tree = c->have_lists = c->have_index = false;
+    c->have_tree = c->have_lists = c->have_index = c->have_quad = false;
     if (c->st_host->flags & ST_TIMEOUT) return GREEM_ERR_TIMEOUT;
     return GREEM_OK;
 }

@@ -69,6 +69,7 @@ struct DevStatus {
     unsigned long long sum_eval;       // pair evaluations of the force kernel
     unsigned long long sum_padded;     // sum of padded list lengths (the pool demand)
     unsigned long long work[4];        // persistent-kernel work queues
+    unsigned long long sum_quad;       // entries the quadrupole lists need (on overflow)
 };
 
 enum : unsigned {
@@ -77,6 +78,7 @@ enum : unsigned {
     ST_LIST_CAP = 4u,
     ST_TIMEOUT = 8u,
     ST_STACK = 16u,
+    ST_QLIST_CAP = 32u,
 };
 
 // Launch shape of the list builder (warps per block, blocks per SM): every warp may
@@ -171,6 +173,9 @@ void launch_tree_links(Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, 
 void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
                     const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw, uint32_t *lvl,
                     uint32_t *inodes, cudaStream_t s, int nsm);
+void launch_quadrupoles(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
+                        const float4 *poff, const float4 *noff, const uint32_t *lvl, const uint32_t *inodes,
+                        const uint32_t *box_off, int nbox, const BoxPar *bps, float4 *quad, cudaStream_t s, int nsm);
 void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
                          const BoxPar *bps, const double *xs, const double *ys, const double *zs, const float *ms,
                          float4 *poff, unsigned long long *pcell, cudaStream_t s);
@@ -207,6 +212,7 @@ struct ListArgs {
     unsigned long long *loff;  // per group: first entry
     uint32_t *llen;            // per group: padded length (multiple of 8)
     uint32_t *lraw;            // per group: unpadded length
+    uint32_t *qcnt;            // per group: accepted node entries (may be null)
     unsigned long long cap;    // entries in the pool
     uint32_t page;             // entries per page
     DevStatus *st;
@@ -226,6 +232,10 @@ struct ForceArgs {
     const float4 *irel;
     const uint32_t *perm;
     const BoxPar *bps;
+    // quadrupole passes: per group the first entry and count in qlist (three float4 each)
+    const uint32_t *qoff;
+    const uint32_t *qcnt;
+    const float4 *qlist;
     // FP64 form
     const double *xs, *ys, *zs;
     const float *ms;
@@ -237,7 +247,8 @@ struct ForceArgs {
 };
 void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t *bins, uint32_t *order,
                         cudaStream_t s, int nsm);
-void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft);
+void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft, bool quad = false);
+void launch_qlist_fill(const ForceArgs &a, const float4 *quad, unsigned long long qcap, cudaStream_t s, int nsm);
 void launch_force_f64(const ForceArgs &a, cudaStream_t s, int nsm);
 void launch_pair_setup(const double *xg, const double *xi, const double *xj, const float *mj, uint32_t np,
                        double inv_eta, Group *groups, float4 *irel, float4 *flist, unsigned long long *loff,

@@ -258,6 +258,55 @@ __device__ __forceinline__ void interact(const float4 j, const float (&xi)[I], c
     }
 }
 
+// ------------------------------------------------------------------ second-order terms
+// Quadrupole part of the force of an accepted node (Sec. 4.1), added by extra passes over
+// each group's list of accepted nodes.  With the pair force m f(r) D/r, f = g(R)/r^2, and
+// R, r, D in eta units, the second-order Taylor term of a node with second moments Q
+// about its COM is
+//   B (Q D + tr(Q)/2 D) + (C/2) (D.Q.D) D,   B = g'/R^4 - 3 g/R^5,  C = g''/R^5 - 7 g'/R^6 + 15 g/R^7.
+// From the factored form of Eq. 2 (g = v^5 C3(R) + u^6 P2(R), v = sat(1 - R/2), u = sat(1 - R)):
+//   B R^5 = v^4 F(R) + u^5 G(R),   (C/2) R^7 = v^3 H(R) + u^4 K(R),
+// with F, G, H, K the polynomials below (exact rationals; F(0)+G(0) = -3 and H(0)+K(0) =
+// 15/2 give the Newtonian quadrupole).  59 FP32 operations and one rsqrt per pair, scalar:
+// the constants stay immediates, and packed instructions would not save FP32-pipe cycles.
+// An entry is three float4: (x, y, z, M), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, tr(Q)/2, 0).
+__device__ __forceinline__ void quad_pair(float dx, float dy, float dz, const float4 q0, const float4 q1, float &ax,
+                                          float &ay, float &az)
+{
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    const float R = r2 * rinv;
+    const float v = fma_sat(R, -0.5f, 1.0f), u = add_sat(1.0f, -R);
+    const float v2 = v * v, v3 = v2 * v, v4 = v2 * v2;
+    const float u2 = u * u, u4 = u2 * u2, u5 = u4 * u;
+    const float F = fmaf(fmaf(fmaf(fmaf(R, -4.0f, -10.057142857142857f), R, -8.457142857142857f), R,
+                              -5.485714285714286f), R, -2.742857142857143f);
+    const float G = fmaf(fmaf(fmaf(R, -1.0f, -2.257142857142857f), R, -1.2857142857142858f), R, -0.2571428571428571f);
+    const float H = fmaf(fmaf(fmaf(fmaf(fmaf(R, 3.0f, 7.0285714285714285f), R, 12.17142857142857f), R,
+                                   12.685714285714285f), R, 10.285714285714286f), R, 6.857142857142857f);
+    const float K = fmaf(fmaf(fmaf(fmaf(R, 1.5f, 3.257142857142857f), R, 4.0285714285714285f), R, 2.5714285714285716f),
+                         R, 0.6428571428571429f);
+    const float ri2 = rinv * rinv, ri5 = ri2 * ri2 * rinv, ri7 = ri5 * ri2;
+    const float B = fmaf(v4, F, u5 * G) * ri5;
+    const float Ch = fmaf(v3, H, u4 * K) * ri7;
+    const float qx = fmaf(q0.x, dx, fmaf(q0.w, dy, q1.x * dz));
+    const float qy = fmaf(q0.w, dx, fmaf(q0.y, dy, q1.y * dz));
+    const float qz = fmaf(q1.x, dx, fmaf(q1.y, dy, q0.z * dz));
+    const float sd = Ch * fmaf(dx, qx, fmaf(dy, qy, dz * qz));
+    ax = fmaf(B, fmaf(q1.z, dx, qx), fmaf(sd, dx, ax));
+    ay = fmaf(B, fmaf(q1.z, dy, qy), fmaf(sd, dy, ay));
+    az = fmaf(B, fmaf(q1.z, dz, qz), fmaf(sd, dz, az));
+}
+
+template <int I>
+__device__ __forceinline__ void interact_quad(const float4 j, const float4 q0, const float4 q1, const float (&xi)[I],
+                                              const float (&yi)[I], const float (&zi)[I], float (&ax)[I],
+                                              float (&ay)[I], float (&az)[I])
+{
+#pragma unroll
+    for (int s = 0; s < I; s++) quad_pair(j.x - xi[s], j.y - yi[s], j.z - zi[s], q0, q1, ax[s], ay[s], az[s]);
+}
+
 // Lane layout of one pass: S parts of li = 32/S lanes, I i-particles per lane; the pass
 // covers li*I of the group's remaining particles.  Cost model of a pass over a list of
 // len entries, in warp cycles: each lane takes len/S entries at I*w + o cycles each (w =
@@ -323,27 +372,74 @@ __device__ __forceinline__ void choose_layout(uint32_t n, int &S, int &I)
     I = (int)(v & 15u);
 }
 
+// Layout of a second-order pass: I in {1, 2, 4} only (the pair body is long, and fewer
+// instantiations keep the instruction cache warm), the fewest slots li*I >= n (ties: more
+// parts); when that wastes more than n/4 slots and n > 32, the largest slot count <= n.
+__device__ __forceinline__ void choose_layout_quad(uint32_t n, int &S, int &I)
+{
+    if (n >= 128u) {
+        S = 1;
+        I = 4;
+        return;
+    }
+    int bs = 1, bi = 4;
+    uint32_t best = 0xffffffffu;
+#pragma unroll
+    for (int s = 32; s >= 1; s >>= 1) {
+#pragma unroll
+        for (int i = 1; i <= 4; i <<= 1) {
+            const uint32_t slots = (32u / s) * (uint32_t)i;
+            if (slots >= n && slots < best) {
+                best = slots;
+                bs = s;
+                bi = i;
+            }
+        }
+    }
+    if (n > 32u && best - n > n / 4u) {
+        uint32_t lo = 0;
+#pragma unroll
+        for (int s = 32; s >= 1; s >>= 1) {
+#pragma unroll
+            for (int i = 1; i <= 4; i <<= 1) {
+                const uint32_t slots = (32u / s) * (uint32_t)i;
+                if (slots <= n && slots > lo) {
+                    lo = slots;
+                    bs = s;
+                    bi = i;
+                }
+            }
+        }
+    }
+    S = bs;
+    I = bi;
+}
+
 struct WarpPipe {
     float4 *buf[2];
     uint64_t *bar;
     uint32_t ph[2];
 };
 
-__device__ __forceinline__ void issue_chunk(const ForceArgs &a, WarpPipe &wp, int b, unsigned long long lo,
-                                            uint32_t c, uint32_t len, int lane)
+// Stages entries [c*ce, min((c+1)*ce, len)) of a list (stride float4 per entry, starting
+// at float4 lo of src) into buffer b.
+__device__ __forceinline__ void issue_chunk(const float4 *src, uint32_t ce, uint32_t stride, WarpPipe &wp, int b,
+                                            unsigned long long lo, uint32_t c, uint32_t len, int lane)
 {
     if (lane == 0) {
-        const uint32_t first = c * (uint32_t)a.chunk;
-        const uint32_t nj = min((uint32_t)a.chunk, len - first);
-        const uint32_t bytes = nj * (uint32_t)sizeof(float4);
+        const uint32_t first = c * ce;
+        const uint32_t nj = min(ce, len - first);
+        const uint32_t bytes = nj * stride * (uint32_t)sizeof(float4);
         fence_proxy_async();
         mbar_arrive_tx(&wp.bar[b], bytes);
-        bulk_g2s(wp.buf[b], a.flist + lo + first, bytes, &wp.bar[b]);
+        bulk_g2s(wp.buf[b], src + lo + (unsigned long long)first * stride, bytes, &wp.bar[b]);
     }
 }
 
-// One pass of a group: I i-particles per lane, S parts; returns false on a timeout.
-template <int I, bool SOFT>
+// One pass of a group: I i-particles per lane, S parts; returns false on a timeout.  QUAD:
+// the pass runs over the group's accepted nodes (three float4 per entry) and adds their
+// second-order terms to the accelerations the monopole passes stored.
+template <int I, bool SOFT, bool QUAD>
 __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uint32_t done, int S,
                                         unsigned long long lo, uint32_t len, WarpPipe &wp, float inv_eta2, float eps2,
                                         int lane)
@@ -364,7 +460,10 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
         zi[s] = v.z;
         ax[s] = ay[s] = az[s] = 0.f;
     }
-    constexpr bool kPacked = (I % 2) == 0;
+    constexpr bool kPacked = !QUAD && (I % 2) == 0;
+    constexpr uint32_t stride = QUAD ? 3u : 1u;
+    const uint32_t ce = QUAD ? (uint32_t)a.chunk / 4u : (uint32_t)a.chunk;
+    const float4 *src = QUAD ? a.qlist : a.flist;
     constexpr int H = kPacked ? I / 2 : 1;
     f32x2 xi2[H], yi2[H], zi2[H], ax2[H], ay2[H], az2[H];
     const f32x2 eps2x2 = pk(eps2, eps2);
@@ -377,12 +476,12 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
             ax2[h] = ay2[h] = az2[h] = pk(0.f, 0.f);
         }
     }
-    const uint32_t nch = (len + (uint32_t)a.chunk - 1) / (uint32_t)a.chunk;
-    if (nch) issue_chunk(a, wp, 0, lo, 0, len, lane);
+    const uint32_t nch = (len + ce - 1) / ce;
+    if (nch) issue_chunk(src, ce, stride, wp, 0, lo, 0, len, lane);
     bool ok = true;
     for (uint32_t c = 0; c < nch; c++) {
         const int b = (int)(c & 1u);
-        if (c + 1 < nch) issue_chunk(a, wp, b ^ 1, lo, c + 1, len, lane);
+        if (c + 1 < nch) issue_chunk(src, ce, stride, wp, b ^ 1, lo, c + 1, len, lane);
         const bool got = mbar_wait_bounded(&wp.bar[b], wp.ph[b]);
         wp.ph[b] ^= 1u;
         if (!__all_sync(FULL, got)) {
@@ -395,8 +494,12 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
             break;
         }
         const float4 *buf = wp.buf[b];
-        const uint32_t nj = min((uint32_t)a.chunk, len - c * (uint32_t)a.chunk);
-        if constexpr (kPacked) {
+        const uint32_t nj = min(ce, len - c * ce);
+        if constexpr (QUAD) {
+#pragma unroll 1
+            for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S)
+                interact_quad<I>(buf[3 * t], buf[3 * t + 1], buf[3 * t + 2], xi, yi, zi, ax, ay, az);
+        } else if constexpr (kPacked) {
 #pragma unroll(kUnroll)
             for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S) {
                 const float4 j = buf[t];
@@ -440,16 +543,24 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
             const uint32_t idx = gr.begin + done + (uint32_t)(s * li + slot);
             if (idx < gend) {
                 const size_t p = (size_t)a.perm[idx] * 3;
-                acc[p] = ax[s] * inv_eta2;
-                acc[p + 1] = ay[s] * inv_eta2;
-                acc[p + 2] = az[s] * inv_eta2;
+                if (QUAD) {
+                    acc[p] += ax[s] * inv_eta2;
+                    acc[p + 1] += ay[s] * inv_eta2;
+                    acc[p + 2] += az[s] * inv_eta2;
+                } else {
+                    acc[p] = ax[s] * inv_eta2;
+                    acc[p + 1] = ay[s] * inv_eta2;
+                    acc[p + 2] = az[s] * inv_eta2;
+                }
             }
         }
     }
     return ok;
 }
 
-template <bool SOFT>
+// QUAD: the second-order passes over the groups' accepted nodes (after the monopole
+// launch; groups without accepted nodes are skipped).
+template <bool SOFT, bool QUAD>
 __global__ void __launch_bounds__(GREEM_FORCE_THREADS, GREEM_FORCE_MINB) k_force_f32(ForceArgs a)
 {
     extern __shared__ __align__(128) float4 sm[];
@@ -468,40 +579,52 @@ __global__ void __launch_bounds__(GREEM_FORCE_THREADS, GREEM_FORCE_MINB) k_force
     }
     __syncwarp();
     if (a.st->flags & ST_NODE_CAP) return;  // the tree was truncated: the call is retried
+    // the quadrupole lists are incomplete (and would be read past their end): the call is
+    // retried with larger lists
+    if (QUAD && (a.st->flags & (ST_LIST_CAP | ST_QLIST_CAP))) return;
     const uint32_t G = *a.n_groups;
     for (;;) {
         unsigned long long gi = 0;
-        if (lane == 0) gi = atomicAdd(&a.st->work[1], 1ull);
+        if (lane == 0) gi = atomicAdd(&a.st->work[QUAD ? 3 : 1], 1ull);
         gi = __shfl_sync(FULL, gi, 0);
         if (gi >= G) break;
         const uint32_t g = a.order ? a.order[gi] : (uint32_t)gi;
         const Group gr = a.groups[g];
         const BoxPar &bp = a.bps[gr.box];
         const float inv_eta2 = bp.inv_eta2, eps2 = bp.eps2;
-        const unsigned long long lo = a.loff[g];
-        const uint32_t len = a.llen[g];
+        const unsigned long long lo = QUAD ? 3ull * a.qoff[g] : a.loff[g];
+        const uint32_t len = QUAD ? a.qcnt[g] : a.llen[g];
+        if (QUAD && len == 0) continue;
         uint32_t done = 0;
         unsigned long long evals = 0;
         bool ok = true;
         while (done < gr.count && ok) {
             int S, I;
+            if (QUAD) {
+                choose_layout_quad(gr.count - done, S, I);
+                if (I == 1) ok = group_pass<1, SOFT, true>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane);
+                else if (I == 2) ok = group_pass<2, SOFT, true>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane);
+                else ok = group_pass<4, SOFT, true>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane);
+                done += (uint32_t)(32 / S) * (uint32_t)I;
+                continue;
+            }
             choose_layout(gr.count - done, S, I);
             switch (I) {
-            case 1: ok = group_pass<1, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
-            case 2: ok = group_pass<2, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
-            case 3: ok = group_pass<3, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
-            case 4: ok = group_pass<4, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 1: ok = group_pass<1, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 2: ok = group_pass<2, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 3: ok = group_pass<3, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 4: ok = group_pass<4, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
 #if GREEM_FORCE_IMAX >= 5
-            case 5: ok = group_pass<5, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 5: ok = group_pass<5, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
 #endif
 #if GREEM_FORCE_IMAX >= 6
-            case 6: ok = group_pass<6, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 6: ok = group_pass<6, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
 #endif
 #if GREEM_FORCE_IMAX >= 7
-            case 7: ok = group_pass<7, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 7: ok = group_pass<7, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
 #endif
 #if GREEM_FORCE_IMAX >= 8
-            case 8: ok = group_pass<8, SOFT>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 8: ok = group_pass<8, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
 #endif
             default: ok = false; break;  // not reachable: choose_layout never exceeds kImax
             }
@@ -509,12 +632,61 @@ __global__ void __launch_bounds__(GREEM_FORCE_THREADS, GREEM_FORCE_MINB) k_force
             evals += (unsigned long long)slots * len;
             done += slots;
         }
-        if (lane == 0) atomicAdd(&a.st->sum_eval, evals);
+        if (!QUAD && lane == 0) atomicAdd(&a.st->sum_eval, evals);
         if (!ok) {
             if (lane == 0) atomicOr(&a.st->flags, ST_TIMEOUT);
             break;
         }
     }
+}
+
+// The accepted nodes of each group's list, compacted in list order into the group's
+// stretch [qoff[g], qoff[g] + qcnt[g]) of the quadrupole list (three float4 per entry:
+// the list entry, then the node's second moments).  One warp per group.  An overflow of
+// qcap entries records the total needed and the call is retried with a larger list.
+__global__ void __launch_bounds__(256) k_qlist_fill(ForceArgs a, const float4 *__restrict__ quad, unsigned long long qcap)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    if (a.st->flags & (ST_NODE_CAP | ST_LIST_CAP)) return;
+    const uint32_t G = *a.n_groups;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long need = a.qoff[G];
+        if (need > qcap) {
+            a.st->sum_quad = need;
+            atomicOr(&a.st->flags, ST_QLIST_CAP);
+        }
+    }
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
+        const unsigned long long lo = a.loff[g];
+        const uint32_t len = a.lraw[g];
+        const unsigned long long q0 = a.qoff[g];
+        if (q0 + a.qcnt[g] > qcap) continue;
+        uint32_t k = 0;
+        for (uint32_t e0 = 0; e0 < len; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            unsigned long long ie = 0;
+            if (e < len) ie = a.ilist[lo + e];
+            const bool node = e < len && ((ie >> 32) & 1ull) != 0;
+            const unsigned bal = __ballot_sync(FULL, node);
+            if (node) {
+                const uint32_t n = (uint32_t)(ie & 0xffffffffull);
+                float4 *d = const_cast<float4 *>(a.qlist) + 3ull * (q0 + k + __popc(bal & lt));
+                d[0] = a.flist[lo + e];
+                d[1] = quad[2 * (size_t)n];
+                d[2] = quad[2 * (size_t)n + 1];
+            }
+            k += __popc(bal);
+        }
+    }
+}
+
+void launch_qlist_fill(const ForceArgs &a, const float4 *quad, unsigned long long qcap, cudaStream_t s, int nsm)
+{
+    k_qlist_fill<<<nsm * 8, 256, 0, s>>>(a, quad, qcap);
+    g_launches++;
 }
 
 // ------------------------------------------------------------------ work order
@@ -589,21 +761,21 @@ void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t 
     g_launches += 3;
 }
 
-static int g_force_smem_set[2] = {0, 0};
+static int g_force_smem_set[3] = {0, 0, 0};
 
-void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft)
+void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft, bool quad)
 {
     const int threads = 32 * a.warps;
     const size_t smem = (size_t)a.warps * 2 * a.chunk * sizeof(float4);
-    auto kern = soft ? k_force_f32<true> : k_force_f32<false>;
-    const int which = soft ? 1 : 0;
+    auto kern = quad ? k_force_f32<false, true> : (soft ? k_force_f32<true, false> : k_force_f32<false, false>);
+    const int which = quad ? 2 : (soft ? 1 : 0);
     if (g_force_smem_set[which] < (int)smem) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         g_force_smem_set[which] = 200 * 1024;
     }
     // occupancy is queried once per shape (not while a stream is being captured)
-    static int cached[2][17][2] = {};
-    static size_t cached_smem[2][17] = {};
+    static int cached[3][17][2] = {};
+    static size_t cached_smem[3][17] = {};
     int &per_sm = cached[which][a.warps][0];
     if (cached_smem[which][a.warps] != smem || per_sm == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);

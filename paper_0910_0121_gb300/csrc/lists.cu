@@ -123,10 +123,11 @@ __device__ __forceinline__ int owner_lane(uint32_t off, uint32_t t)
 // goes through the per-particle r_cut test unless its whole leaf lies within r_cut.
 __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb, const int4 th, const BoxPar &bp,
                                uint32_t root, uint32_t *__restrict__ stk, unsigned long long pos0,
-                               unsigned long long lim, int lane)
+                               unsigned long long lim, int lane, uint32_t &nacc)
 {
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
+    nacc = 0;
     const uint32_t gend = gr.begin + gr.count;
     const long long Tp = bp.T_prune;
     const int lmin = bp.lmin;
@@ -195,6 +196,7 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
                 }
             }
             cnt += __popc(ab);
+            nacc += __popc(ab);
             const unsigned pb = __ballot_sync(FULL, push);
             if (sp + __popc(pb) > cap) {
                 if (lane == 0) atomicOr(&a.st->flags, ST_STACK);
@@ -293,7 +295,8 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
         const int4 tb = a.gbox[2 * (size_t)g], th = a.gbox[2 * (size_t)g + 1];
         const BoxPar &bp = a.bps[gr.box];
         const uint32_t root = a.base[bp.p_begin];
-        const uint32_t len = walk_group(a, gr, tb, th, bp, root, stk, page_cur, page_end, lane);
+        uint32_t nacc = 0;
+        const uint32_t len = walk_group(a, gr, tb, th, bp, root, stk, page_cur, page_end, lane, nacc);
         const uint32_t padded = (len + 7u) & ~7u;
         if (lane == 0) atomicAdd(&a.st->sum_padded, (unsigned long long)padded);
         if (exhausted) {
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
             }
             page_cur = first * a.page;
             page_end = (first + np) * a.page;
-            walk_group(a, gr, tb, th, bp, root, stk, page_cur, page_end, lane);
+            walk_group(a, gr, tb, th, bp, root, stk, page_cur, page_end, lane, nacc);
         }
         for (uint32_t t = len + lane; t < padded; t += 32) {
             a.flist[page_cur + t] = make_float4(16.f, 16.f, 16.f, 0.f);
@@ -333,6 +336,7 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
             a.loff[g] = page_cur;
             a.llen[g] = padded;
             a.lraw[g] = len;
+            if (a.qcnt) a.qcnt[g] = nacc;
             atomicAdd(&a.st->sum_len, (unsigned long long)len);
             atomicAdd(&a.st->sum_inter, (unsigned long long)len * gr.count);
         }

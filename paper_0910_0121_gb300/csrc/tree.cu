@@ -305,6 +305,97 @@ void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_ca
     }
 }
 
+// Second moments about the COM (the second-order terms of Sec. 4.1), FP32 in eta^2 units,
+// as two float4 per node: (xx, yy, zz, xy), (xz, yz, (xx+yy+zz)/2, 0).  A leaf sums
+// m (p - c)(p - c)^T over its particles, p the particle's offset from the leaf's cell
+// centre and c the COM's (both already in eta units).  An internal node adds its
+// children's moments moved to its own COM (parallel axes): Q_c + M_c d_c d_c^T, d_c =
+// child COM - node COM, from the exact cell-centre difference and the COM offsets.
+__device__ __forceinline__ void quad_store(float4 *__restrict__ quad, uint32_t n, const float q[6])
+{
+    quad[2 * (size_t)n] = make_float4(q[0], q[1], q[2], q[3]);
+    quad[2 * (size_t)n + 1] = make_float4(q[4], q[5], 0.5f * (q[0] + q[1] + q[2]), 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_quad_leaf(const Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
+                                                   uint32_t node_cap, const float4 *__restrict__ poff,
+                                                   const float4 *__restrict__ noff, float4 *__restrict__ quad)
+{
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
+        const Node nd = nodes[n];
+        if (!(nd.lvl & 256u)) continue;
+        const float4 c = noff[n];
+        float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (uint32_t j = nd.begin; j < nd.end; j++) {
+            const float4 p = poff[j];
+            const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+            const float mx = p.w * dx, my = p.w * dy, mz = p.w * dz;
+            q[0] = fmaf(mx, dx, q[0]);
+            q[1] = fmaf(my, dy, q[1]);
+            q[2] = fmaf(mz, dz, q[2]);
+            q[3] = fmaf(mx, dy, q[3]);
+            q[4] = fmaf(mx, dz, q[4]);
+            q[5] = fmaf(my, dz, q[5]);
+        }
+        quad_store(quad, n, q);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_quad_level(int level, const uint32_t *__restrict__ lvl,
+                                                    const uint32_t *__restrict__ inodes,
+                                                    const Node *__restrict__ nodes, const uint32_t *__restrict__ kids,
+                                                    const float4 *__restrict__ noff,
+                                                    const uint32_t *__restrict__ box_off, int nbox,
+                                                    const BoxPar *__restrict__ bps, float4 *__restrict__ quad)
+{
+    const uint32_t b = lvl[32 + level], e = b + lvl[level];
+    for (uint32_t i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
+        const uint32_t p = inodes[i];
+        const Node np = nodes[p];
+        const float kf = bps[box_of(np.begin, box_off, nbox)].k_f;
+        const int hp = 1 << (kMaxLevel - level);
+        const float4 cp = noff[p];
+        float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const uint4 *kp = reinterpret_cast<const uint4 *>(kids + (size_t)p * 8);
+        const uint4 k0 = kp[0], k1 = kp[1];
+        const uint32_t kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            const uint32_t c = kk[t];
+            if (c == kNone) break;
+            const Node nc = nodes[c];
+            const int hc = hp >> 1;
+            const float4 cc = noff[c];
+            // child COM - node COM: cell-centre difference (exact integer in u) and COM offsets
+            const float dx = fmaf((float)(2 * ((int)nc.ix - (int)np.ix) + hc - hp), kf, cc.x - cp.x);
+            const float dy = fmaf((float)(2 * ((int)nc.iy - (int)np.iy) + hc - hp), kf, cc.y - cp.y);
+            const float dz = fmaf((float)(2 * ((int)nc.iz - (int)np.iz) + hc - hp), kf, cc.z - cp.z);
+            const float4 q0 = quad[2 * (size_t)c], q1 = quad[2 * (size_t)c + 1];
+            const float mx = cc.w * dx, my = cc.w * dy, mz = cc.w * dz;
+            q[0] += fmaf(mx, dx, q0.x);
+            q[1] += fmaf(my, dy, q0.y);
+            q[2] += fmaf(mz, dz, q0.z);
+            q[3] += fmaf(mx, dy, q0.w);
+            q[4] += fmaf(mx, dz, q1.x);
+            q[5] += fmaf(my, dz, q1.y);
+        }
+        quad_store(quad, p, q);
+    }
+}
+
+void launch_quadrupoles(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
+                        const float4 *poff, const float4 *noff, const uint32_t *lvl, const uint32_t *inodes,
+                        const uint32_t *box_off, int nbox, const BoxPar *bps, float4 *quad, cudaStream_t s, int nsm)
+{
+    k_quad_leaf<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, poff, noff, quad);
+    g_launches++;
+    for (int level = kMaxLevel - 1; level >= 0; level--) {
+        k_quad_level<<<nsm * 4, 256, 0, s>>>(level, lvl, inodes, nodes, kids, noff, box_off, nbox, bps, quad);
+        g_launches++;
+    }
+}
+
 // Each particle's offset from the centre of its leaf cell (level K_i) in eta units: the
 // FP64 subtraction is done once per particle, then rounded to FP32 for the list builder.
 __global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ K8,

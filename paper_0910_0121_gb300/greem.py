@@ -29,10 +29,11 @@ FLAG_INDEX_LISTS = 1
 FLAG_STAGE_TIMES = 2
 FLAG_ADD_PM = 4
 FLAG_THETA_EQ12 = 8
+FLAG_QUADRUPOLE = 16
 ASSIGN_CIC = 0
 ASSIGN_TSC = 1
 
-DUMP_KEYS, DUMP_PERM, DUMP_NODES, DUMP_MOMENTS, DUMP_GROUPS, DUMP_LIST_OFFSETS, DUMP_LISTS = range(7)
+DUMP_KEYS, DUMP_PERM, DUMP_NODES, DUMP_MOMENTS, DUMP_GROUPS, DUMP_LIST_OFFSETS, DUMP_LISTS, DUMP_QUADRUPOLES = range(8)
 
 
 class GreemError(RuntimeError):
@@ -291,6 +292,8 @@ class Context:
             return raw.view(np.int64).copy()
         if what == DUMP_LISTS:
             return raw.view(np.int64).reshape(-1, 5).copy()
+        if what == DUMP_QUADRUPOLES:
+            return raw.view(np.float64).reshape(-1, 6).copy()
         raise ValueError(what)
 
 

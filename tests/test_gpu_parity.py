@@ -342,3 +342,40 @@ def test_eq12_needs_a_positive_theta0(ctx):
         gpu_force(ctx, pos, mass, dict(L=1.0, r_cut=0.1, theta=0.7, n_crit=16),
                   flags=greem.FLAG_THETA_EQ12, theta0=0.0)
     assert ei.value.code == greem.ERR_INVALID_ARG
+
+
+# --------------------------------------------------------------------------- second-order terms
+@pytest.mark.parametrize("name,theta", [("clustered", 0.7), ("nfw24", 0.6), ("boxL3", 0.7), ("uniform32", 0.8)])
+def test_quadrupole_moments_and_force(ctx, name, theta):
+    """GREEM_FLAG_QUADRUPOLE (Sec. 4.1): FP32 second moments against the oracle's FP64
+    ones (to 2e-5 of M * side^2 per component), and the force with the second-order terms
+    against the oracle's on identical lists, within the FP32 bounds."""
+    pos, mass, prm = CASES[name]()
+    prm = dict(prm, theta=theta)
+    if not prm.get("n_crit"):
+        prm["n_crit"] = 64
+    acc = gpu_force(ctx, pos, mass, prm, flags=greem.FLAG_QUADRUPOLE)
+    T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm.get("n_leaf", 10))
+    T.build_lists(theta)
+    gq = ctx.dump(greem.DUMP_QUADRUPOLES)
+    oq = T.quadrupoles()
+    nodes, mom = T.nodes(), T.moments()
+    scale = mom[:, 0] * (prm["L"] / 2.0 ** nodes[:, 0]) ** 2
+    assert gq.shape == oq.shape
+    assert np.all(np.abs(gq - oq) <= 2e-5 * scale[:, None] + 1e-30)
+    ref = T.list_force_input_order(quad=True)
+    e = rel_err(acc, ref)
+    assert np.median(e) <= MED_BOUND and np.quantile(e, 0.999) <= P999_BOUND, (np.median(e), np.quantile(e, 0.999))
+    # the terms matter on these lists: the monopole-only force is farther from the reference
+    e0 = rel_err(gpu_force(ctx, pos, mass, prm), ref)
+    assert np.quantile(e0, 0.99) > 10 * np.quantile(e, 0.99)
+
+
+def test_quadrupole_needs_fp32_and_no_softening(ctx):
+    pos, mass = clustered(300, 3)
+    prm = dict(L=1.0, r_cut=0.1, theta=0.7, n_crit=16)
+    for kw in (dict(eps=1e-3), dict(precision=greem.F64)):
+        with pytest.raises(greem.GreemError) as ei:
+            gpu_force(ctx, pos, mass, dict(prm, **{k: v for k, v in kw.items() if k == "eps"}),
+                      precision=kw.get("precision", greem.F32_REL), flags=greem.FLAG_QUADRUPOLE)
+        assert ei.value.code == greem.ERR_INVALID_ARG

@@ -65,7 +65,11 @@ def test_treepm_in_one_call_equals_pp_plus_pm(ctx):
     s = (pp + pmf).cpu().numpy().astype(np.float64)
     b = both.cpu().numpy().astype(np.float64)
     scale = np.linalg.norm(s, axis=1)
-    assert np.all(np.linalg.norm(b - s, axis=1) <= 1e-5 * scale + 1e-6 * np.median(scale))
+    # the PM assignment adds with FP32 atomics in no fixed order, so two PM evaluations of
+    # the same particles differ at the 1e-7 level of the PM field (up to 4e-7 of its
+    # largest value here); where PP and PM nearly cancel that is the whole difference
+    pm_rms = float(np.sqrt(np.mean(np.sum(pmf.cpu().numpy().astype(np.float64) ** 2, axis=1))))
+    assert np.all(np.linalg.norm(b - s, axis=1) <= 1e-5 * scale + 2e-6 * pm_rms)
 
 
 def test_treepm_total_force_against_ewald(ctx):
