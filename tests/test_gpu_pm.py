@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 from oracle import pm as pmo
+from paper_0910_0121_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
@@ -104,3 +105,32 @@ def test_pm_invalid_arguments(ctx):
     for args in ((1.0, 4, 0.1, 1), (1.0, 32, 0.6, 1), (0.0, 32, 0.1, 1), (1.0, 32, 0.1, 7)):
         with pytest.raises(greem.GreemError):
             ctx.pm_force(P, M, *args)
+
+
+def test_treepm_error_distribution_on_a_zeldovich_set(ctx):
+    """The accuracy analysis of Sec. 3.1.2 (Figs. 3-5) on a synthetic stand-in for the
+    paper's 128^3 LCDM snapshot: 32^3 Zel'dovich particles with NFW halos, total TreePM
+    force (PP + TSC PM, r_cut = 3 grid spacings) against the Ewald sum on 1000 particles,
+    for N_PM in {16, 32, 64} and theta in {0.3, 0.5, 1.0}.  The paper's goal, 90% of the
+    particles below 2% error, holds for theta <= 0.5 at every N_PM."""
+    pos, mass = synth.config_zeldovich(32, 0.5 / 32, 40, synth.SEED0 + 21)
+    pos = np.mod(pos, 1.0)
+    N = len(pos)
+    sample = np.random.default_rng(5).choice(N, 1000, replace=False)
+    ref = pmo.ewald_field(pos[sample], pos, mass.astype(np.float64))
+    nref = np.linalg.norm(ref, axis=1)
+    P, M = _t(pos, np.float64), _t(mass, np.float32)
+    rows = []
+    for n in (16, 32, 64):
+        for theta in (0.3, 0.5, 1.0):
+            a = ctx.short_force(P, M, greem.params(L=1.0, r_cut=3.0 / n, theta=theta, n_crit=64,
+                                                   flags=greem.FLAG_ADD_PM, n_pm=n, assign=greem.ASSIGN_TSC))
+            torch.cuda.synchronize()
+            a = a.cpu().numpy().astype(np.float64)[sample]
+            e = np.linalg.norm(a - ref, axis=1) / nref
+            rows.append((n, theta, np.median(e), np.quantile(e, 0.9), np.quantile(e, 0.99)))
+    for n, theta, m, p90, p99 in rows:
+        print(f"N_PM {n:3d} theta {theta:.1f}: median {m:.2e}  90% {p90:.2e}  99% {p99:.2e}")
+    for n, theta, m, p90, p99 in rows:
+        if theta <= 0.5:
+            assert p90 < 0.02, (n, theta, p90)

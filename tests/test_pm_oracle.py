@@ -57,3 +57,19 @@ def test_symmetric_pair_momentum():
     pos = np.vstack([c + d, c - d])
     a = pm.pm_accel(pos, np.ones(2, np.float32), L, n, 3.0 / n, pm.TSC)
     assert np.abs(a[0] + a[1]).max() < 1e-12 * np.abs(a).max()
+
+
+def test_ewald_field_matches_the_pairwise_ewald_sum():
+    """The structure-factor Ewald sum equals the pairwise one (itself pinned to Newton's
+    law at short range) on a small random set, sources and targets overlapping."""
+    rng = np.random.default_rng(12)
+    src = rng.random((40, 3))
+    m = rng.uniform(0.5, 1.5, 40)
+    tg = np.vstack([rng.random((5, 3)), src[:3]])
+    got = pm.ewald_field(tg, src, m)
+    ref = np.zeros_like(got)
+    for t in range(tg.shape[0]):
+        d = tg[t][None, :] - src
+        keep = np.linalg.norm(d, axis=1) > 0
+        ref[t] = (pm.ewald_accel(d[keep]) * m[keep][:, None]).sum(axis=0)
+    assert np.allclose(got, ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max())
