@@ -212,8 +212,9 @@ def traffic_per_launch(list_entries):
 
 def extras(ctx, P, M, p, prm, acc, stream):
     """Context numbers beside the headline: CUDA-graph replay of the same step, the
-    opening-angle scan, the distance-dependent opening angle of Eq. 12, the second-order
-    terms, and the 64-box batched workload (one call vs per-box calls)."""
+    opening-angle scan, the distance-dependent opening angle of Eq. 12, the integration
+    kernels, the second-order terms, and the 64-box batched workload (one call vs per-box
+    calls)."""
     import torch
     from paper_0910_0121_gb300 import greem, synth
     out = {}
@@ -263,6 +264,20 @@ def extras(ctx, P, M, p, prm, acc, stream):
     s = ctx.stats()
     out["theta_eq12"] = {"theta0": 0.25, "theta_max": 0.7, "ms_per_step": a.elapsed_time(b),
                          "N_int": s["n_interactions"] / N, "lists_ms": s["ms_lists"], "force_ms": s["ms_force"]}
+    # the integration around the force (Sec. 2.2 steps 1, 6, 7; Eq. 7): kick, drift and the
+    # shared timestep on the bench particles (velocities zero, the force of the last call)
+    vel = torch.zeros((N, 3), dtype=torch.float32, device=P.device)
+    Pc = P.clone()
+    ctx.kick(vel, acc, 1e-3)
+    a, b = ev(), ev()
+    a.record(stream)
+    ctx.kick(vel, acc, 1e-3)
+    ctx.drift(Pc, vel, p.L, 1e-3)
+    dtq = ctx.timestep(vel, acc, 1e-4, 1.0)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["kick_drift_timestep_ms"] = a.elapsed_time(b)
+    del Pc, vel
     # second-order (quadrupole) terms of Sec. 4.1 at theta = 0.5 and 0.7
     quad = {}
     for th in (0.5, 0.7):

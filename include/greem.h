@@ -240,6 +240,44 @@ int greem_pair_force_f32(greem_ctx *ctx, const double *x_g, const double *x_i, c
 int greem_pair_force_f32_noalloc(const double *x_g, const double *x_i, const double *x_j, const float *m_j,
                                  int64_t npairs, double r_cut, double eps, float *acc, void *cuda_stream);
 
+/* ---- Time integration (Sec. 2.2 steps 1, 6, 7; Sec. 2.4) --------------------------------
+ * The paper kicks the velocities with the PM and then the PP force of the step (it keeps
+ * no accelerations) and then drifts the positions; with the total force of one call that
+ * is one kick and one drift per step (leapfrog with velocities half a step apart).
+ * Comoving coordinates: with the momentum-like velocity w = a^2 dx/dt and the acceleration
+ * of the comoving positions, the factors are f_kick = int dt/a and f_drift = int dt/a^2
+ * over the step (greem_cosmo_factors); a non-cosmological run passes dt for both. */
+
+/* v += f_kick * acc, per component in FP32 (vel, acc: float32 [N,3] device).  Errors:
+ * INVALID_ARG (N < 1, NULL, non-finite f_kick), CUDA. */
+int greem_kick(greem_ctx *ctx, float *vel, const float *acc, int64_t N, double f_kick);
+
+/* pos += f_drift * vel in FP64, each coordinate wrapped into [0, L) by the key's wrap rule
+ * (pos: float64 [N,3] device, updated in place; vel: float32 [N,3] device).  Errors:
+ * INVALID_ARG (N < 1, NULL, L <= 0, non-finite f_drift), CUDA. */
+int greem_drift(greem_ctx *ctx, double *pos, const float *vel, int64_t N, double L, double f_drift);
+
+/* Shared adaptive timestep, Eq. 7: *dt = zeta * min_i( sqrt(eps/|a_i|), eps/|v_i| ),
+ * computed as zeta * min( sqrt(eps / max|a|), eps / max|v| ) from device maxima of |a|^2
+ * and |v|^2 in FP32 ((x^2 + y^2) + z^2); a term whose maximum is 0 gives no bound (+inf
+ * when both are).  Waits for the stream.  Errors: INVALID_ARG (N < 1, NULL, eps <= 0,
+ * zeta <= 0), CUDA. */
+int greem_timestep(greem_ctx *ctx, const float *vel, const float *acc, int64_t N, double eps, double zeta,
+                   double *dt);
+
+/* Shared softening, Eq. 6, read as the physical softening: (1+z_crit)/(1+z) eps_fin for
+ * z >= z_crit (then eps_fin (1+z_crit) in comoving coordinates, a constant), eps_fin for
+ * z < z_crit (constant physically).  The force calls take comoving lengths: pass
+ * greem_softening(...) * (1+z) as eps.  Host only. */
+double greem_softening(double eps_fin, double z_crit, double z);
+
+/* Comoving kick and drift factors of a step from scale factor a0 to a1 > a0 > 0 with
+ * H(a) = H0 sqrt(omega_m a^-3 + (1 - omega_m - omega_l) a^-2 + omega_l): *kick = int da /
+ * (a^2 H), *drift = int da / (a^3 H), by 4-point Gauss-Legendre on 4096 intervals.  Host
+ * only.  Errors: INVALID_ARG (a0 <= 0, a1 <= a0, H0 <= 0, H^2 <= 0 on the interval). */
+int greem_cosmo_factors(double a0, double a1, double omega_m, double omega_l, double h0, double *kick,
+                        double *drift);
+
 /* Measured arithmetic peak of this GPU: which = 0 FP32 FMA, 1 FP64 FMA; *tflops gets
  * the rate (2 flops per FMA) of an FMA-chain microbenchmark over all SMs, at whatever
  * clock the GPU runs at the time.  Errors: INVALID_ARG, CUDA. */

@@ -1203,6 +1203,61 @@ int greem_pair_force_f32(greem_ctx *c, const double *x_g, const double *x_i, con
     return GREEM_OK;
 }
 
+int greem_kick(greem_ctx *c, float *vel, const float *acc, int64_t N, double f_kick)
+{
+    if (!c || !vel || !acc || N < 1 || N >= (int64_t)0x7FFFFFF0 || !std::isfinite(f_kick)) return GREEM_ERR_INVALID_ARG;
+    greem::g_launches = 0;
+    launch_kick(vel, acc, (uint32_t)N, (float)f_kick, c->stream, c->nsm);
+    if (!cuda_ok(cudaGetLastError())) return GREEM_ERR_CUDA;
+    c->stats.kernel_launches = greem::g_launches;
+    return GREEM_OK;
+}
+
+int greem_drift(greem_ctx *c, double *pos, const float *vel, int64_t N, double L, double f_drift)
+{
+    if (!c || !pos || !vel || N < 1 || N >= (int64_t)0x7FFFFFF0 || !(L > 0) || !std::isfinite(L) ||
+        !std::isfinite(f_drift))
+        return GREEM_ERR_INVALID_ARG;
+    greem::g_launches = 0;
+    launch_drift(pos, vel, (uint32_t)N, f_drift, L, c->stream, c->nsm);
+    if (!cuda_ok(cudaGetLastError())) return GREEM_ERR_CUDA;
+    c->stats.kernel_launches = greem::g_launches;
+    return GREEM_OK;
+}
+
+int greem_timestep(greem_ctx *c, const float *vel, const float *acc, int64_t N, double eps, double zeta, double *dt)
+{
+    if (!c || !vel || !acc || !dt || N < 1 || N >= (int64_t)0x7FFFFFF0 || !(eps > 0) || !(zeta > 0))
+        return GREEM_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = ensure(c, c->small, 16))) return rc;
+    launch_vmax_amax(vel, acc, (uint32_t)N, c->small.p, c->stream, c->nsm);
+    unsigned int h[2] = {0, 0};
+    if (!cuda_ok(cudaMemcpyAsync(h, c->small.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream)) ||
+        !cuda_ok(cudaStreamSynchronize(c->stream)))
+        return GREEM_ERR_CUDA;
+    float v2, a2;
+    memcpy(&v2, &h[0], 4);
+    memcpy(&a2, &h[1], 4);
+    *dt = timestep_eq7(eps, zeta, v2, a2);
+    return GREEM_OK;
+}
+
+double greem_softening(double eps_fin, double z_crit, double z) { return softening_eq6(eps_fin, z_crit, z); }
+
+int greem_cosmo_factors(double a0, double a1, double omega_m, double omega_l, double h0, double *kick, double *drift)
+{
+    if (!kick || !drift || !(a0 > 0) || !(a1 > a0) || !(h0 > 0) || !std::isfinite(a1)) return GREEM_ERR_INVALID_ARG;
+    // H^2 must stay positive on [a0, a1] (checked on 65 points spanning it)
+    for (int i = 0; i <= 64; i++) {
+        const double a = a0 + (a1 - a0) * i / 64.0;
+        if (!(omega_m / (a * a * a) + (1.0 - omega_m - omega_l) / (a * a) + omega_l > 0)) return GREEM_ERR_INVALID_ARG;
+    }
+    *kick = cosmo_integral(a0, a1, omega_m, omega_l, h0, 2);
+    *drift = cosmo_integral(a0, a1, omega_m, omega_l, h0, 3);
+    return GREEM_OK;
+}
+
 int greem_peak_tflops(greem_ctx *c, int which, double *tflops)
 {
     if (!c || !tflops || (which != 0 && which != 1)) return GREEM_ERR_INVALID_ARG;

@@ -258,4 +258,12 @@ double peak_tflops(int which, int nsm, cudaStream_t s, int *err);
 // PM (pm.cu)
 void launch_pm_table(int n, double L, double r_cut, int scheme, float *table, cudaStream_t s, int nsm);
 
+// time integration (integrate.cu)
+void launch_kick(float *vel, const float *acc, uint32_t N, float f, cudaStream_t s, int nsm);
+void launch_drift(double *pos, const float *vel, uint32_t N, double f, double L, cudaStream_t s, int nsm);
+void launch_vmax_amax(const float *vel, const float *acc, uint32_t N, unsigned int *out, cudaStream_t s, int nsm);
+double timestep_eq7(double eps, double zeta, float v2max, float a2max);
+double softening_eq6(double eps_fin, double z_crit, double z);
+double cosmo_integral(double a0, double a1, double om, double ol, double h0, int p);
+
 }  // namespace greem

@@ -95,12 +95,19 @@ def _lib():
             L.greem_debug_dump_group_lists.argtypes = [vp, vp, i64, vp, vp, i64, ctypes.POINTER(i64)]
             L.greem_pair_force_f32.argtypes = [vp, vp, vp, vp, vp, i64, dbl, dbl, vp]
             L.greem_peak_tflops.argtypes = [vp, i32, ctypes.POINTER(dbl)]
+            L.greem_kick.argtypes = [vp, vp, vp, i64, dbl]
+            L.greem_drift.argtypes = [vp, vp, vp, i64, dbl, dbl]
+            L.greem_timestep.argtypes = [vp, vp, vp, i64, dbl, dbl, ctypes.POINTER(dbl)]
+            L.greem_softening.argtypes = [dbl, dbl, dbl]
+            L.greem_softening.restype = dbl
+            L.greem_cosmo_factors.argtypes = [dbl, dbl, dbl, dbl, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
             L.greem_strerror.argtypes = [i32]
             L.greem_strerror.restype = ctypes.c_char_p
             for f in ("greem_create", "greem_build_tree", "greem_short_force", "greem_short_force_ex",
                       "greem_short_force_batched", "greem_pm_force", "greem_graph_capture", "greem_graph_launch",
                       "greem_get_stats", "greem_debug_dump", "greem_autotune", "greem_pair_force_f32",
-                      "greem_peak_tflops", "greem_debug_dump_group_lists"):
+                      "greem_peak_tflops", "greem_debug_dump_group_lists", "greem_kick", "greem_drift",
+                      "greem_timestep", "greem_cosmo_factors"):
                 getattr(L, f).restype = i32
             _L = L
     return _L
@@ -210,6 +217,32 @@ class Context:
                                      int(assign), _dev(acc, torch.float32, (N, 3), "acc")), "greem_pm_force")
         return acc
 
+    def kick(self, vel, acc, f_kick: float):
+        """greem_kick: vel += f_kick * acc (float32 [N,3] device, in place)."""
+        import torch
+        N = vel.shape[0]
+        _check(_lib().greem_kick(self._h, _dev(vel, torch.float32, (N, 3), "vel"), _dev(acc, torch.float32, (N, 3), "acc"),
+                                 N, float(f_kick)), "greem_kick")
+        return vel
+
+    def drift(self, pos, vel, L: float, f_drift: float):
+        """greem_drift: pos += f_drift * vel, wrapped into [0, L) (pos float64, in place)."""
+        import torch
+        N = pos.shape[0]
+        _check(_lib().greem_drift(self._h, _dev(pos, torch.float64, (N, 3), "pos"), _dev(vel, torch.float32, (N, 3), "vel"),
+                                  N, float(L), float(f_drift)), "greem_drift")
+        return pos
+
+    def timestep(self, vel, acc, eps: float, zeta: float) -> float:
+        """greem_timestep: the shared timestep of Eq. 7."""
+        import torch
+        N = vel.shape[0]
+        dt = ctypes.c_double()
+        _check(_lib().greem_timestep(self._h, _dev(vel, torch.float32, (N, 3), "vel"),
+                                     _dev(acc, torch.float32, (N, 3), "acc"), N, float(eps), float(zeta),
+                                     ctypes.byref(dt)), "greem_timestep")
+        return dt.value
+
     def graph_capture(self, pos, mass, p: Params, acc):
         import torch
         N = pos.shape[0]
@@ -309,3 +342,16 @@ def short_force(pos, mass, L: float, r_cut: float, theta: float, n_crit: int, ac
                                     N, float(L), float(r_cut), float(theta), int(n_crit),
                                     _dev(acc, torch.float32, (N, 3), "acc")), "greem_short_force")
     return acc
+
+
+def softening(eps_fin: float, z_crit: float, z: float) -> float:
+    """greem_softening: the physical softening of Eq. 6 at redshift z."""
+    return _lib().greem_softening(float(eps_fin), float(z_crit), float(z))
+
+
+def cosmo_factors(a0: float, a1: float, omega_m: float, omega_l: float, h0: float):
+    """greem_cosmo_factors: (int dt/a, int dt/a^2) from scale factor a0 to a1."""
+    k, d = ctypes.c_double(), ctypes.c_double()
+    _check(_lib().greem_cosmo_factors(float(a0), float(a1), float(omega_m), float(omega_l), float(h0), ctypes.byref(k),
+                                      ctypes.byref(d)), "greem_cosmo_factors")
+    return k.value, d.value
