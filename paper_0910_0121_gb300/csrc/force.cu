@@ -89,7 +89,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 #define GREEM_FORCE_MINB 1
 #endif
 #ifndef GREEM_FORCE_UNROLL
-#define GREEM_FORCE_UNROLL 2
+#define GREEM_FORCE_UNROLL 4
 #endif
 constexpr int kImax = GREEM_FORCE_IMAX;
 constexpr int kUnroll = GREEM_FORCE_UNROLL;
