@@ -425,6 +425,7 @@ def gpu_arm(args, rank, world, local):
     ms64 = g0.elapsed_time(g1)
     force64_ms = ctx.stats()["ms_force"]
     peak_meas = ctx.peak_tflops(0)
+    pairloop = ctx.peak_tflops(2)      # the kernel's own pair loop with no list or group overhead
     sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     # ---- roofline of the dominant kernel (S6 force): plain FP32 ALU arithmetic
@@ -448,6 +449,8 @@ def gpu_arm(args, rank, world, local):
         "pct_fp32_peak_force": 100.0 * achieved / peak,
         "pct_fp32_measured_ffma_force": 100.0 * achieved / peak_meas,
         "fp32_ffma_microbench_tflops": peak_meas,
+        "pair_loop_microbench_tflops": pairloop,
+        "pct_of_pair_loop_force": 100.0 * achieved / pairloop,
         "fp64_form": {"ms_per_step": ms64, "force_kernel_ms": force64_ms,
                       "particles_per_s": world * N / (ms64 * 1e-3),
                       "force_speedup_fp32_vs_fp64": force64_ms / fms, "step_speedup": ms64 / ms},

@@ -278,9 +278,11 @@ double greem_softening(double eps_fin, double z_crit, double z);
 int greem_cosmo_factors(double a0, double a1, double omega_m, double omega_l, double h0, double *kick,
                         double *drift);
 
-/* Measured arithmetic peak of this GPU: which = 0 FP32 FMA, 1 FP64 FMA; *tflops gets
- * the rate (2 flops per FMA) of an FMA-chain microbenchmark over all SMs, at whatever
- * clock the GPU runs at the time.  Errors: INVALID_ARG, CUDA. */
+/* Measured arithmetic rates of this GPU at whatever clock it runs at the time: which = 0
+ * FP32 FMA and 1 FP64 FMA (*tflops = 2 flops per FMA of an FMA-chain microbenchmark over
+ * all SMs); 2 the force kernel's own packed pair loop over list entries held in shared
+ * memory, with no list streaming or group overhead (42 flops per pair): the ceiling of
+ * this formulation of Eq. 1-2.  Errors: INVALID_ARG, CUDA. */
 int greem_peak_tflops(greem_ctx *ctx, int which, double *tflops);
 
 const char *greem_strerror(int code);

@@ -1260,7 +1260,7 @@ int greem_cosmo_factors(double a0, double a1, double omega_m, double omega_l, do
 
 int greem_peak_tflops(greem_ctx *c, int which, double *tflops)
 {
-    if (!c || !tflops || (which != 0 && which != 1)) return GREEM_ERR_INVALID_ARG;
+    if (!c || !tflops || which < 0 || which > 2) return GREEM_ERR_INVALID_ARG;
     int err = 0;
     *tflops = peak_tflops(which, c->nsm, c->stream, &err);
     return err;

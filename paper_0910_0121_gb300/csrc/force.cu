@@ -1012,6 +1012,44 @@ __global__ void __launch_bounds__(256) k_peak_f64(double *out, int iters)
     if (s == 1234.5) out[0] = s;
 }
 
+// The force kernel's own packed pair loop (interact2, six i-particles per lane) over 256
+// list entries held in shared memory, with no list streaming and no group overhead: the
+// rate this formulation reaches by itself, counted at 42 flops per pair.
+__global__ void __launch_bounds__(256) k_peak_pairloop(float *out, int iters)
+{
+    __shared__ float4 sj[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        sj[t] = make_float4(0.3f + t * 1e-3f, 0.2f - t * 1e-3f, 0.1f + t * 2e-3f, 1e-3f);
+    __syncthreads();
+    constexpr int H = 3;
+    f32x2 xi[H], yi[H], zi[H], ax[H], ay[H], az[H];
+#pragma unroll
+    for (int h = 0; h < H; h++) {
+        const float b = threadIdx.x * 1e-4f + h * 0.01f;
+        xi[h] = pk(b, b + 1e-3f);
+        yi[h] = pk(0.5f * b, b);
+        zi[h] = pk(b, -b);
+        ax[h] = ay[h] = az[h] = pk(0.f, 0.f);
+    }
+    const f32x2 eps2 = pk(0.f, 0.f);
+    for (int it = 0; it < iters; it++) {
+#pragma unroll(kUnroll)
+        for (int t = 0; t < 256; t++) interact2<H, false>(sj[t], xi, yi, zi, ax, ay, az, eps2);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int h = 0; h < H; h++) {
+        float a, b;
+        upk(ax[h], a, b);
+        sum += a + b;
+        upk(ay[h], a, b);
+        sum += a + b;
+        upk(az[h], a, b);
+        sum += a + b;
+    }
+    if (sum == 1234.5f) out[0] = sum;
+}
+
 double peak_tflops(int which, int nsm, cudaStream_t s, int *err)
 {
     *err = 0;
@@ -1020,8 +1058,8 @@ double peak_tflops(int which, int nsm, cudaStream_t s, int *err)
         *err = -3;
         return 0.0;
     }
-    const int blocks = nsm * 8, threads = 256;
-    const int iters = which == 0 ? 4000 : 64;
+    const int blocks = which == 2 ? nsm * 2 : nsm * 8, threads = 256;
+    const int iters = which == 0 ? 4000 : (which == 1 ? 64 : 40);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1029,12 +1067,14 @@ double peak_tflops(int which, int nsm, cudaStream_t s, int *err)
     for (int rep = 0; rep < 4; rep++) {
         cudaEventRecord(e0, s);
         if (which == 0) k_peak_f32<<<blocks, threads, 0, s>>>((float *)out, iters);
-        else k_peak_f64<<<blocks, threads, 0, s>>>((double *)out, iters);
+        else if (which == 1) k_peak_f64<<<blocks, threads, 0, s>>>((double *)out, iters);
+        else k_peak_pairloop<<<blocks, threads, 0, s>>>((float *)out, iters);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double flops = 2.0 * 8 * 16 * (double)iters * blocks * threads;
+        const double flops = which == 2 ? 42.0 * 6 * 256 * (double)iters * blocks * threads
+                                        : 2.0 * 8 * 16 * (double)iters * blocks * threads;
         const double tf = flops / (ms * 1e-3) / 1e12;
         if (rep > 0 && tf > best) best = tf;
     }
