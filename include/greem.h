@@ -86,7 +86,9 @@ typedef struct greem_params {
     int precision;   /* GREEM_F32_REL or GREEM_F64 */
     int list_chunk;  /* list entries staged per force-kernel chunk: 0 = default (256); power of
                         two in [64, 2048] */
-    int block_shape; /* warps per force-kernel block: 0 = default (8); 1..16 */
+    int block_shape; /* warps per force-kernel block: 0 = default (8); 1..16; block_shape x
+                        list_chunk x 32 bytes (two chunk buffers per warp) must not exceed
+                        226 KB of shared memory */
     unsigned flags;  /* GREEM_FLAG_* */
     int n_pm;        /* PM grid points per side for GREEM_FLAG_ADD_PM (8..1024) */
     int assign;      /* GREEM_ASSIGN_CIC or GREEM_ASSIGN_TSC for GREEM_FLAG_ADD_PM */

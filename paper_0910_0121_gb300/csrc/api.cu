@@ -251,6 +251,9 @@ static int check_common(const greem_params &p)
     if (p.list_chunk != 0 && (p.list_chunk < 64 || p.list_chunk > 2048 || (p.list_chunk & (p.list_chunk - 1))))
         return GREEM_ERR_INVALID_ARG;
     if (p.block_shape < 0 || p.block_shape > 16) return GREEM_ERR_INVALID_ARG;
+    // the force kernel's chunk buffers must fit in one block's shared memory
+    if (force_smem_bytes(p.list_chunk ? p.list_chunk : 256, p.block_shape ? p.block_shape : 8) > kForceSmemMax)
+        return GREEM_ERR_INVALID_ARG;
     if ((p.flags & GREEM_FLAG_QUADRUPOLE) && (p.precision != GREEM_F32_REL || p.eps != 0.0))
         return GREEM_ERR_INVALID_ARG;
     if (p.flags & GREEM_FLAG_ADD_PM) {
@@ -1136,7 +1139,7 @@ int greem_autotune(greem_ctx *c, const double *pos, const float *mass, int64_t N
                 greem_params q = base;
                 q.list_chunk = chunks[ci];
                 q.block_shape = shapes[si];
-                if ((size_t)q.block_shape * 2 * q.list_chunk * 16 > 200 * 1024) continue;
+                if (force_smem_bytes(q.list_chunk, q.block_shape) > kForceSmemMax) continue;
                 float t;
                 if ((rc = timeit(q, &t))) break;
                 if (t < bt) {

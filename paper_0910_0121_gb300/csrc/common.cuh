@@ -247,6 +247,10 @@ struct ForceArgs {
 };
 void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t *bins, uint32_t *order,
                         cudaStream_t s, int nsm);
+// Dynamic shared memory of the FP32 force kernel, and its limit: the 227 KB a block may
+// opt in to, less room for the kernel's static shared memory (its mbarriers).
+size_t force_smem_bytes(int chunk, int warps);
+constexpr size_t kForceSmemMax = 226 * 1024;
 void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft, bool quad = false);
 void launch_qlist_fill(const ForceArgs &a, const float4 *quad, unsigned long long qcap, cudaStream_t s, int nsm);
 void launch_force_f64(const ForceArgs &a, cudaStream_t s, int nsm);

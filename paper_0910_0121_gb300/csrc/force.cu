@@ -763,15 +763,21 @@ void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t 
 
 static int g_force_smem_set[3] = {0, 0, 0};
 
+// Dynamic shared memory of the FP32 force kernel: two chunk buffers per warp.
+size_t force_smem_bytes(int chunk, int warps)
+{
+    return (size_t)warps * 2 * (size_t)chunk * sizeof(float4);
+}
+
 void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft, bool quad)
 {
     const int threads = 32 * a.warps;
-    const size_t smem = (size_t)a.warps * 2 * a.chunk * sizeof(float4);
+    const size_t smem = force_smem_bytes(a.chunk, a.warps);
     auto kern = quad ? k_force_f32<false, true> : (soft ? k_force_f32<true, false> : k_force_f32<false, false>);
     const int which = quad ? 2 : (soft ? 1 : 0);
     if (g_force_smem_set[which] < (int)smem) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        g_force_smem_set[which] = 200 * 1024;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForceSmemMax);
+        g_force_smem_set[which] = (int)kForceSmemMax;
     }
     // occupancy is queried once per shape (not while a stream is being captured)
     static int cached[3][17][2] = {};

@@ -49,10 +49,16 @@ def full(request):
     best = ctx.autotune(P, M, base, acc, candidates=BENCH_CANDIDATES)
     p = greem.params(L=best.L, r_cut=best.r_cut, theta=best.theta, n_crit=best.n_crit, n_leaf=best.n_leaf,
                      list_chunk=best.list_chunk, block_shape=best.block_shape, flags=greem.FLAG_INDEX_LISTS)
+    # without index lists: exactly the launch bench.py times
+    pf = greem.params(L=best.L, r_cut=best.r_cut, theta=best.theta, n_crit=best.n_crit, n_leaf=best.n_leaf,
+                      list_chunk=best.list_chunk, block_shape=best.block_shape)
+    acc_plain = ctx.short_force(P, M, pf, acc).cpu().numpy().astype(np.float64)
+    stats_plain = ctx.stats()
     acc = ctx.short_force(P, M, p, acc)
     torch.cuda.synchronize()
     out = dict(name=request.param, pos=pos, mass=mass, prm=prm, p=p, ctx=ctx, P=P, M=M,
-               acc=acc.cpu().numpy().astype(np.float64))
+               acc=acc.cpu().numpy().astype(np.float64), acc_plain=acc_plain, stats_plain=stats_plain,
+               stats_index=ctx.stats())
     for w in (greem.DUMP_KEYS, greem.DUMP_PERM, greem.DUMP_NODES, greem.DUMP_MOMENTS, greem.DUMP_GROUPS):
         out[w] = ctx.dump(w)
     T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=p.n_crit, n_leaf=p.n_leaf)
@@ -101,15 +107,25 @@ def test_sampled_force_fp32_and_fp64(full):
     nodes, grp = T.nodes(), T.groups()
     rows = np.concatenate([np.arange(nodes[grp[g], 4], nodes[grp[g], 5]) for g in full["sel"]])
     ref = ref_sorted[rows]
-    got = full["acc"][perm[rows]]
-    e = _rel(got, ref)
-    print(f"{full['name']}: n_crit {full['p'].n_crit}, {len(rows)} sampled particles, "
-          f"median {np.median(e):.2e}, p99.9 {np.quantile(e, 0.999):.2e}")
-    assert np.median(e) <= 1e-5
-    assert np.quantile(e, 0.999) <= 1e-4
+    for form in ("acc", "acc_plain"):
+        got = full[form][perm[rows]]
+        e = _rel(got, ref)
+        print(f"{full['name']} {form}: n_crit {full['p'].n_crit}, {len(rows)} sampled particles, "
+              f"median {np.median(e):.2e}, p99.9 {np.quantile(e, 0.999):.2e}")
+        assert np.median(e) <= 1e-5
+        assert np.quantile(e, 0.999) <= 1e-4
     p = full["p"]
     p64 = greem.params(L=p.L, r_cut=p.r_cut, theta=p.theta, n_crit=p.n_crit, n_leaf=p.n_leaf, precision=greem.F64)
     a64 = full["ctx"].short_force(full["P"], full["M"], p64)
     torch.cuda.synchronize()
     a64 = a64.cpu().numpy()[perm[rows]]
     assert np.abs(a64 - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_counts_without_index_lists_equal_index_lists(full):
+    """The launch bench.py times (no index lists) builds the same lists as the index-list
+    call: equal list lengths and interaction counts over the whole workload."""
+    si, sp = full["stats_index"], full["stats_plain"]
+    assert sp["n_groups"] == si["n_groups"]
+    assert sp["n_list_entries"] == si["n_list_entries"]
+    assert sp["n_interactions"] == si["n_interactions"]

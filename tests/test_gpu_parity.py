@@ -77,12 +77,16 @@ def case(request, ctx):
     prm = dict(prm)
     if not prm.get("n_crit"):
         prm["n_crit"] = 64
+    acc_plain = gpu_force(ctx, pos, mass, prm, flags=0)   # no index lists: the launch bench.py times
+    stats_plain = ctx.stats()
     acc32 = gpu_force(ctx, pos, mass, prm)
+    stats_index = ctx.stats()
     dumps = {w: ctx.dump(w) for w in (greem.DUMP_KEYS, greem.DUMP_PERM, greem.DUMP_NODES, greem.DUMP_MOMENTS,
                                       greem.DUMP_GROUPS, greem.DUMP_LIST_OFFSETS, greem.DUMP_LISTS)}
     T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm.get("n_leaf", 10))
     T.build_lists(prm["theta"])
-    return dict(name=request.param, pos=pos, mass=mass, prm=prm, acc32=acc32, dumps=dumps, T=T)
+    return dict(name=request.param, pos=pos, mass=mass, prm=prm, acc32=acc32, acc_plain=acc_plain, dumps=dumps, T=T,
+                stats_plain=stats_plain, stats_index=stats_index)
 
 
 def test_keys_and_sort_bit_exact(case):
@@ -131,6 +135,20 @@ def test_lists_bit_exact(case):
 def test_force_f32_within_bounds(case):
     ref = case["T"].list_force_input_order()
     e = rel_err(case["acc32"], ref)
+    assert np.median(e) <= MED_BOUND, np.median(e)
+    assert np.quantile(e, 0.999) <= P999_BOUND, np.quantile(e, 0.999)
+
+
+def test_force_f32_without_index_lists(case):
+    """The FP32 call without index lists (the launch bench.py times): the same list
+    lengths and interaction counts as the index-list call and as the oracle's lists, and
+    the force within the same bounds."""
+    si, sp = case["stats_index"], case["stats_plain"]
+    off, _, _, _ = case["T"].lists()
+    assert sp["n_list_entries"] == si["n_list_entries"] == off[-1]
+    assert sp["n_interactions"] == si["n_interactions"]
+    ref = case["T"].list_force_input_order()
+    e = rel_err(case["acc_plain"], ref)
     assert np.median(e) <= MED_BOUND, np.median(e)
     assert np.quantile(e, 0.999) <= P999_BOUND, np.quantile(e, 0.999)
 
@@ -283,6 +301,13 @@ def test_invalid_inputs_are_errors(ctx):
                 dict(L=0.0, r_cut=0.1, theta=0.5, n_crit=8), dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=0)):
         with pytest.raises(greem.GreemError):
             gpu_force(ctx, pos, mass, prm)
+    # force-kernel shapes whose chunk buffers exceed a block's shared memory are refused
+    # (16 warps x 2 x 1024 entries x 16 bytes = 512 KB); the largest that fits runs
+    with pytest.raises(greem.GreemError) as ei:
+        gpu_force(ctx, pos, mass, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=8), list_chunk=1024, block_shape=16)
+    assert ei.value.code == greem.ERR_INVALID_ARG
+    ok = gpu_force(ctx, pos, mass, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=8), list_chunk=256, block_shape=16)
+    assert np.all(np.isfinite(ok))
     # the context is still usable afterwards
     gpu_force(ctx, pos, mass, dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=8))
     assert greem.lib().greem_pm_force(ctx._h, None, None, 0, 1.0, 32, 0.1, 0, None) == greem.ERR_INVALID_ARG
