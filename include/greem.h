@@ -86,7 +86,7 @@ typedef struct greem_params {
     int precision;   /* GREEM_F32_REL or GREEM_F64 */
     int list_chunk;  /* list entries staged per force-kernel chunk: 0 = default (256); power of
                         two in [64, 2048] */
-    int block_shape; /* warps per force-kernel block: 0 = default (8); 1..16; block_shape x
+    int block_shape; /* warps per force-kernel block: 0 = default (16); 1..16; block_shape x
                         list_chunk x 32 bytes (two chunk buffers per warp) must not exceed
                         226 KB of shared memory */
     unsigned flags;  /* GREEM_FLAG_* */
@@ -212,9 +212,11 @@ int greem_debug_dump_group_lists(greem_ctx *ctx, const int64_t *groups, int64_t 
                                  int64_t *entries, int64_t cap_entries, int64_t *n_entries);
 
 /* Picks n_crit from candidates[0..ncand) (ncand = 0 -> 32, 48, 64, 96, 128, 192, 256, 384,
- * 512), then list_chunk and block_shape, by timing the whole force on these inputs; writes
- * the best parameters to *best (a copy of *p with those three fields set).  acc is scratch
- * output of the right type.  Errors as greem_short_force_ex. */
+ * 512) at p's list_chunk and block_shape, then list_chunk and block_shape at that n_crit,
+ * then re-times the neighbouring n_crit candidates at the chosen shape; each setting is
+ * timed on the whole force over these inputs (best of three calls).  Writes the best
+ * parameters to *best (a copy of *p with those three fields set).  acc is scratch output
+ * of the right type.  Errors as greem_short_force_ex. */
 int greem_autotune(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, const greem_params *p,
                    const int *candidates, int ncand, void *acc, greem_params *best);
 

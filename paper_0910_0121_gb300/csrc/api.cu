@@ -252,7 +252,7 @@ static int check_common(const greem_params &p)
         return GREEM_ERR_INVALID_ARG;
     if (p.block_shape < 0 || p.block_shape > 16) return GREEM_ERR_INVALID_ARG;
     // the force kernel's chunk buffers must fit in one block's shared memory
-    if (force_smem_bytes(p.list_chunk ? p.list_chunk : 256, p.block_shape ? p.block_shape : 8) > kForceSmemMax)
+    if (force_smem_bytes(p.list_chunk ? p.list_chunk : 256, p.block_shape ? p.block_shape : 16) > kForceSmemMax)
         return GREEM_ERR_INVALID_ARG;
     if ((p.flags & GREEM_FLAG_QUADRUPOLE) && (p.precision != GREEM_F32_REL || p.eps != 0.0))
         return GREEM_ERR_INVALID_ARG;
@@ -645,7 +645,7 @@ static RunCfg make_cfg(const greem_params &p, const double *pos, const float *ma
     r.soft = false;
     r.timing = (p.flags & GREEM_FLAG_STAGE_TIMES) != 0;
     r.chunk = p.list_chunk ? p.list_chunk : 256;
-    r.warps = p.block_shape ? p.block_shape : 8;
+    r.warps = p.block_shape ? p.block_shape : 16;
     r.add_pm = (p.flags & GREEM_FLAG_ADD_PM) != 0;
     r.n_pm = p.n_pm;
     r.assign = p.assign;
@@ -1102,7 +1102,7 @@ int greem_autotune(greem_ctx *c, const double *pos, const float *mass, int64_t N
         int rc = greem_short_force_ex(c, pos, mass, N, &q, acc);  // warm (sizes buffers)
         if (rc) return rc;
         float bestms = 1e30f;
-        for (int rep = 0; rep < 2; rep++) {
+        for (int rep = 0; rep < 3; rep++) {
             cudaEventRecord(e0, c->stream);
             rc = greem_short_force_ex(c, pos, mass, N, &q, acc);
             cudaEventRecord(e1, c->stream);
@@ -1120,33 +1120,48 @@ int greem_autotune(greem_ctx *c, const double *pos, const float *mass, int64_t N
     float bt = 1e30f;
     int rc = GREEM_OK;
     greem_params bp = cur;
-    for (int i = 0; i < ncand; i++) {
-        greem_params q = cur;
-        q.n_crit = candidates[i];
+    auto tryq = [&](const greem_params &q) -> int {
         float t;
-        if ((rc = timeit(q, &t))) break;
-        if (t < bt) {
+        const int r = timeit(q, &t);
+        if (!r && t < bt) {
             bt = t;
             bp = q;
         }
+        return r;
+    };
+    // 1. n_crit at the given shape (unset fields: the default shape)
+    int ib = 0;
+    for (int i = 0; i < ncand && !rc; i++) {
+        greem_params q = cur;
+        q.n_crit = candidates[i];
+        const float before = bt;
+        rc = tryq(q);
+        if (bt < before) ib = i;
     }
+    // 2. list chunk and block shape at that n_crit
     if (!rc) {
         const int chunks[] = {128, 256, 512, 1024};
         const int shapes[] = {4, 8, 16};
-        greem_params base = bp;
+        const greem_params base = bp;
         for (int ci = 0; ci < 4 && !rc; ci++)
             for (int si = 0; si < 3 && !rc; si++) {
                 greem_params q = base;
                 q.list_chunk = chunks[ci];
                 q.block_shape = shapes[si];
                 if (force_smem_bytes(q.list_chunk, q.block_shape) > kForceSmemMax) continue;
-                float t;
-                if ((rc = timeit(q, &t))) break;
-                if (t < bt) {
-                    bt = t;
-                    bp = q;
-                }
+                rc = tryq(q);
             }
+    }
+    // 3. the neighbouring n_crit candidates again at the chosen shape (the best n_crit
+    // depends on the shape)
+    if (!rc) {
+        const greem_params base = bp;
+        for (int i = ib - 1; i <= ib + 1 && !rc; i += 2) {
+            if (i < 0 || i >= ncand) continue;
+            greem_params q = base;
+            q.n_crit = candidates[i];
+            rc = tryq(q);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
