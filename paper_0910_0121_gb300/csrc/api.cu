@@ -383,7 +383,7 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
         ENS(qlist, c->qcap * 3);
     }
     ENS(kids, nc * 8);
-    ENS(lvl, 96);
+    ENS(lvl, 192);
     ENS(bps, (size_t)r.nbox);
     ENS(box_off, (size_t)r.nbox + 1);
     ENS(st, 1);

@@ -62,17 +62,18 @@ __device__ __forceinline__ Node load_node(const Node *p)
 }
 
 // Geometry of a cell against the group: the offset of its centre from the group's cell
-// centre (u, wrapped to the nearest image, shift code of that image), the squared gap
-// to the group's particle box, and the squared distance from its centre to the group
-// cell (both in u^2).
+// centre (u, wrapped to the nearest image, with the image's shift), the squared gap to
+// the group's particle box, and the squared distance from its centre to the group cell
+// (both in u^2).  cell_gap computes what the prune test needs; the accept distance
+// follows only for cells that pass it.
 struct CellTest {
     int dx, dy, dz;
     unsigned shc;
-    long long Sg, Sd;
+    long long Sg;
 };
 
-__device__ __forceinline__ CellTest cell_test(uint32_t ix, uint32_t iy, uint32_t iz, int h, const Group &gr,
-                                              const int4 tb, const int4 th)
+__device__ __forceinline__ CellTest cell_gap(uint32_t ix, uint32_t iy, uint32_t iz, int h, const Group &gr,
+                                             const int4 tb, const int4 th)
 {
     CellTest c;
     int sx, sy, sz;
@@ -82,10 +83,14 @@ __device__ __forceinline__ CellTest cell_test(uint32_t ix, uint32_t iy, uint32_t
     c.shc = shift_code(sx, sy, sz);
     const int gx = max(0, abs(c.dx - tb.x) - h - th.x), gy = max(0, abs(c.dy - tb.y) - h - th.y),
               gz = max(0, abs(c.dz - tb.z) - h - th.z);
-    const int ex = max(0, abs(c.dx) - gr.hg), ey = max(0, abs(c.dy) - gr.hg), ez = max(0, abs(c.dz) - gr.hg);
     c.Sg = (long long)gx * gx + (long long)gy * gy + (long long)gz * gz;
-    c.Sd = (long long)ex * ex + (long long)ey * ey + (long long)ez * ez;
     return c;
+}
+
+__device__ __forceinline__ long long cell_dist2(const CellTest &c, const Group &gr)
+{
+    const int ex = max(0, abs(c.dx) - gr.hg), ey = max(0, abs(c.dy) - gr.hg), ez = max(0, abs(c.dz) - gr.hg);
+    return (long long)ex * ex + (long long)ey * ey + (long long)ez * ez;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
@@ -122,8 +127,8 @@ __device__ __forceinline__ int owner_lane(uint32_t off, uint32_t t)
 // pushed.  Last, the particles of the popped leaves are spread over the lanes and each
 // goes through the per-particle r_cut test unless its whole leaf lies within r_cut.
 __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb, const int4 th, const BoxPar &bp,
-                               uint32_t root, uint32_t *__restrict__ stk, unsigned long long pos0,
-                               unsigned long long lim, int lane, uint32_t &nacc)
+                               uint32_t root, uint32_t *__restrict__ stk, const uint8_t *__restrict__ octq,
+                               unsigned long long pos0, unsigned long long lim, int lane, uint32_t &nacc)
 {
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
@@ -172,14 +177,14 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
             CellTest ct;
             if (t < ctot) {
                 const uint32_t q = t - o_s;
-                const uint32_t oct = __fns((plvl >> 16) & 255u, 0, (int)q + 1);
+                const uint32_t oct = octq[((plvl >> 13) & (255u << 3)) | q];
                 const int kc = (int)(plvl & 255u) + 1;
                 const int hc = 1 << (kMaxLevel - kc);
-                ct = cell_test(pix + ((oct >> 2) & 1u) * (uint32_t)hc, piy + ((oct >> 1) & 1u) * (uint32_t)hc,
-                               piz + (oct & 1u) * (uint32_t)hc, hc, gr, tb, th);
+                ct = cell_gap(pix + ((oct >> 2) & 1u) * (uint32_t)hc, piy + ((oct >> 1) & 1u) * (uint32_t)hc,
+                              piz + (oct & 1u) * (uint32_t)hc, hc, gr, tb, th);
                 if (ct.Sg <= Tp) {
                     child = __ldg(a.kids + (size_t)pm * 8 + q);
-                    acc = kc >= lmin && ct.Sd > bp.A[kc];
+                    acc = kc >= lmin && cell_dist2(ct, gr) > bp.A[kc];
                     push = !acc;
                 }
             }
@@ -192,7 +197,8 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
                                              __fadd_rn(__fmul_rn((float)ct.dz, kf), v.z), v.w);
                 if (p < lim) {
                     a.flist[p] = e;
-                    if (a.ilist) a.ilist[p] = (unsigned long long)child | (1ull << 32) | ((unsigned long long)ct.shc << 33);
+                    if (a.ilist)
+                        a.ilist[p] = (unsigned long long)child | (1ull << 32) | ((unsigned long long)ct.shc << 33);
                 }
             }
             cnt += __popc(ab);
@@ -215,7 +221,7 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
         unsigned shc = 0;
         if (leaf) {
             const int h = 1 << (kMaxLevel - k);
-            const CellTest lc = cell_test(nd.ix, nd.iy, nd.iz, h, gr, tb, th);
+            const CellTest lc = cell_gap(nd.ix, nd.iy, nd.iz, h, gr, tb, th);
             // a leaf whose whole cell lies within r_cut of the particle box keeps every
             // particle (each particle's finest cell is inside the leaf's cell)
             const int fx = max(0, abs(lc.dx - tb.x) + h - th.x), fy = max(0, abs(lc.dy - tb.y) + h - th.y),
@@ -280,6 +286,15 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    // octq[8 mask + q]: the octant of the (q+1)-th set bit of an 8-bit child mask
+    __shared__ uint8_t octq[256 * 8];
+    for (uint32_t m = threadIdx.x; m < 256; m += blockDim.x) {
+        uint32_t q = 0;
+        for (uint32_t o = 0; o < 8; o++)
+            if (m & (1u << o)) octq[8 * m + q++] = (uint8_t)o;
+        for (; q < 8; q++) octq[8 * m + q] = 0;
+    }
+    __syncthreads();
     if (a.st->flags & ST_NODE_CAP) return;  // the tree was truncated: the call is retried
     const uint32_t G = *a.n_groups;
     uint32_t *stk = a.stack + (size_t)(blockIdx.x * kListWarps + (threadIdx.x >> 5)) * a.stack_cap;
@@ -296,7 +311,7 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
         const BoxPar &bp = a.bps[gr.box];
         const uint32_t root = a.base[bp.p_begin];
         uint32_t nacc = 0;
-        const uint32_t len = walk_group(a, gr, tb, th, bp, root, stk, page_cur, page_end, lane, nacc);
+        const uint32_t len = walk_group(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc);
         const uint32_t padded = (len + 7u) & ~7u;
         if (lane == 0) atomicAdd(&a.st->sum_padded, (unsigned long long)padded);
         if (exhausted) {
@@ -326,7 +341,7 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
             }
             page_cur = first * a.page;
             page_end = (first + np) * a.page;
-            walk_group(a, gr, tb, th, bp, root, stk, page_cur, page_end, lane, nacc);
+            walk_group(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc);
         }
         for (uint32_t t = len + lane; t < padded; t += 32) {
             a.flist[page_cur + t] = make_float4(16.f, 16.f, 16.f, 0.f);

@@ -36,12 +36,31 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x)
     return (uint32_t)x;
 }
 
+// Window LCPs of a block: w[t] = lcp_level(keys[t], keys[t + N_leaf - 1]) for the windows
+// t = i0 - kPrepHalo ... i0 + 255 that stay inside their box (-1 otherwise), computed once
+// and shared by the N_leaf particles each window covers.
+constexpr int kPrepHalo = 64;
+
 __global__ void __launch_bounds__(256) k_tree_prep(const uint64_t *__restrict__ keys, uint32_t N,
                                                    const uint32_t *__restrict__ box_off, int nbox,
                                                    const BoxPar *__restrict__ bps, uint8_t *__restrict__ d8,
                                                    uint8_t *__restrict__ K8, uint32_t *__restrict__ own)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int8_t ws[256 + kPrepHalo];
+    const long long i0 = (long long)blockIdx.x * 256;
+    for (int k = threadIdx.x; k < 256 + kPrepHalo; k += 256) {
+        const long long t = i0 - kPrepHalo + k;
+        int w = -1;
+        if (t >= 0 && t < (long long)N) {
+            const int bt = box_of((uint32_t)t, box_off, nbox);
+            const int nl = bps[bt].n_leaf;
+            if (nl <= kPrepHalo + 1 && t + nl - 1 < (long long)box_off[bt + 1])
+                w = lcp_level(keys[t], keys[t + nl - 1]);
+        }
+        ws[k] = (int8_t)w;
+    }
+    __syncthreads();
+    const uint32_t i = (uint32_t)i0 + threadIdx.x;
     if (i >= N) return;
     const int b = box_of(i, box_off, nbox);
     const long long o = box_off[b], e = box_off[b + 1];
@@ -53,9 +72,13 @@ __global__ void __launch_bounds__(256) k_tree_prep(const uint64_t *__restrict__ 
     if (tlo < o) tlo = o;
     long long thi = e - nl;
     if (thi > (long long)i) thi = i;
-    for (long long t = tlo; t <= thi; t++) {
-        int w = lcp_level(keys[t], keys[t + nl - 1]);
-        J = w > J ? w : J;
+    if (nl <= kPrepHalo + 1) {
+        for (long long t = tlo; t <= thi; t++) J = max(J, (int)ws[t - i0 + kPrepHalo]);
+    } else {
+        for (long long t = tlo; t <= thi; t++) {
+            int w = lcp_level(keys[t], keys[t + nl - 1]);
+            J = w > J ? w : J;
+        }
     }
     int K = J + 1;
     K = K < lmin ? lmin : K;
@@ -195,81 +218,108 @@ void launch_tree_links(Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, 
     g_launches++;
 }
 
-// Monopole moments (Sec. 3.1.2, centre-of-mass approximation), bottom up.  Leaves sum
-// their particles in FP64 (one thread per leaf, in sorted order); internal nodes are
-// bucketed by level and each level, deepest first, sums its children's raw moments in
-// child order (one thread per node, full warps: FP64 issue is expensive on this GPU).
-// Every sum has a fixed order, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) k_moments_leaf(const Node *__restrict__ nodes,
-                                                      const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
-                                                      const double *__restrict__ xs, const double *__restrict__ ys,
-                                                      const double *__restrict__ zs, const float *__restrict__ ms,
-                                                      Dbl4 *__restrict__ raw, uint32_t *__restrict__ lvl)
+// Monopole moments (Sec. 3.1.2, centre-of-mass approximation), bottom up.  The nodes are
+// first bucketed: internal nodes by level (buckets 0-31), leaves by particle count
+// (buckets 32-63, count min(n, 31)).  Leaves then sum their particles in FP64, one
+// thread per leaf in bucket order, so the lanes of a warp loop over equally many
+// particles (an FP64 warp instruction costs the same with idle lanes, and FP64 issue is
+// expensive on this GPU).  Internal nodes follow level by level, deepest first, each
+// summing its children's raw moments in child order.  Every sum has a fixed order, so
+// the result does not depend on scheduling.
+//
+// lvl[0..64): nodes per bucket, lvl[64..128): bucket start, lvl[128..192): cursor.
+constexpr int kLeafBucket = 32;
+
+__device__ __forceinline__ uint32_t node_bucket(const Node &nd)
 {
-    __shared__ uint32_t cnt[32];
-    if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
+    return (nd.lvl & 256u) ? kLeafBucket + min(nd.end - nd.begin, 31u) : (nd.lvl & 255u);
+}
+
+__global__ void __launch_bounds__(256) k_node_buckets(const Node *__restrict__ nodes,
+                                                      const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
+                                                      uint32_t *__restrict__ lvl)
+{
+    __shared__ uint32_t cnt[64];
+    if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t nn = node_count(n_nodes, node_cap);
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n < nn) {
-        const Node nd = nodes[n];
-        if (nd.lvl & 256u) {
-            double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-            for (uint32_t j = nd.begin; j < nd.end; j++) {
-                const double m = (double)ms[j];
-                M += m;
-                sx = fma(m, xs[j], sx);
-                sy = fma(m, ys[j], sy);
-                sz = fma(m, zs[j], sz);
-            }
-            raw[n] = make_dbl4(sx, sy, sz, M);
-        } else {
-            atomicAdd(&cnt[nd.lvl & 255u], 1u);
-        }
-    }
+    if (n < nn) atomicAdd(&cnt[node_bucket(nodes[n])], 1u);
     __syncthreads();
-    if (threadIdx.x < 32 && cnt[threadIdx.x]) atomicAdd(&lvl[threadIdx.x], cnt[threadIdx.x]);
+    if (threadIdx.x < 64 && cnt[threadIdx.x]) atomicAdd(&lvl[threadIdx.x], cnt[threadIdx.x]);
 }
 
-// lvl[0..32): internal nodes per level -> lvl[32..64): level start, lvl[64..96): cursor
 __global__ void k_level_scan(uint32_t *lvl)
 {
     const uint32_t lane = threadIdx.x;
-    const uint32_t v = lvl[lane];
-    uint32_t x = v;
+    const uint32_t v0 = lvl[lane], v1 = lvl[32 + lane];
+    uint32_t x0 = v0, x1 = v1;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= (uint32_t)o) x += y;
+        const uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+        if (lane >= (uint32_t)o) {
+            x0 += y0;
+            x1 += y1;
+        }
     }
-    lvl[32 + lane] = x - v;
-    lvl[64 + lane] = x - v;
+    const uint32_t tot0 = __shfl_sync(0xffffffffu, x0, 31);
+    lvl[64 + lane] = lvl[128 + lane] = x0 - v0;
+    lvl[96 + lane] = lvl[160 + lane] = tot0 + x1 - v1;
 }
 
+// Places every node in its bucket: a slot within the block from a shared-memory counter,
+// then one global atomic per bucket and block.  The order within a bucket is free (its
+// nodes are summed independently).
 __global__ void __launch_bounds__(256) k_level_scatter(const Node *__restrict__ nodes,
                                                        const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
                                                        uint32_t *__restrict__ lvl, uint32_t *__restrict__ inodes)
 {
+    __shared__ uint32_t cnt[64], base[64];
+    if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+    __syncthreads();
     const uint32_t nn = node_count(n_nodes, node_cap);
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t l = n < nn ? nodes[n].lvl : 256u;
-    const bool internal = !(l & 256u);
-    const uint32_t key = internal ? (l & 255u) : 1024u;
-    // one atomic per distinct level per warp
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (internal && lane == leader) base = atomicAdd(&lvl[64 + key], (uint32_t)__popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (internal) inodes[base + __popc(peers & ((1u << lane) - 1u))] = n;
+    uint32_t key = 0, slot = 0;
+    if (n < nn) {
+        key = node_bucket(nodes[n]);
+        slot = atomicAdd(&cnt[key], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && cnt[threadIdx.x]) base[threadIdx.x] = atomicAdd(&lvl[128 + threadIdx.x], cnt[threadIdx.x]);
+    __syncthreads();
+    if (n < nn) inodes[base[key] + slot] = n;
+}
+
+__global__ void __launch_bounds__(256) k_moments_leaf(const Node *__restrict__ nodes,
+                                                      const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
+                                                      const uint32_t *__restrict__ lvl,
+                                                      const uint32_t *__restrict__ inodes,
+                                                      const double *__restrict__ xs, const double *__restrict__ ys,
+                                                      const double *__restrict__ zs, const float *__restrict__ ms,
+                                                      Dbl4 *__restrict__ raw)
+{
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    for (uint32_t i = lvl[64 + kLeafBucket] + blockIdx.x * blockDim.x + threadIdx.x; i < nn;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t n = inodes[i];
+        const uint32_t b = nodes[n].begin, e = nodes[n].end;
+        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (uint32_t j = b; j < e; j++) {
+            const double m = (double)ms[j];
+            M += m;
+            sx = fma(m, xs[j], sx);
+            sy = fma(m, ys[j], sy);
+            sz = fma(m, zs[j], sz);
+        }
+        raw[n] = make_dbl4(sx, sy, sz, M);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_moments_level(int level, const uint32_t *__restrict__ lvl,
                                                        const uint32_t *__restrict__ inodes,
                                                        const uint32_t *__restrict__ kids, Dbl4 *__restrict__ raw)
 {
-    const uint32_t b = lvl[32 + level], e = b + lvl[level];
+    const uint32_t b = lvl[64 + level], e = b + lvl[level];
     for (uint32_t i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
         const uint32_t p = inodes[i];
         const uint4 *kp = reinterpret_cast<const uint4 *>(kids + (size_t)p * 8);
@@ -293,12 +343,13 @@ void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_ca
                     const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw, uint32_t *lvl,
                     uint32_t *inodes, cudaStream_t s, int nsm)
 {
-    cudaMemsetAsync(lvl, 0, 96 * sizeof(uint32_t), s);
+    cudaMemsetAsync(lvl, 0, 192 * sizeof(uint32_t), s);
     const unsigned grid = (node_cap + 255) / 256;
-    k_moments_leaf<<<grid, 256, 0, s>>>(nodes, n_nodes, node_cap, xs, ys, zs, ms, raw, lvl);
+    k_node_buckets<<<grid, 256, 0, s>>>(nodes, n_nodes, node_cap, lvl);
     k_level_scan<<<1, 32, 0, s>>>(lvl);
     k_level_scatter<<<grid, 256, 0, s>>>(nodes, n_nodes, node_cap, lvl, inodes);
-    g_launches += 3;
+    k_moments_leaf<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, lvl, inodes, xs, ys, zs, ms, raw);
+    g_launches += 4;
     for (int level = kMaxLevel - 1; level >= 0; level--) {
         k_moments_level<<<nsm * 4, 256, 0, s>>>(level, lvl, inodes, kids, raw);
         g_launches++;
@@ -349,7 +400,7 @@ __global__ void __launch_bounds__(256) k_quad_level(int level, const uint32_t *_
                                                     const uint32_t *__restrict__ box_off, int nbox,
                                                     const BoxPar *__restrict__ bps, float4 *__restrict__ quad)
 {
-    const uint32_t b = lvl[32 + level], e = b + lvl[level];
+    const uint32_t b = lvl[64 + level], e = b + lvl[level];
     for (uint32_t i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
         const uint32_t p = inodes[i];
         const Node np = nodes[p];
