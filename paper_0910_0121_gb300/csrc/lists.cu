@@ -62,16 +62,17 @@ __device__ __forceinline__ Node load_node(const Node *p)
 }
 
 // Geometry of a cell against the group: the offset of its centre from the group's cell
-// centre (u, wrapped to the nearest image, with the image's shift), the squared gap to
-// the group's particle box, and the squared distance from its centre to the group cell
-// (both in u^2).  cell_gap computes what the prune test needs; the accept distance
-// follows only for cells that pass it.
+// centre (u, wrapped to the nearest image; with SHIFT also the image's shift code, which
+// only index entries record), the squared gap to the group's particle box, and the
+// squared distance from its centre to the group cell (both in u^2).  cell_gap computes
+// what the prune test needs; the accept distance follows only for cells that pass it.
 struct CellTest {
     int dx, dy, dz;
     unsigned shc;
     long long Sg;
 };
 
+template <bool SHIFT>
 __device__ __forceinline__ CellTest cell_gap(uint32_t ix, uint32_t iy, uint32_t iz, int h, const Group &gr,
                                              const int4 tb, const int4 th)
 {
@@ -80,7 +81,7 @@ __device__ __forceinline__ CellTest cell_gap(uint32_t ix, uint32_t iy, uint32_t 
     c.dx = wrap_delta(2 * (int)ix + h - gr.cx, sx);
     c.dy = wrap_delta(2 * (int)iy + h - gr.cy, sy);
     c.dz = wrap_delta(2 * (int)iz + h - gr.cz, sz);
-    c.shc = shift_code(sx, sy, sz);
+    c.shc = SHIFT ? shift_code(sx, sy, sz) : 0u;
     const int gx = max(0, abs(c.dx - tb.x) - h - th.x), gy = max(0, abs(c.dy - tb.y) - h - th.y),
               gz = max(0, abs(c.dz - tb.z) - h - th.z);
     c.Sg = (long long)gx * gx + (long long)gy * gy + (long long)gz * gz;
@@ -126,6 +127,8 @@ __device__ __forceinline__ int owner_lane(uint32_t off, uint32_t t)
 // accepted child is written as one entry at its centre of mass, and the others are
 // pushed.  Last, the particles of the popped leaves are spread over the lanes and each
 // goes through the per-particle r_cut test unless its whole leaf lies within r_cut.
+// INDEX: the index entries are written too (a.ilist).
+template <bool INDEX>
 __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb, const int4 th, const BoxPar &bp,
                                uint32_t root, uint32_t *__restrict__ stk, const uint8_t *__restrict__ octq,
                                unsigned long long pos0, unsigned long long lim, int lane, uint32_t &nacc)
@@ -180,8 +183,8 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
                 const uint32_t oct = octq[((plvl >> 13) & (255u << 3)) | q];
                 const int kc = (int)(plvl & 255u) + 1;
                 const int hc = 1 << (kMaxLevel - kc);
-                ct = cell_gap(pix + ((oct >> 2) & 1u) * (uint32_t)hc, piy + ((oct >> 1) & 1u) * (uint32_t)hc,
-                              piz + (oct & 1u) * (uint32_t)hc, hc, gr, tb, th);
+                ct = cell_gap<INDEX>(pix + ((oct >> 2) & 1u) * (uint32_t)hc, piy + ((oct >> 1) & 1u) * (uint32_t)hc,
+                                     piz + (oct & 1u) * (uint32_t)hc, hc, gr, tb, th);
                 if (ct.Sg <= Tp) {
                     child = __ldg(a.kids + (size_t)pm * 8 + q);
                     acc = kc >= lmin && cell_dist2(ct, gr) > bp.A[kc];
@@ -197,7 +200,7 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
                                              __fadd_rn(__fmul_rn((float)ct.dz, kf), v.z), v.w);
                 if (p < lim) {
                     a.flist[p] = e;
-                    if (a.ilist)
+                    if (INDEX)
                         a.ilist[p] = (unsigned long long)child | (1ull << 32) | ((unsigned long long)ct.shc << 33);
                 }
             }
@@ -218,10 +221,11 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
         // ---- particles of the popped leaves
         uint32_t ne = 0;
         float bx = 0.f, by = 0.f, bz = 0.f;
-        unsigned shc = 0;
+        unsigned shc = 0;   // test flag in bit 6; INDEX: the leaf's shift code in bits 0-5
+        int ox = 0, oy = 0, oz = 0;
         if (leaf) {
             const int h = 1 << (kMaxLevel - k);
-            const CellTest lc = cell_gap(nd.ix, nd.iy, nd.iz, h, gr, tb, th);
+            const CellTest lc = cell_gap<INDEX>(nd.ix, nd.iy, nd.iz, h, gr, tb, th);
             // a leaf whose whole cell lies within r_cut of the particle box keeps every
             // particle (each particle's finest cell is inside the leaf's cell)
             const int fx = max(0, abs(lc.dx - tb.x) + h - th.x), fy = max(0, abs(lc.dy - tb.y) + h - th.y),
@@ -232,6 +236,11 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
             by = __fmul_rn((float)lc.dy, kf);
             bz = __fmul_rn((float)lc.dz, kf);
             shc = lc.shc | (test_each ? 64u : 0u);
+            // a particle in finest cell c of this leaf sits at 2c + o (u) from the centre of
+            // the group's particle box, in the leaf's image
+            ox = lc.dx - 2 * (int)nd.ix - h + 1 - tb.x;
+            oy = lc.dy - 2 * (int)nd.iy - h + 1 - tb.y;
+            oz = lc.dz - 2 * (int)nd.iz - h + 1 - tb.z;
         }
         const uint32_t isum = warp_incl_scan(ne, lane);
         const uint32_t off = isum - ne;
@@ -244,6 +253,7 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
             const float bx_s = __shfl_sync(FULL, bx, s), by_s = __shfl_sync(FULL, by, s),
                         bz_s = __shfl_sync(FULL, bz, s);
             const unsigned sh_s = __shfl_sync(FULL, shc, s);
+            const int ox_s = __shfl_sync(FULL, ox, s), oy_s = __shfl_sync(FULL, oy, s), oz_s = __shfl_sync(FULL, oz, s);
             bool keep = false;
             float4 e;
             uint32_t j = kNone;
@@ -254,12 +264,9 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
                 if (sh_s & 64u) {
                     // the particle's finest cell, in its leaf's image, against the particle box
                     const unsigned long long c = __ldg(a.pcell + j);
-                    const int px = 2 * (int)((uint32_t)c & 0x1fffffu) + 1 - gr.cx - tb.x +
-                                   ((sh_s & 1u) ? kPeriod : ((sh_s & 2u) ? -kPeriod : 0));
-                    const int py = 2 * (int)((uint32_t)(c >> 21) & 0x1fffffu) + 1 - gr.cy - tb.y +
-                                   ((sh_s & 4u) ? kPeriod : ((sh_s & 8u) ? -kPeriod : 0));
-                    const int pz = 2 * (int)(uint32_t)(c >> 42) + 1 - gr.cz - tb.z +
-                                   ((sh_s & 16u) ? kPeriod : ((sh_s & 32u) ? -kPeriod : 0));
+                    const int px = 2 * (int)((uint32_t)c & 0x1fffffu) + ox_s;
+                    const int py = 2 * (int)((uint32_t)(c >> 21) & 0x1fffffu) + oy_s;
+                    const int pz = 2 * (int)(uint32_t)(c >> 42) + oz_s;
                     const int qx = max(0, abs(px) - 1 - th.x), qy = max(0, abs(py) - 1 - th.y),
                               qz = max(0, abs(pz) - 1 - th.z);
                     keep = (long long)qx * qx + (long long)qy * qy + (long long)qz * qz <= Tp;
@@ -272,7 +279,7 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
                 const unsigned long long p = pos0 + cnt + __popc(kb & lt);
                 if (p < lim) {
                     a.flist[p] = e;
-                    if (a.ilist) a.ilist[p] = (unsigned long long)j | ((unsigned long long)(sh_s & 63u) << 33);
+                    if (INDEX) a.ilist[p] = (unsigned long long)j | ((unsigned long long)(sh_s & 63u) << 33);
                 }
             }
             cnt += __popc(kb);
@@ -282,6 +289,7 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
     return cnt;
 }
 
+template <bool INDEX>
 __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(ListArgs a)
 {
     const unsigned FULL = 0xffffffffu;
@@ -311,7 +319,7 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
         const BoxPar &bp = a.bps[gr.box];
         const uint32_t root = a.base[bp.p_begin];
         uint32_t nacc = 0;
-        const uint32_t len = walk_group(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc);
+        const uint32_t len = walk_group<INDEX>(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc);
         const uint32_t padded = (len + 7u) & ~7u;
         if (lane == 0) atomicAdd(&a.st->sum_padded, (unsigned long long)padded);
         if (exhausted) {
@@ -341,11 +349,11 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
             }
             page_cur = first * a.page;
             page_end = (first + np) * a.page;
-            walk_group(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc);
+            walk_group<INDEX>(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc);
         }
         for (uint32_t t = len + lane; t < padded; t += 32) {
             a.flist[page_cur + t] = make_float4(16.f, 16.f, 16.f, 0.f);
-            if (a.ilist) a.ilist[page_cur + t] = ~0ull;
+            if (INDEX) a.ilist[page_cur + t] = ~0ull;
         }
         if (lane == 0) {
             a.loff[g] = page_cur;
@@ -361,7 +369,8 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
 
 void launch_lists(const ListArgs &a, cudaStream_t s, int nsm)
 {
-    k_lists<<<nsm * kListBlocksPerSM, kListWarps * 32, 0, s>>>(a);
+    if (a.ilist) k_lists<true><<<nsm * kListBlocksPerSM, kListWarps * 32, 0, s>>>(a);
+    else k_lists<false><<<nsm * kListBlocksPerSM, kListWarps * 32, 0, s>>>(a);
     g_launches++;
 }
 
