@@ -72,15 +72,17 @@ struct CellTest {
     long long Sg;
 };
 
+// rx, ry, rz: the cell centre minus the group's cell centre (u), before wrapping; h: the
+// cell's half side (u).
 template <bool SHIFT>
-__device__ __forceinline__ CellTest cell_gap(uint32_t ix, uint32_t iy, uint32_t iz, int h, const Group &gr,
-                                             const int4 tb, const int4 th)
+__device__ __forceinline__ CellTest cell_gap(int rx, int ry, int rz, int h, const Group &gr, const int4 tb,
+                                             const int4 th)
 {
     CellTest c;
     int sx, sy, sz;
-    c.dx = wrap_delta(2 * (int)ix + h - gr.cx, sx);
-    c.dy = wrap_delta(2 * (int)iy + h - gr.cy, sy);
-    c.dz = wrap_delta(2 * (int)iz + h - gr.cz, sz);
+    c.dx = wrap_delta(rx, sx);
+    c.dy = wrap_delta(ry, sy);
+    c.dz = wrap_delta(rz, sz);
     c.shc = SHIFT ? shift_code(sx, sy, sz) : 0u;
     const int gx = max(0, abs(c.dx - tb.x) - h - th.x), gy = max(0, abs(c.dy - tb.y) - h - th.y),
               gz = max(0, abs(c.dz - tb.z) - h - th.z);
@@ -162,6 +164,9 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
         const int k = nd.lvl & 255u;
         const bool leaf = valid && (nd.lvl & 256u) != 0;
         const uint32_t mask = valid && !leaf ? (nd.lvl >> 16) & 255u : 0u;
+        // the popped node's centre minus the group's cell centre (u, before wrapping)
+        const int hn = 1 << (kMaxLevel - k);
+        const int ncx = 2 * (int)nd.ix + hn - gr.cx, ncy = 2 * (int)nd.iy + hn - gr.cy, ncz = 2 * (int)nd.iz + hn - gr.cz;
 
         // ---- children of the opened nodes: prune, accept (one entry), or push
         const uint32_t nch = __popc(mask);
@@ -172,9 +177,9 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
             const uint32_t t = c0 + lane;
             const int s = owner_lane(coff, t);
             const uint32_t o_s = __shfl_sync(FULL, coff, s);
-            const uint32_t pix = __shfl_sync(FULL, nd.ix, s), piy = __shfl_sync(FULL, nd.iy, s),
-                           piz = __shfl_sync(FULL, nd.iz, s), plvl = __shfl_sync(FULL, nd.lvl, s),
-                           pm = __shfl_sync(FULL, m, s);
+            const int pcx = __shfl_sync(FULL, ncx, s), pcy = __shfl_sync(FULL, ncy, s),
+                      pcz = __shfl_sync(FULL, ncz, s);
+            const uint32_t plvl = __shfl_sync(FULL, nd.lvl, s), pm = __shfl_sync(FULL, m, s);
             bool acc = false, push = false;
             uint32_t child = 0;
             CellTest ct;
@@ -183,8 +188,9 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
                 const uint32_t oct = octq[((plvl >> 13) & (255u << 3)) | q];
                 const int kc = (int)(plvl & 255u) + 1;
                 const int hc = 1 << (kMaxLevel - kc);
-                ct = cell_gap<INDEX>(pix + ((oct >> 2) & 1u) * (uint32_t)hc, piy + ((oct >> 1) & 1u) * (uint32_t)hc,
-                                     piz + (oct & 1u) * (uint32_t)hc, hc, gr, tb, th);
+                // a child's centre is its parent's shifted by +-hc per axis
+                ct = cell_gap<INDEX>(pcx + ((oct & 4u) ? hc : -hc), pcy + ((oct & 2u) ? hc : -hc),
+                                     pcz + ((oct & 1u) ? hc : -hc), hc, gr, tb, th);
                 if (ct.Sg <= Tp) {
                     child = __ldg(a.kids + (size_t)pm * 8 + q);
                     acc = kc >= lmin && cell_dist2(ct, gr) > bp.A[kc];
@@ -224,8 +230,8 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
         unsigned shc = 0;   // test flag in bit 6; INDEX: the leaf's shift code in bits 0-5
         int ox = 0, oy = 0, oz = 0;
         if (leaf) {
-            const int h = 1 << (kMaxLevel - k);
-            const CellTest lc = cell_gap<INDEX>(nd.ix, nd.iy, nd.iz, h, gr, tb, th);
+            const int h = hn;
+            const CellTest lc = cell_gap<INDEX>(ncx, ncy, ncz, h, gr, tb, th);
             // a leaf whose whole cell lies within r_cut of the particle box keeps every
             // particle (each particle's finest cell is inside the leaf's cell)
             const int fx = max(0, abs(lc.dx - tb.x) + h - th.x), fy = max(0, abs(lc.dy - tb.y) + h - th.y),
@@ -238,9 +244,9 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
             shc = lc.shc | (test_each ? 64u : 0u);
             // a particle in finest cell c of this leaf sits at 2c + o (u) from the centre of
             // the group's particle box, in the leaf's image
-            ox = lc.dx - 2 * (int)nd.ix - h + 1 - tb.x;
-            oy = lc.dy - 2 * (int)nd.iy - h + 1 - tb.y;
-            oz = lc.dz - 2 * (int)nd.iz - h + 1 - tb.z;
+            ox = lc.dx - ncx - gr.cx + 1 - tb.x;
+            oy = lc.dy - ncy - gr.cy + 1 - tb.y;
+            oz = lc.dz - ncz - gr.cz + 1 - tb.z;
         }
         const uint32_t isum = warp_incl_scan(ne, lane);
         const uint32_t off = isum - ne;
