@@ -156,7 +156,7 @@ def oracle_force_sample(T, prm, frac, seed):
     return t_sample, float(cnt.sum()) / float(cnt[sel].sum()), ns, nthreads
 
 
-def oracle_sample(pos, mass, prm, n_crit, frac=0.0025, seed=7):
+def oracle_sample(pos, mass, prm, n_crit, frac=0.02, seed=7):
     """One oracle step on a bounded sample: S1-S4 on everything, S5-S6 on a group sample
     scaled to all groups.  Returns (seconds for the whole step, description, threads)."""
     T, t_tree = oracle_tree(pos, mass, prm, n_crit)

@@ -121,13 +121,17 @@ __device__ __forceinline__ double wrap_pos(double x, double L)
     return r;
 }
 
+// The FP64 formula as a real call: inlined, the compiler may predicate it, and every
+// lane then issues its FP64 instructions (64 cycles per warp instruction on this GPU).
+static __device__ __noinline__ double wrap_pos_call(double x, double L) { return wrap_pos(x, L); }
+
 // Wrap with the in-range test done on the bit pattern (non-negative doubles order like
 // their bits): x in [0, L) returns x unchanged; anything else takes the FP64 formula.
 __device__ __forceinline__ double wrap_pos_fast(double x, double L)
 {
     const long long bx = __double_as_longlong(x), bl = __double_as_longlong(L);
     if (bx >= 0 && bx < bl) return x;
-    return wrap_pos(x, L);
+    return wrap_pos_call(x, L);
 }
 
 // Box of sorted/input particle i: box_off holds nbox+1 increasing offsets.

@@ -449,6 +449,16 @@ void launch_quadrupoles(const Node *nodes, const uint32_t *n_nodes, uint32_t nod
 
 // Each particle's offset from the centre of its leaf cell (level K_i) in eta units: the
 // FP64 subtraction is done once per particle, then rounded to FP32 for the list builder.
+// The general-L form is a real call so that it is not predicated into the integer form's
+// lanes (FP64 instructions are slow on this GPU).
+static __device__ __noinline__ float4 leaf_offset_fp64(double x, double y, double z, float m, uint32_t cx,
+                                                       uint32_t cy, uint32_t cz, double u, double ie)
+{
+    const double cxa = __dmul_rn((double)cx, u), cya = __dmul_rn((double)cy, u), cza = __dmul_rn((double)cz, u);
+    return make_float4((float)__dmul_rn(__dsub_rn(x, cxa), ie), (float)__dmul_rn(__dsub_rn(y, cya), ie),
+                       (float)__dmul_rn(__dsub_rn(z, cza), ie), m);
+}
+
 __global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ K8,
                                                       uint32_t N, const uint32_t *__restrict__ box_off, int nbox,
                                                       const BoxPar *__restrict__ bps, const double *__restrict__ xs,
@@ -475,10 +485,7 @@ __global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict
                               __ll2float_rn(fixed52(zs[i], e) - ((long long)cz << 30)) * s, ms[i]);
         return;
     }
-    const double u = bp.u, ie = bp.inv_eta;
-    const double cxa = __dmul_rn((double)cx, u), cya = __dmul_rn((double)cy, u), cza = __dmul_rn((double)cz, u);
-    poff[i] = make_float4((float)__dmul_rn(__dsub_rn(xs[i], cxa), ie), (float)__dmul_rn(__dsub_rn(ys[i], cya), ie),
-                          (float)__dmul_rn(__dsub_rn(zs[i], cza), ie), ms[i]);
+    poff[i] = leaf_offset_fp64(xs[i], ys[i], zs[i], ms[i], cx, cy, cz, bp.u, bp.inv_eta);
 }
 
 void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
@@ -487,6 +494,16 @@ void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, co
 {
     k_leaf_offsets<<<(N + 255) / 256, 256, 0, s>>>(keys, K8, N, box_off, nbox, bps, xs, ys, zs, ms, poff, pcell);
     g_launches++;
+}
+
+// COM offset from the cell centre for a general L (FP64), as a real call (see
+// leaf_offset_fp64).
+static __device__ __noinline__ float4 node_offset_fp64(double cx, double cy, double cz, float m, uint32_t ux,
+                                                       uint32_t uy, uint32_t uz, double u, double ie)
+{
+    const double cxa = __dmul_rn((double)ux, u), cya = __dmul_rn((double)uy, u), cza = __dmul_rn((double)uz, u);
+    return make_float4((float)__dmul_rn(__dsub_rn(cx, cxa), ie), (float)__dmul_rn(__dsub_rn(cy, cya), ie),
+                       (float)__dmul_rn(__dsub_rn(cz, cza), ie), m);
 }
 
 // COM = S/M (the cell centre for a massless node), and the COM's offset from the node's
@@ -504,17 +521,18 @@ __global__ void __launch_bounds__(256) k_node_finish(const Node *__restrict__ no
         const BoxPar &bp = bps[box_of(nd.begin, box_off, nbox)];
         const int k = nd.lvl & 255u;
         const uint32_t h = 1u << (kMaxLevel - k);
-        const double u = bp.u, ie = bp.inv_eta;
-        const double cxa = __dmul_rn((double)(2u * nd.ix + h), u);
-        const double cya = __dmul_rn((double)(2u * nd.iy + h), u);
-        const double cza = __dmul_rn((double)(2u * nd.iz + h), u);
         const Dbl4 r = raw[n];
-        double cx = cxa, cy = cya, cz = cza;
+        double cx, cy, cz;
         if (r.w > 0.0) {
             const double inv = 1.0 / r.w;
             cx = r.x * inv;
             cy = r.y * inv;
             cz = r.z * inv;
+        } else {
+            // no mass: the cell centre stands in for the centre of mass
+            cx = __dmul_rn((double)(2u * nd.ix + h), bp.u);
+            cy = __dmul_rn((double)(2u * nd.iy + h), bp.u);
+            cz = __dmul_rn((double)(2u * nd.iz + h), bp.u);
         }
         mom64[n] = make_dbl4(cx, cy, cz, r.w);
         if (bp.pow2_e != kNotPow2) {
@@ -525,8 +543,8 @@ __global__ void __launch_bounds__(256) k_node_finish(const Node *__restrict__ no
                                   __ll2float_rn(fixed52(cy, e) - ((long long)(2u * nd.iy + h) << sh)) * s,
                                   __ll2float_rn(fixed52(cz, e) - ((long long)(2u * nd.iz + h) << sh)) * s, (float)r.w);
         } else {
-            noff[n] = make_float4((float)__dmul_rn(__dsub_rn(cx, cxa), ie), (float)__dmul_rn(__dsub_rn(cy, cya), ie),
-                                  (float)__dmul_rn(__dsub_rn(cz, cza), ie), (float)r.w);
+            noff[n] = node_offset_fp64(cx, cy, cz, (float)r.w, 2u * nd.ix + h, 2u * nd.iy + h, 2u * nd.iz + h, bp.u,
+                                       bp.inv_eta);
         }
     }
 }
