@@ -68,6 +68,9 @@ CASES = {
     "boxL3": lambda: (*clustered(3001, 9, L=3.0), dict(L=3.0, r_cut=0.4, theta=0.7, n_crit=40, n_leaf=6)),
     "crit1": lambda: (*clustered(700, 5), dict(L=1.0, r_cut=0.2, theta=0.4, n_crit=1, n_leaf=1)),
     "bigcrit": lambda: (*clustered(4000, 6), dict(L=1.0, r_cut=0.15, theta=0.5, n_crit=700, n_leaf=20)),
+    # leaves of up to 99 particles: the tree's window levels beyond the shared-memory
+    # halo, and leaf moments in the >= 31-particle bucket
+    "bigleaf": lambda: (*clustered(5000, 8), dict(L=1.0, r_cut=0.12, theta=0.5, n_crit=400, n_leaf=100)),
 }
 
 
@@ -251,6 +254,35 @@ def test_batched_equals_single_boxes(ctx):
     off = np.cumsum([0] + [len(b[0]) for b in boxes])
     per = [greem.params(**prm) for prm in prms]
     acc = ctx.short_force_batched(_t(pos, np.float64), _t(mass, np.float32), off, per)
+    torch.cuda.synchronize()
+    acc = acc.cpu().numpy().astype(np.float64)
+    for b in range(len(boxes)):
+        assert np.array_equal(acc[off[b]:off[b + 1]], singles[b])
+
+
+def test_batched_boxes_with_mixed_leaf_sizes(ctx):
+    """Boxes with different N_leaf side by side in one call (a block of the tree builder
+    then spans boxes with different windows, some beyond the shared-memory halo): the
+    tree and the force equal the single-box calls."""
+    boxes = [clustered(n, 50 + n) for n in (900, 2100, 1300, 700)]
+    prms = [dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=nc, n_leaf=nl) for nc, nl in
+            ((64, 6), (300, 100), (64, 10), (200, 70))]
+    singles, nodes = [], []
+    for (p, m), prm in zip(boxes, prms):
+        singles.append(gpu_force(ctx, p, m, prm, flags=0))
+        T = oracle.Tree(p, m, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm["n_leaf"])
+        nodes.append(T.nodes())
+        T.build_lists(prm["theta"])
+        e = rel_err(singles[-1], T.list_force_input_order())
+        assert np.median(e) <= MED_BOUND and np.quantile(e, 0.999) <= P999_BOUND
+    # each single-box tree is the oracle's
+    for (p, m), prm, on in zip(boxes, prms, nodes):
+        gpu_force(ctx, p, m, prm)
+        assert np.array_equal(ctx.dump(greem.DUMP_NODES)[:, :8], on[:, :8])
+    pos = np.concatenate([b[0] for b in boxes])
+    mass = np.concatenate([b[1] for b in boxes])
+    off = np.cumsum([0] + [len(b[0]) for b in boxes])
+    acc = ctx.short_force_batched(_t(pos, np.float64), _t(mass, np.float32), off, [greem.params(**q) for q in prms])
     torch.cuda.synchronize()
     acc = acc.cpu().numpy().astype(np.float64)
     for b in range(len(boxes)):
