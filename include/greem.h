@@ -178,7 +178,11 @@ typedef struct greem_stats {
     int64_t kernel_launches;  /* kernels launched by the last call */
     int32_t l_min;            /* shallowest group level of box 0 */
     int32_t retries;          /* capacity retries of the last call */
-    double ms_keys, ms_sort, ms_tree, ms_groups, ms_lists, ms_force, ms_total; /* with STAGE_TIMES */
+    /* with STAGE_TIMES, by events on the context's stream: keys; sort and gather; tree,
+     * moments and node COM offsets; groups (particle offsets and groups run on a second
+     * stream beside the moments: what remains of them after the moments, and the
+     * second-order moments); lists; force (and PM); total */
+    double ms_keys, ms_sort, ms_tree, ms_groups, ms_lists, ms_force, ms_total;
 } greem_stats;
 
 /* Counters of the last call.  Errors: INVALID_ARG for NULL arguments. */

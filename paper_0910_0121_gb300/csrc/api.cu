@@ -34,6 +34,10 @@ struct greem_ctx {
     int nsm = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;  // private stream for graph capture on the legacy stream
+    // second stream of a call: the particle offsets and the groups run on it beside the
+    // moments (fork and join by events, so the whole call stays capturable)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // S1-S2
     DBuf<uint64_t> k0, k1;
@@ -435,22 +439,30 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     const uint32_t *n_nodes = c->base.p + N;
     launch_tree_fill(ks, N, c->box_off.p, nbox, c->d8.p, c->K8.p, c->base.p, c->nodes.p, ncap, c->st.p, s, nsm);
     launch_tree_links(c->nodes.p, n_nodes, ncap, c->nchild.p, c->kids.p, s, nsm);
+    // fork: the moments (FP64-bound) on s; the particle offsets and the groups (integer
+    // work, reading only the tree) on the second stream
+    cudaStream_t s2 = c->aux;
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(s2, c->ev_fork, 0);
+    launch_leaf_offsets(ks, c->K8.p, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->poff.p,
+                        c->pcell.p, s2);
+    launch_group_flags(c->nodes.p, n_nodes, ncap, c->box_off.p, nbox, c->bps.p, c->gflag.p, s2, nsm);
+    scan_u32(c->gflag.p, c->gidx.p, ncap, c->scratch.p, s2);
+    const uint32_t *n_groups = c->gidx.p + ncap;
+    launch_group_fill(c->nodes.p, n_nodes, ncap, c->gflag.p, c->gidx.p, c->box_off.p, nbox, c->groups.p, s2, nsm);
+    launch_group_box(c->groups.p, n_groups, c->pcell.p, c->gbox.p, s2, nsm);
+    launch_record_counts(n_nodes, n_groups, c->st.p, ncap, s2);
+    cudaEventRecord(c->ev_join, s2);
     launch_moments(c->nodes.p, n_nodes, ncap, c->kids.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p, c->lvl.p,
                    c->ctr.p, s, nsm);
-    launch_leaf_offsets(ks, c->K8.p, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->poff.p,
-                        c->pcell.p, s);
     launch_node_finish(c->nodes.p, n_nodes, ncap, c->raw.p, c->box_off.p, nbox, c->bps.p, c->mom64.p, c->noff.p, s,
                        nsm);
+    ev_record(c, r, ev, 3);
+    // join: what the second stream still had to do counts as the groups stage
+    cudaStreamWaitEvent(s, c->ev_join, 0);
     if (r.quad)
         launch_quadrupoles(c->nodes.p, n_nodes, ncap, c->kids.p, c->poff.p, c->noff.p, c->lvl.p, c->ctr.p,
                            c->box_off.p, nbox, c->bps.p, c->quad.p, s, nsm);
-    ev_record(c, r, ev, 3);
-    launch_group_flags(c->nodes.p, n_nodes, ncap, c->box_off.p, nbox, c->bps.p, c->gflag.p, s, nsm);
-    scan_u32(c->gflag.p, c->gidx.p, ncap, c->scratch.p, s);
-    const uint32_t *n_groups = c->gidx.p + ncap;
-    launch_group_fill(c->nodes.p, n_nodes, ncap, c->gflag.p, c->gidx.p, c->box_off.p, nbox, c->groups.p, s, nsm);
-    launch_group_box(c->groups.p, n_groups, c->pcell.p, c->gbox.p, s, nsm);
-    launch_record_counts(n_nodes, n_groups, c->st.p, ncap, s);
     ev_record(c, r, ev, 4);
     if (r.lists_force) {
         ListArgs la;
@@ -688,6 +700,12 @@ int greem_create(greem_ctx **out, void *cuda_stream)
         return GREEM_ERR_OOM;
     }
     memset(c->st_host, 0, sizeof(DevStatus));
+    if (!cuda_ok(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) ||
+        !cuda_ok(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) ||
+        !cuda_ok(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming))) {
+        greem_destroy(c);
+        return GREEM_ERR_CUDA;
+    }
     *out = c;
     return GREEM_OK;
 }
@@ -700,6 +718,10 @@ void greem_destroy(greem_ctx *c)
     pm_plan_destroy(c->pm);
     release(c->pm_grid); release(c->pm_table); release(c->pm_spec); release(c->pm_tmp);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->aux) cudaStreamSynchronize(c->aux);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     release(c->k0); release(c->k1); release(c->v0); release(c->v1); release(c->hist); release(c->scratch);
     release(c->rs_status);
     release(c->xs); release(c->ys); release(c->zs); release(c->ms);
