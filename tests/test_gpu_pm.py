@@ -73,6 +73,30 @@ def test_treepm_in_one_call_equals_pp_plus_pm(ctx):
     assert np.all(np.linalg.norm(b - s, axis=1) <= 1e-5 * scale + 2e-6 * pm_rms)
 
 
+def test_treepm_graph_replay_equals_direct_call(ctx):
+    """The one-call TreePM step captured as a CUDA graph (the 512^3 benchmark runs it this
+    way) replays to the direct call's result on new positions."""
+    pos, mass = clustered(20000, 9)
+    n, rc = 32, 3.0 / 32
+    p = greem.params(L=1.0, r_cut=rc, theta=0.5, n_crit=64, flags=greem.FLAG_ADD_PM, n_pm=n,
+                     assign=greem.ASSIGN_TSC)
+    P, M = _t(pos, np.float64), _t(mass, np.float32)
+    acc = torch.zeros((len(pos), 3), dtype=torch.float32, device="cuda")
+    ctx.short_force(P, M, p, acc)   # plans and tables exist before the capture
+    ctx.graph_capture(P, M, p, acc)
+    newpos = np.mod(pos + 0.0037, 1.0)
+    P.copy_(_t(newpos, np.float64))
+    acc.zero_()
+    assert ctx.graph_launch() == greem.OK
+    torch.cuda.synchronize()
+    g = acc.cpu().numpy().astype(np.float64)
+    d = ctx.short_force(_t(newpos, np.float64), M, p).cpu().numpy().astype(np.float64)
+    pmf = ctx.pm_force(P, M, 1.0, n, rc, greem.ASSIGN_TSC).cpu().numpy().astype(np.float64)
+    pm_rms = float(np.sqrt(np.mean(np.sum(pmf ** 2, axis=1))))
+    # the only difference allowed: the order of the PM assignment's FP32 atomics
+    assert np.all(np.linalg.norm(g - d, axis=1) <= 1e-6 * np.linalg.norm(d, axis=1) + 2e-6 * pm_rms)
+
+
 def test_treepm_total_force_against_ewald(ctx):
     """Total TreePM force vs the Ewald sum (Sec. 3.1.2 method): with TSC and theta = 0.5 the
     error of 90% of the particles stays below 2%, the paper's accuracy goal."""
