@@ -10,6 +10,8 @@
 //   g(R) = v^5 C(R) + u^6 P(R),  C = (8/35)(7R^3 + 22R^2 + 10R + 4),  P = (7R^2 + 18R + 3)/35,
 // a sum of two non-negative terms for every R >= 0 that is exactly 0 for R >= 2.  The
 // relative error of g therefore stays at a few ulp even where g -> 0 near the cutoff.
+// The kernels need g(R)/R^3 = v^5 C(R)/R^3 + u^6 P(R)/R^3, and both quotients are
+// polynomials in 1/R with positive coefficients, evaluated by Horner's rule in 1/R.
 //
 // Two forms of the pair loop.  With an even number I of i-particles per lane, pairs of
 // i-particles share the sm_100-family packed FP32x2 instructions (two FP32 operations
@@ -168,17 +170,6 @@ __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
     asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-// max(x, 0) of both halves as a signed-integer max on the bit patterns (a negative float
-// is a negative integer; the result is +0), on the integer pipe instead of the FP32 pipe
-__device__ __forceinline__ f32x2 relu2(f32x2 v)
-{
-    f32x2 d;
-    asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmax.s32 lo, lo, 0;\n\tmax.s32 hi, hi, 0;\n\t"
-        "mov.b64 %0, {lo, hi};\n\t}"
-        : "=l"(d)
-        : "l"(v));
-    return d;
-}
 __device__ __forceinline__ f32x2 rsqrt2(f32x2 v)
 {
     float lo, hi;
@@ -200,31 +191,39 @@ __device__ __forceinline__ void interact2(const float4 j, const f32x2 (&xi)[H], 
                                           const f32x2 eps2)
 {
     const f32x2 jx = pk(j.x, j.x), jy = pk(j.y, j.y), jz = pk(j.z, j.z), jm = pk(j.w, j.w);
-    const f32x2 k[11] = {pk(kR2Floor, kR2Floor), pk(1.0f, 1.0f), pk(-0.5f, -0.5f), pk(-1.0f, -1.0f), pk(kC3, kC3),
-                         pk(kC2, kC2),           pk(kC1, kC1),   pk(kC0, kC0),     pk(kP2, kP2),     pk(kP1, kP1),
-                         pk(kP0, kP0)};
+    const f32x2 k[9] = {pk(kR2Floor, kR2Floor), pk(1.0f, 1.0f), pk(kC3, kC3), pk(kC2, kC2), pk(kC1, kC1),
+                        pk(kC0, kC0),           pk(kP2, kP2),   pk(kP1, kP1), pk(kP0, kP0)};
 #pragma unroll
     for (int h = 0; h < H; h++) {
         const f32x2 dx = sub2(jx, xi[h]), dy = sub2(jy, yi[h]), dz = sub2(jz, zi[h]);
         const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, k[0])));
         const f32x2 rinv = rsqrt2(r2);
         const f32x2 R = mul2(r2, rinv);
-        const f32x2 v = relu2(fma2(R, k[2], k[1]));
-        const f32x2 u = relu2(fma2(R, k[3], k[1]));
-        const f32x2 c = fma2(fma2(fma2(R, k[4], k[5]), R, k[6]), R, k[7]);
-        const f32x2 p = fma2(fma2(R, k[8], k[9]), R, k[10]);
+        // v and u as two scalar saturating operations each: the clamp rides on the FP32
+        // instruction, where a packed operation and a separate max would take twice the
+        // issue slots (the packed forms have no .sat)
+        float Rl, Rh;
+        upk(R, Rl, Rh);
+        const f32x2 v = pk(fma_sat(Rl, -0.5f, 1.0f), fma_sat(Rh, -0.5f, 1.0f));
+        const f32x2 u = pk(add_sat(1.0f, -Rl), add_sat(1.0f, -Rh));
         const f32x2 v2 = mul2(v, v), v5 = mul2(mul2(v2, v2), v);
         const f32x2 u2 = mul2(u, u), u6 = mul2(mul2(u2, u2), u2);
-        const f32x2 g = fma2(u6, p, mul2(v5, c));
-        f32x2 ri3;
+        f32x2 sc;
         if (!SOFT) {
-            ri3 = mul2(mul2(rinv, rinv), rinv);
+            // g(R)/R^3 = v^5 C(R)/R^3 + u^6 P(R)/R^3 with both quotients as polynomials in
+            // 1/R (positive coefficients, no cancellation): two FP32 operations per pair
+            // fewer than g(R) times 1/R^3
+            const f32x2 cq = fma2(fma2(fma2(rinv, k[5], k[4]), rinv, k[3]), rinv, k[2]);
+            const f32x2 pq = mul2(fma2(fma2(rinv, k[8], k[7]), rinv, k[6]), rinv);
+            sc = mul2(jm, fma2(u6, pq, mul2(v5, cq)));
         } else {
-            // Plummer softening: 1/(r^2+eps^2)^(3/2), g at the unsoftened R
+            // Plummer softening: g at the unsoftened R times 1/(r^2+eps^2)^(3/2)
+            const f32x2 c = fma2(fma2(fma2(R, k[2], k[3]), R, k[4]), R, k[5]);
+            const f32x2 p = fma2(fma2(R, k[6], k[7]), R, k[8]);
+            const f32x2 g = fma2(u6, p, mul2(v5, c));
             const f32x2 rs = rsqrt2(fma2(k[1], eps2, r2));
-            ri3 = mul2(mul2(rs, rs), rs);
+            sc = mul2(mul2(jm, g), mul2(mul2(rs, rs), rs));
         }
-        const f32x2 sc = mul2(mul2(jm, g), ri3);
         ax[h] = fma2(sc, dx, ax[h]);
         ay[h] = fma2(sc, dy, ay[h]);
         az[h] = fma2(sc, dz, az[h]);
@@ -242,10 +241,15 @@ __device__ __forceinline__ void interact(const float4 j, const float (&xi)[I], c
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         float sc;
         if (!SOFT) {
+            // g(R)/R^3 in the form of the packed loop
             const float rinv = rsqrtf(r2);
-            const float g = g_p3m(r2 * rinv);
-            const float rinv3 = rinv * rinv * rinv;
-            sc = (r2 > 0.0f) ? (j.w * g) * rinv3 : 0.0f;
+            const float R = r2 * rinv;
+            const float v = fma_sat(R, -0.5f, 1.0f), u = add_sat(1.0f, -R);
+            const float v2 = v * v, u2 = u * u;
+            const float cq = fmaf(fmaf(fmaf(rinv, kC0, kC1), rinv, kC2), rinv, kC3);
+            const float pq = fmaf(fmaf(rinv, kP0, kP1), rinv, kP2) * rinv;
+            const float F = fmaf(u2 * u2 * u2, pq, (v2 * v2 * v) * cq);
+            sc = (r2 > 0.0f) ? j.w * F : 0.0f;
         } else {
             // Plummer softening: 1/(r^2+eps^2)^(3/2), g at the unsoftened R
             const float rs = rsqrtf(r2 + eps2);
