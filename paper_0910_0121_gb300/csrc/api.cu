@@ -224,10 +224,11 @@ static int derive_box(const greem_params &p, uint32_t pb, uint32_t pe, BoxPar &b
     bp.eta = 0.5 * p.r_cut;
     bp.inv_eta = 1.0 / bp.eta;
     bp.eps = p.eps;
-    bp.k_f = (float)(bp.u / bp.eta);
-    bp.k52_f = (float)(std::ldexp(p.L, -52) / bp.eta);
-    bp.inv_eta2 = (float)(bp.inv_eta * bp.inv_eta);
-    bp.eps2 = (float)((p.eps / bp.eta) * (p.eps / bp.eta));
+    bp.inv_rc = 1.0 / p.r_cut;
+    bp.k_f = (float)(bp.u / p.r_cut);
+    bp.k52_f = (float)(std::ldexp(p.L, -52) / p.r_cut);
+    bp.inv_rc2 = (float)(bp.inv_rc * bp.inv_rc);
+    bp.eps2 = (float)((p.eps / p.r_cut) * (p.eps / p.r_cut));
     bp.soft = p.eps > 0 ? 1 : 0;
     // r_cut pruning: prune iff (double)S_gap * (u*u) > r_cut*r_cut
     bp.T_prune = max_s_le(bp.u * bp.u, p.r_cut * p.r_cut);
@@ -979,7 +980,7 @@ int greem_debug_dump(greem_ctx *c, int what, void *host_buf, int64_t cap_bytes, 
         int b = 0;
         for (uint32_t n = 0; n < nn; n++) {
             while (b + 1 < c->last_nbox && hn[n].begin >= c->box_off_host[b + 1]) b++;
-            const double e2 = c->bps_host[b].eta * c->bps_host[b].eta;  // eta^2 units -> physical
+            const double rc = 2.0 * c->bps_host[b].eta, e2 = rc * rc;  // r_cut^2 units -> physical
             const float4 q0 = h[2 * (size_t)n], q1 = h[2 * (size_t)n + 1];
             o[6 * n + 0] = q0.x * e2;
             o[6 * n + 1] = q0.y * e2;
@@ -1210,14 +1211,15 @@ int greem_pair_force_f32(greem_ctx *c, const double *x_g, const double *x_i, con
     memset(&bp, 0, sizeof(bp));
     bp.eta = 0.5 * r_cut;
     bp.inv_eta = 1.0 / bp.eta;
-    bp.inv_eta2 = (float)(bp.inv_eta * bp.inv_eta);
+    bp.inv_rc = 1.0 / r_cut;
+    bp.inv_rc2 = (float)(bp.inv_rc * bp.inv_rc);
     bp.eps = eps;
-    bp.eps2 = (float)((eps / bp.eta) * (eps / bp.eta));
+    bp.eps2 = (float)((eps / r_cut) * (eps / r_cut));
     cudaStream_t s = c->stream;
     greem::g_launches = 0;
     cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s);
     cudaMemcpyAsync(c->bps.p, c->bps_host, sizeof(BoxPar), cudaMemcpyHostToDevice, s);
-    launch_pair_setup(x_g, x_i, x_j, m_j, (uint32_t)np, bp.inv_eta, c->groups.p, c->irel.p, c->flist.p, c->loff.p,
+    launch_pair_setup(x_g, x_i, x_j, m_j, (uint32_t)np, bp.inv_rc, c->groups.p, c->irel.p, c->flist.p, c->loff.p,
                       c->llen.p, c->lraw.p, c->v0.p, c->small.p, s);
     ForceArgs fa;
     memset(&fa, 0, sizeof(fa));

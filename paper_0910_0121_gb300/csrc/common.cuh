@@ -43,11 +43,13 @@ static_assert(sizeof(Group) == 32, "Group must be 32 bytes");
 
 // Per-box constants, derived on the host from greem_params.
 struct BoxPar {
-    double L, inv_L, u, eta, inv_eta, eps;
-    float k_f;             // u/eta rounded to float: cell offsets -> eta units
-    float k52_f;           // (L/2^52)/eta rounded to float: fixed52 offsets -> eta units
-    float inv_eta2;        // 1/eta^2: eta-unit accelerations -> physical
-    float eps2;            // (eps/eta)^2
+    // The FP32 path works in units of r_cut (offsets, list entries, i-particles); the FP64
+    // form and Eq. 12 work in units of eta = r_cut/2.
+    double L, inv_L, u, eta, inv_eta, inv_rc, eps;
+    float k_f;             // u/r_cut rounded to float: cell offsets -> r_cut units
+    float k52_f;           // (L/2^52)/r_cut rounded to float: fixed52 offsets -> r_cut units
+    float inv_rc2;         // 1/r_cut^2: r_cut-unit accelerations -> physical
+    float eps2;            // (eps/r_cut)^2
     long long T_prune;     // prune a node iff S_gap > T_prune (exact form of the r_cut test)
     long long A[22];       // accept a node of level k iff S_d > A[k] (exact form of the theta test)
     uint32_t p_begin, p_end;
@@ -206,8 +208,8 @@ struct ListArgs {
     const uint32_t *kids;      // child table, 8 slots per node (kNone = unused)
     uint32_t *stack;           // per-warp traversal stacks
     uint32_t stack_cap;        // entries per warp stack
-    const float4 *poff;        // per sorted particle: offset from its leaf centre (eta units), mass
-    const float4 *noff;        // per node: COM offset from its cell centre (eta units), mass
+    const float4 *poff;        // per sorted particle: offset from its leaf centre (r_cut units), mass
+    const float4 *noff;        // per node: COM offset from its cell centre (r_cut units), mass
     const unsigned long long *pcell;  // per sorted particle: finest cell, x | y << 21 | z << 42
     const int4 *gbox;          // per group: particle box centre minus cell centre, then half sides (u)
     float4 *flist;             // list pool, FP32 relative entries
@@ -259,7 +261,7 @@ void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft, bo
 void launch_qlist_fill(const ForceArgs &a, const float4 *quad, unsigned long long qcap, cudaStream_t s, int nsm);
 void launch_force_f64(const ForceArgs &a, cudaStream_t s, int nsm);
 void launch_pair_setup(const double *xg, const double *xi, const double *xj, const float *mj, uint32_t np,
-                       double inv_eta, Group *groups, float4 *irel, float4 *flist, unsigned long long *loff,
+                       double inv_rc, Group *groups, float4 *irel, float4 *flist, unsigned long long *loff,
                        uint32_t *llen, uint32_t *lraw, uint32_t *perm, uint32_t *n_groups, cudaStream_t s);
 double peak_tflops(int which, int nsm, cudaStream_t s, int *err);
 

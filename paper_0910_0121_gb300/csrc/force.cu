@@ -1,22 +1,24 @@
 // S6 pairwise cutoff force over the interaction lists (Sec. 2.1 Eq. 1-2; Sec. 3.1.1).
 //
-// FP32 kernel.  Positions are in eta units relative to the group's cell centre (the
-// list builder did the FP64 work), so with R = r/eta
-//   acc_i = (1/eta^2) sum_j m_j g(R) D / R^3 ,   D = X_j - X_i .
+// FP32 kernel.  Positions are in units of r_cut = 2 eta relative to the group's cell
+// centre (the list builder did the FP64 work), so with xi = r/r_cut and R = r/eta = 2 xi
+//   acc_i = (1/r_cut^2) sum_j m_j g(2 xi) D / xi^3 ,   D = X_j - X_i .
 // Eq. 2 is evaluated without cancellation.  Its outer branch factors exactly as
 //   g(R) = (2-R)^5 (7R^3 + 22R^2 + 10R + 4) / 140            (1 <= R < 2),
 // and the inner branch is the outer one plus (1-R)^6 (7R^2 + 18R + 3) / 35, so with
-// v = saturate(1 - R/2) and u = saturate(1 - R)
+// v = saturate(1 - R/2) = saturate(1 - xi) and u = saturate(1 - R) = saturate(2v - 1)
 //   g(R) = v^5 C(R) + u^6 P(R),  C = (8/35)(7R^3 + 22R^2 + 10R + 4),  P = (7R^2 + 18R + 3)/35,
 // a sum of two non-negative terms for every R >= 0 that is exactly 0 for R >= 2.  The
 // relative error of g therefore stays at a few ulp even where g -> 0 near the cutoff.
-// The kernels need g(R)/R^3 = v^5 C(R)/R^3 + u^6 P(R)/R^3, and both quotients are
-// polynomials in 1/R with positive coefficients, evaluated by Horner's rule in 1/R.
+// The kernels need g(2 xi)/xi^3 = v^5 C(2 xi)/xi^3 + u^6 P(2 xi)/xi^3, and with w = 1/xi
+// both quotients are polynomials in w with positive coefficients:
+//   Chat(w) = (8/35)(4w^3 + 20w^2 + 88w + 56),   Phat(w) = (3w^3 + 36w^2 + 28w)/35,
+// evaluated by Horner's rule.  v comes from r^2 and w without forming xi.
 //
 // Two forms of the pair loop.  With an even number I of i-particles per lane, pairs of
 // i-particles share the sm_100-family packed FP32x2 instructions (two FP32 operations
 // per instruction: half the issue slots, the FP32 pipe is then the limit); r^2 gets a
-// floor of 2^-60 eta^2, so a pair at distance 0 (the particle itself, a coincident one)
+// floor of 2^-60 r_cut^2, so a pair at distance 0 (the particle itself, a coincident one)
 // adds exactly 0 without a select.  With odd I the scalar loop runs and such a pair is
 // selected out.
 //
@@ -97,13 +99,16 @@ constexpr int kImax = GREEM_FORCE_IMAX;
 constexpr int kUnroll = GREEM_FORCE_UNROLL;
 
 // ------------------------------------------------------------------ Eq. 2 constants
-constexpr float kC3 = 1.6f;                     // (8/35) * 7
-constexpr float kC2 = 5.028571428571428571f;    // (8/35) * 22
-constexpr float kC1 = 2.285714285714285714f;    // (8/35) * 10
-constexpr float kC0 = 0.914285714285714286f;    // (8/35) * 4
-constexpr float kP2 = 0.2f;                     //  7/35
-constexpr float kP1 = 0.514285714285714286f;    // 18/35
-constexpr float kP0 = 0.0857142857142857143f;   //  3/35
+// Chat(w) = ((kA3 w + kA2) w + kA1) w + kA0 and Phat(w) = ((kB3 w + kB2) w + kB1) w; the
+// same numbers in reverse order give C(2 xi) = ((kA0 xi + kA1) xi + kA2) xi + kA3 and
+// P(2 xi) = (kB1 xi + kB2) xi + kB3.
+constexpr float kA0 = 12.8f;                    // 448/35
+constexpr float kA1 = 20.11428571428571429f;    // 704/35
+constexpr float kA2 = 4.571428571428571429f;    // 160/35
+constexpr float kA3 = 0.9142857142857142857f;   //  32/35
+constexpr float kB1 = 0.8f;                     //  28/35
+constexpr float kB2 = 1.028571428571428571f;    //  36/35
+constexpr float kB3 = 0.08571428571428571429f;  //   3/35
 
 // saturate(a*b + c) and saturate(a + b) as single instructions (the .sat modifier clamps
 // to [0, 1] and turns NaN into 0)
@@ -118,20 +123,6 @@ __device__ __forceinline__ float add_sat(float a, float b)
     float d;
     asm("add.rn.ftz.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
     return d;
-}
-
-// g(R) of Eq. 2 for R >= 0 (see the header comment); 0 for R >= 2.
-__device__ __forceinline__ float g_p3m(float R)
-{
-    const float v = fma_sat(R, -0.5f, 1.0f);
-    const float v2 = v * v;
-    const float v5 = v2 * v2 * v;
-    const float c = fmaf(fmaf(fmaf(R, kC3, kC2), R, kC1), R, kC0);
-    const float u = add_sat(1.0f, -R);
-    const float u2 = u * u;
-    const float u6 = u2 * u2 * u2;
-    const float p = fmaf(fmaf(R, kP2, kP1), R, kP0);
-    return fmaf(u6, p, v5 * c);
 }
 
 // ------------------------------------------------------------------ packed FP32 pairs
@@ -178,48 +169,56 @@ __device__ __forceinline__ f32x2 rsqrt2(f32x2 v)
     asm("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(hi));
     return pk(lo, hi);
 }
-// r^2 gets 2^-60 (in eta^2) before the square root.  That is far below what FP32
-// coordinates relative to the group centre resolve (~1e-7 eta), and it keeps 1/r^3
+// r^2 gets 2^-60 (in r_cut^2) before the square root.  That is far below what FP32
+// coordinates relative to the group centre resolve (~1e-7 r_cut), and it keeps w^3
 // below 2^90, so a pair with D = 0 (the particle itself, a coincident particle) adds
 // exactly 0 without a select; masses must stay below 2^38 for that (checked on input).
 constexpr float kR2Floor = 8.673617379884035e-19f;  // 2^-60
 
+// v = saturate(1 - xi) from r^2 and w = 1/xi, and u = saturate(2v - 1), as scalar
+// saturating operations: the clamp rides on the FP32 instruction, where a packed
+// operation and a separate max would take twice the issue slots (the packed forms
+// have no .sat)
+__device__ __forceinline__ void vu_pair(f32x2 r2, f32x2 w, f32x2 &v, f32x2 &u)
+{
+    float rl, rh, wl, wh;
+    upk(r2, rl, rh);
+    upk(w, wl, wh);
+    const float vl = fma_sat(rl, -wl, 1.0f), vh = fma_sat(rh, -wh, 1.0f);
+    v = pk(vl, vh);
+    u = pk(fma_sat(vl, 2.0f, -1.0f), fma_sat(vh, 2.0f, -1.0f));
+}
+
 // Packed form of interact() for I = 2H i-particles: (xi[2h], xi[2h+1]) in xi2[h].
+// 26 FP32 operations per pair (without softening) and one rsqrt.
 template <int H, bool SOFT>
 __device__ __forceinline__ void interact2(const float4 j, const f32x2 (&xi)[H], const f32x2 (&yi)[H],
                                           const f32x2 (&zi)[H], f32x2 (&ax)[H], f32x2 (&ay)[H], f32x2 (&az)[H],
                                           const f32x2 eps2)
 {
     const f32x2 jx = pk(j.x, j.x), jy = pk(j.y, j.y), jz = pk(j.z, j.z), jm = pk(j.w, j.w);
-    const f32x2 k[9] = {pk(kR2Floor, kR2Floor), pk(1.0f, 1.0f), pk(kC3, kC3), pk(kC2, kC2), pk(kC1, kC1),
-                        pk(kC0, kC0),           pk(kP2, kP2),   pk(kP1, kP1), pk(kP0, kP0)};
+    const f32x2 k[9] = {pk(kR2Floor, kR2Floor), pk(1.0f, 1.0f), pk(kA0, kA0), pk(kA1, kA1), pk(kA2, kA2),
+                        pk(kA3, kA3),           pk(kB1, kB1),   pk(kB2, kB2), pk(kB3, kB3)};
 #pragma unroll
     for (int h = 0; h < H; h++) {
         const f32x2 dx = sub2(jx, xi[h]), dy = sub2(jy, yi[h]), dz = sub2(jz, zi[h]);
         const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, k[0])));
-        const f32x2 rinv = rsqrt2(r2);
-        const f32x2 R = mul2(r2, rinv);
-        // v and u as two scalar saturating operations each: the clamp rides on the FP32
-        // instruction, where a packed operation and a separate max would take twice the
-        // issue slots (the packed forms have no .sat)
-        float Rl, Rh;
-        upk(R, Rl, Rh);
-        const f32x2 v = pk(fma_sat(Rl, -0.5f, 1.0f), fma_sat(Rh, -0.5f, 1.0f));
-        const f32x2 u = pk(add_sat(1.0f, -Rl), add_sat(1.0f, -Rh));
+        const f32x2 w = rsqrt2(r2);
+        f32x2 v, u;
+        vu_pair(r2, w, v, u);
         const f32x2 v2 = mul2(v, v), v5 = mul2(mul2(v2, v2), v);
         const f32x2 u2 = mul2(u, u), u6 = mul2(mul2(u2, u2), u2);
         f32x2 sc;
         if (!SOFT) {
-            // g(R)/R^3 = v^5 C(R)/R^3 + u^6 P(R)/R^3 with both quotients as polynomials in
-            // 1/R (positive coefficients, no cancellation): two FP32 operations per pair
-            // fewer than g(R) times 1/R^3
-            const f32x2 cq = fma2(fma2(fma2(rinv, k[5], k[4]), rinv, k[3]), rinv, k[2]);
-            const f32x2 pq = mul2(fma2(fma2(rinv, k[8], k[7]), rinv, k[6]), rinv);
+            // g(2 xi)/xi^3 = v^5 Chat(w) + u^6 Phat(w)
+            const f32x2 cq = fma2(fma2(fma2(w, k[5], k[4]), w, k[3]), w, k[2]);
+            const f32x2 pq = mul2(fma2(fma2(w, k[8], k[7]), w, k[6]), w);
             sc = mul2(jm, fma2(u6, pq, mul2(v5, cq)));
         } else {
-            // Plummer softening: g at the unsoftened R times 1/(r^2+eps^2)^(3/2)
-            const f32x2 c = fma2(fma2(fma2(R, k[2], k[3]), R, k[4]), R, k[5]);
-            const f32x2 p = fma2(fma2(R, k[6], k[7]), R, k[8]);
+            // Plummer softening: g at the unsoftened R = 2 xi times 1/(xi^2+eps^2)^(3/2)
+            const f32x2 x = mul2(r2, w);
+            const f32x2 c = fma2(fma2(fma2(x, k[2], k[3]), x, k[4]), x, k[5]);
+            const f32x2 p = fma2(fma2(x, k[6], k[7]), x, k[8]);
             const f32x2 g = fma2(u6, p, mul2(v5, c));
             const f32x2 rs = rsqrt2(fma2(k[1], eps2, r2));
             sc = mul2(mul2(jm, g), mul2(mul2(rs, rs), rs));
@@ -239,22 +238,23 @@ __device__ __forceinline__ void interact(const float4 j, const float (&xi)[I], c
     for (int s = 0; s < I; s++) {
         const float dx = j.x - xi[s], dy = j.y - yi[s], dz = j.z - zi[s];
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        // the same form as the packed loop; r^2 = 0 is selected out
+        const float w = rsqrtf(r2);
+        const float v = fma_sat(r2, -w, 1.0f), u = fma_sat(v, 2.0f, -1.0f);
+        const float v2 = v * v, u2 = u * u;
+        const float v5 = v2 * v2 * v, u6 = u2 * u2 * u2;
         float sc;
         if (!SOFT) {
-            // g(R)/R^3 in the form of the packed loop
-            const float rinv = rsqrtf(r2);
-            const float R = r2 * rinv;
-            const float v = fma_sat(R, -0.5f, 1.0f), u = add_sat(1.0f, -R);
-            const float v2 = v * v, u2 = u * u;
-            const float cq = fmaf(fmaf(fmaf(rinv, kC0, kC1), rinv, kC2), rinv, kC3);
-            const float pq = fmaf(fmaf(rinv, kP0, kP1), rinv, kP2) * rinv;
-            const float F = fmaf(u2 * u2 * u2, pq, (v2 * v2 * v) * cq);
-            sc = (r2 > 0.0f) ? j.w * F : 0.0f;
+            const float cq = fmaf(fmaf(fmaf(w, kA3, kA2), w, kA1), w, kA0);
+            const float pq = fmaf(fmaf(w, kB3, kB2), w, kB1) * w;
+            sc = (r2 > 0.0f) ? j.w * fmaf(u6, pq, v5 * cq) : 0.0f;
         } else {
-            // Plummer softening: 1/(r^2+eps^2)^(3/2), g at the unsoftened R
+            // Plummer softening: 1/(xi^2+eps^2)^(3/2), g at the unsoftened R = 2 xi
+            const float x = r2 * w;
+            const float c = fmaf(fmaf(fmaf(x, kA0, kA1), x, kA2), x, kA3);
+            const float p = fmaf(fmaf(x, kB1, kB2), x, kB3);
             const float rs = rsqrtf(r2 + eps2);
-            const float g = g_p3m(r2 * rsqrtf(r2));
-            sc = (r2 > 0.0f) ? (j.w * g) * (rs * rs * rs) : 0.0f;
+            sc = (r2 > 0.0f) ? (j.w * fmaf(u6, p, v5 * c)) * (rs * rs * rs) : 0.0f;
         }
         ax[s] = fmaf(sc, dx, ax[s]);
         ay[s] = fmaf(sc, dy, ay[s]);
@@ -445,7 +445,7 @@ __device__ __forceinline__ void issue_chunk(const float4 *src, uint32_t ce, uint
 // second-order terms to the accelerations the monopole passes stored.
 template <int I, bool SOFT, bool QUAD>
 __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uint32_t done, int S,
-                                        unsigned long long lo, uint32_t len, WarpPipe &wp, float inv_eta2, float eps2,
+                                        unsigned long long lo, uint32_t len, WarpPipe &wp, float scale, float eps2,
                                         int lane)
 {
     const unsigned FULL = 0xffffffffu;
@@ -459,9 +459,10 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
         const uint32_t idx = gr.begin + done + (uint32_t)(s * li + slot);
         float4 v = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f);
         if (idx < gend) v = a.irel[idx];
-        xi[s] = v.x;
-        yi[s] = v.y;
-        zi[s] = v.z;
+        // the second-order terms work in eta = r_cut/2 units (exact rescaling)
+        xi[s] = QUAD ? 2.0f * v.x : v.x;
+        yi[s] = QUAD ? 2.0f * v.y : v.y;
+        zi[s] = QUAD ? 2.0f * v.z : v.z;
         ax[s] = ay[s] = az[s] = 0.f;
     }
     constexpr bool kPacked = !QUAD && (I % 2) == 0;
@@ -548,13 +549,13 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
             if (idx < gend) {
                 const size_t p = (size_t)a.perm[idx] * 3;
                 if (QUAD) {
-                    acc[p] += ax[s] * inv_eta2;
-                    acc[p + 1] += ay[s] * inv_eta2;
-                    acc[p + 2] += az[s] * inv_eta2;
+                    acc[p] += ax[s] * scale;
+                    acc[p + 1] += ay[s] * scale;
+                    acc[p + 2] += az[s] * scale;
                 } else {
-                    acc[p] = ax[s] * inv_eta2;
-                    acc[p + 1] = ay[s] * inv_eta2;
-                    acc[p + 2] = az[s] * inv_eta2;
+                    acc[p] = ax[s] * scale;
+                    acc[p + 1] = ay[s] * scale;
+                    acc[p + 2] = az[s] * scale;
                 }
             }
         }
@@ -595,7 +596,8 @@ __global__ void __launch_bounds__(GREEM_FORCE_THREADS, GREEM_FORCE_MINB) k_force
         const uint32_t g = a.order ? a.order[gi] : (uint32_t)gi;
         const Group gr = a.groups[g];
         const BoxPar &bp = a.bps[gr.box];
-        const float inv_eta2 = bp.inv_eta2, eps2 = bp.eps2;
+        // r_cut-unit accelerations (eta-unit ones in the second-order passes) -> physical
+        const float scale = QUAD ? 4.0f * bp.inv_rc2 : bp.inv_rc2, eps2 = bp.eps2;
         const unsigned long long lo = QUAD ? 3ull * a.qoff[g] : a.loff[g];
         const uint32_t len = QUAD ? a.qcnt[g] : a.llen[g];
         if (QUAD && len == 0) continue;
@@ -606,29 +608,29 @@ __global__ void __launch_bounds__(GREEM_FORCE_THREADS, GREEM_FORCE_MINB) k_force
             int S, I;
             if (QUAD) {
                 choose_layout_quad(gr.count - done, S, I);
-                if (I == 1) ok = group_pass<1, SOFT, true>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane);
-                else if (I == 2) ok = group_pass<2, SOFT, true>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane);
-                else ok = group_pass<4, SOFT, true>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane);
+                if (I == 1) ok = group_pass<1, SOFT, true>(a, gr, done, S, lo, len, wp, scale, eps2, lane);
+                else if (I == 2) ok = group_pass<2, SOFT, true>(a, gr, done, S, lo, len, wp, scale, eps2, lane);
+                else ok = group_pass<4, SOFT, true>(a, gr, done, S, lo, len, wp, scale, eps2, lane);
                 done += (uint32_t)(32 / S) * (uint32_t)I;
                 continue;
             }
             choose_layout(gr.count - done, S, I);
             switch (I) {
-            case 1: ok = group_pass<1, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
-            case 2: ok = group_pass<2, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
-            case 3: ok = group_pass<3, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
-            case 4: ok = group_pass<4, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 1: ok = group_pass<1, SOFT, false>(a, gr, done, S, lo, len, wp, scale, eps2, lane); break;
+            case 2: ok = group_pass<2, SOFT, false>(a, gr, done, S, lo, len, wp, scale, eps2, lane); break;
+            case 3: ok = group_pass<3, SOFT, false>(a, gr, done, S, lo, len, wp, scale, eps2, lane); break;
+            case 4: ok = group_pass<4, SOFT, false>(a, gr, done, S, lo, len, wp, scale, eps2, lane); break;
 #if GREEM_FORCE_IMAX >= 5
-            case 5: ok = group_pass<5, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 5: ok = group_pass<5, SOFT, false>(a, gr, done, S, lo, len, wp, scale, eps2, lane); break;
 #endif
 #if GREEM_FORCE_IMAX >= 6
-            case 6: ok = group_pass<6, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 6: ok = group_pass<6, SOFT, false>(a, gr, done, S, lo, len, wp, scale, eps2, lane); break;
 #endif
 #if GREEM_FORCE_IMAX >= 7
-            case 7: ok = group_pass<7, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 7: ok = group_pass<7, SOFT, false>(a, gr, done, S, lo, len, wp, scale, eps2, lane); break;
 #endif
 #if GREEM_FORCE_IMAX >= 8
-            case 8: ok = group_pass<8, SOFT, false>(a, gr, done, S, lo, len, wp, inv_eta2, eps2, lane); break;
+            case 8: ok = group_pass<8, SOFT, false>(a, gr, done, S, lo, len, wp, scale, eps2, lane); break;
 #endif
             default: ok = false; break;  // not reachable: choose_layout never exceeds kImax
             }
@@ -646,7 +648,7 @@ __global__ void __launch_bounds__(GREEM_FORCE_THREADS, GREEM_FORCE_MINB) k_force
 
 // The accepted nodes of each group's list, compacted in list order into the group's
 // stretch [qoff[g], qoff[g] + qcnt[g]) of the quadrupole list (three float4 per entry:
-// the list entry, then the node's second moments).  One warp per group.  An overflow of
+// the list entry, then the node's second moments, both in eta units).  One warp per group.  An overflow of
 // qcap entries records the total needed and the call is retried with a larger list.
 __global__ void __launch_bounds__(256) k_qlist_fill(ForceArgs a, const float4 *__restrict__ quad, unsigned long long qcap)
 {
@@ -678,9 +680,11 @@ __global__ void __launch_bounds__(256) k_qlist_fill(ForceArgs a, const float4 *_
             if (node) {
                 const uint32_t n = (uint32_t)(ie & 0xffffffffull);
                 float4 *d = const_cast<float4 *>(a.qlist) + 3ull * (q0 + k + __popc(bal & lt));
-                d[0] = a.flist[lo + e];
-                d[1] = quad[2 * (size_t)n];
-                d[2] = quad[2 * (size_t)n + 1];
+                // r_cut units -> eta units (positions x2, second moments x4; exact)
+                const float4 f = a.flist[lo + e], q0 = quad[2 * (size_t)n], q1 = quad[2 * (size_t)n + 1];
+                d[0] = make_float4(2.0f * f.x, 2.0f * f.y, 2.0f * f.z, f.w);
+                d[1] = make_float4(4.0f * q0.x, 4.0f * q0.y, 4.0f * q0.z, 4.0f * q0.w);
+                d[2] = make_float4(4.0f * q1.x, 4.0f * q1.y, 4.0f * q1.z, 4.0f * q1.w);
             }
             k += __popc(bal);
         }
@@ -947,9 +951,9 @@ void launch_force_f64(const ForceArgs &a, cudaStream_t s, int nsm)
 
 // ------------------------------------------------------------------ pairwise experiment
 // Every pair k becomes a one-particle group with a one-entry list (padded to 8):
-// i and j are passed relative to x_g in eta units (FP64 subtract, one FP32 rounding).
+// i and j are passed relative to x_g in r_cut units (FP64 subtract, one FP32 rounding).
 __global__ void k_pair_setup(const double *__restrict__ xg, const double *__restrict__ xi,
-                             const double *__restrict__ xj, const float *__restrict__ mj, uint32_t np, double inv_eta,
+                             const double *__restrict__ xj, const float *__restrict__ mj, uint32_t np, double inv_rc,
                              Group *groups, float4 *irel, float4 *flist, unsigned long long *loff, uint32_t *llen,
                              uint32_t *lraw, uint32_t *perm, uint32_t *n_groups)
 {
@@ -966,8 +970,8 @@ __global__ void k_pair_setup(const double *__restrict__ xg, const double *__rest
     groups[k] = g;
     float r[3], q[3];
     for (int c = 0; c < 3; c++) {
-        r[c] = (float)__dmul_rn(__dsub_rn(xi[3 * (size_t)k + c], xg[3 * (size_t)k + c]), inv_eta);
-        q[c] = (float)__dmul_rn(__dsub_rn(xj[3 * (size_t)k + c], xg[3 * (size_t)k + c]), inv_eta);
+        r[c] = (float)__dmul_rn(__dsub_rn(xi[3 * (size_t)k + c], xg[3 * (size_t)k + c]), inv_rc);
+        q[c] = (float)__dmul_rn(__dsub_rn(xj[3 * (size_t)k + c], xg[3 * (size_t)k + c]), inv_rc);
     }
     irel[k] = make_float4(r[0], r[1], r[2], 0.f);
     flist[8 * (size_t)k] = make_float4(q[0], q[1], q[2], mj[k]);
@@ -979,10 +983,10 @@ __global__ void k_pair_setup(const double *__restrict__ xg, const double *__rest
 }
 
 void launch_pair_setup(const double *xg, const double *xi, const double *xj, const float *mj, uint32_t np,
-                       double inv_eta, Group *groups, float4 *irel, float4 *flist, unsigned long long *loff,
+                       double inv_rc, Group *groups, float4 *irel, float4 *flist, unsigned long long *loff,
                        uint32_t *llen, uint32_t *lraw, uint32_t *perm, uint32_t *n_groups, cudaStream_t s)
 {
-    k_pair_setup<<<(np + 255) / 256, 256, 0, s>>>(xg, xi, xj, mj, np, inv_eta, groups, irel, flist, loff, llen, lraw,
+    k_pair_setup<<<(np + 255) / 256, 256, 0, s>>>(xg, xi, xj, mj, np, inv_rc, groups, irel, flist, loff, llen, lraw,
                                                    perm, n_groups);
     g_launches++;
 }

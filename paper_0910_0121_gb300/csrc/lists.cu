@@ -20,8 +20,8 @@
 // so the lists are exact and bit-identical to a sequential FP64 walk.
 //
 // Entries are written as float4 (x, y, z, m) relative to the group's cell centre in
-// eta units (Sec. 3.1.1: positions passed relative to the group centre): the cell
-// offset (an exact integer in u, wrapped to the nearest image) times u/eta, plus the
+// r_cut units (Sec. 3.1.1: positions passed relative to the group centre): the cell
+// offset (an exact integer in u, wrapped to the nearest image) times u/r_cut, plus the
 // particle's FP32 offset from its own leaf centre (or the node's COM offset from its
 // cell centre).  The group's own particles get the same float4 in irel[], so a
 // particle and its own list entry are bit-identical and the self pair has r = 0.

@@ -43,10 +43,10 @@ constexpr size_t kScratchBytes = align256(kOffPerm + sizeof(uint32_t) * kNoAlloc
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Writes the one box of constants the force kernel reads (no host staging buffer).
-__global__ void k_noalloc_box(BoxPar *bp, float inv_eta2, float eps2)
+__global__ void k_noalloc_box(BoxPar *bp, float inv_rc2, float eps2)
 {
     BoxPar b = {};
-    b.inv_eta2 = inv_eta2;
+    b.inv_rc2 = inv_rc2;
     b.eps2 = eps2;
     *bp = b;
 }
@@ -93,11 +93,11 @@ extern "C" int greem_pair_force_f32_noalloc(const double *x_g, const double *x_i
     uint32_t *lraw = reinterpret_cast<uint32_t *>(base + kOffLraw);
     uint32_t *perm = reinterpret_cast<uint32_t *>(base + kOffPerm);
 
-    const double eta = 0.5 * r_cut, inv_eta = 1.0 / eta;
+    const double inv_rc = 1.0 / r_cut;
     // the status word (flags and work-queue counters) must start at zero on every call
     cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
-    k_noalloc_box<<<1, 1, 0, s>>>(bp, (float)(inv_eta * inv_eta), (float)((eps / eta) * (eps / eta)));
-    launch_pair_setup(x_g, x_i, x_j, m_j, (uint32_t)npairs, inv_eta, groups, irel, flist, loff, llen, lraw, perm, ng,
+    k_noalloc_box<<<1, 1, 0, s>>>(bp, (float)(inv_rc * inv_rc), (float)((eps / r_cut) * (eps / r_cut)));
+    launch_pair_setup(x_g, x_i, x_j, m_j, (uint32_t)npairs, inv_rc, groups, irel, flist, loff, llen, lraw, perm, ng,
                       s);
     ForceArgs fa = {};
     fa.groups = groups;

@@ -356,10 +356,10 @@ void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_ca
     }
 }
 
-// Second moments about the COM (the second-order terms of Sec. 4.1), FP32 in eta^2 units,
+// Second moments about the COM (the second-order terms of Sec. 4.1), FP32 in r_cut^2 units,
 // as two float4 per node: (xx, yy, zz, xy), (xz, yz, (xx+yy+zz)/2, 0).  A leaf sums
 // m (p - c)(p - c)^T over its particles, p the particle's offset from the leaf's cell
-// centre and c the COM's (both already in eta units).  An internal node adds its
+// centre and c the COM's (both already in r_cut units).  An internal node adds its
 // children's moments moved to its own COM (parallel axes): Q_c + M_c d_c d_c^T, d_c =
 // child COM - node COM, from the exact cell-centre difference and the COM offsets.
 __device__ __forceinline__ void quad_store(float4 *__restrict__ quad, uint32_t n, const float q[6])
@@ -447,7 +447,7 @@ void launch_quadrupoles(const Node *nodes, const uint32_t *n_nodes, uint32_t nod
     }
 }
 
-// Each particle's offset from the centre of its leaf cell (level K_i) in eta units: the
+// Each particle's offset from the centre of its leaf cell (level K_i) in r_cut units: the
 // FP64 subtraction is done once per particle, then rounded to FP32 for the list builder.
 // The general-L form is a real call so that it is not predicated into the integer form's
 // lanes (FP64 instructions are slow on this GPU).
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256) k_leaf_offsets(const uint64_t *__restrict
                               __ll2float_rn(fixed52(zs[i], e) - ((long long)cz << 30)) * s, ms[i]);
         return;
     }
-    poff[i] = leaf_offset_fp64(xs[i], ys[i], zs[i], ms[i], cx, cy, cz, bp.u, bp.inv_eta);
+    poff[i] = leaf_offset_fp64(xs[i], ys[i], zs[i], ms[i], cx, cy, cz, bp.u, bp.inv_rc);
 }
 
 void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
@@ -507,7 +507,7 @@ static __device__ __noinline__ float4 node_offset_fp64(double cx, double cy, dou
 }
 
 // COM = S/M (the cell centre for a massless node), and the COM's offset from the node's
-// cell centre in eta units for the list builder.
+// cell centre in r_cut units for the list builder.
 __global__ void __launch_bounds__(256) k_node_finish(const Node *__restrict__ nodes,
                                                      const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
                                                      const Dbl4 *__restrict__ raw,
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(256) k_node_finish(const Node *__restrict__ no
                                   __ll2float_rn(fixed52(cz, e) - ((long long)(2u * nd.iz + h) << sh)) * s, (float)r.w);
         } else {
             noff[n] = node_offset_fp64(cx, cy, cz, (float)r.w, 2u * nd.ix + h, 2u * nd.iy + h, 2u * nd.iz + h, bp.u,
-                                       bp.inv_eta);
+                                       bp.inv_rc);
         }
     }
 }
