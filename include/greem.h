@@ -16,9 +16,10 @@
  *
  * Conventions for every call:
  *  - pos is [N,3] float64 row-major, mass is [N] float32, acc is [N,3] (float32, or
- *    float64 for GREEM_F64), all CONTIGUOUS DEVICE pointers owned by the caller.  The
- *    library never frees them and does not keep them after the call returns, except
- *    the pointers captured by greem_graph_capture (see there).
+ *    float64 for GREEM_F64), all CONTIGUOUS DEVICE pointers owned by the caller (HOST
+ *    pointers in greem_short_force_host only).  The library never frees them and does
+ *    not keep them after the call returns, except the pointers captured by
+ *    greem_graph_capture (see there).
  *  - acc is written in INPUT order.  Positions outside [0, L) are wrapped (periodic);
  *    they are not errors.
  *  - Work is enqueued on the context's stream.  Calls that return a status wait for
@@ -131,6 +132,23 @@ int greem_short_force(const double *pos, const float *mass, int64_t N, double L,
  * GREEM_F32_REL and float64 [N,3] for GREEM_F64.  Errors as greem_build_tree. */
 int greem_short_force_ex(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, const greem_params *p,
                          void *acc);
+
+/* nstep independent short-range force problems whose inputs and results live in HOST
+ * memory, each one greem_short_force_ex with the same p.  Problem k reads pos[k]
+ * (float64 [N[k],3]) and mass[k] (float32 [N[k]]) and writes acc[k] (float32 or
+ * float64 [N[k],3] by p->precision), all host pointers owned by the caller.  The copies
+ * overlap the computation: while problem k runs on the context's stream, the inputs of
+ * k+1 are copied in and the result of k-1 is copied out on two more streams, through
+ * two device staging slots that the context keeps (about 40 bytes per particle each,
+ * sized for the largest N seen).  The overlap needs page-locked host memory
+ * (cudaHostAlloc, cudaHostRegister, or torch pin_memory); pageable pointers work but
+ * their copies do not overlap.  Returns when every result is in host memory, or at the
+ * first failing problem: its code is returned, its acc and those of later problems are
+ * not written, and earlier ones are complete.  The statistics are those of the last
+ * problem run.  Errors as greem_short_force_ex, plus INVALID_ARG for nstep < 1 or a NULL
+ * array or pointer. */
+int greem_short_force_host(greem_ctx *ctx, int nstep, const double *const *pos, const float *const *mass,
+                           const int64_t *N, const greem_params *p, void *const *acc);
 
 /* nbox independent periodic boxes in one pass: box b holds particles
  * [offsets[b], offsets[b+1]) of pos/mass/acc and uses per_box[b] (every box may have

@@ -91,6 +91,14 @@ struct greem_ctx {
     int pm_tab_n = 0, pm_tab_scheme = -1;
     double pm_tab_L = 0, pm_tab_rc = 0;
 
+    // host-buffer calls: two device staging slots for inputs and results, and the copy
+    // streams that fill and drain them beside the computation
+    DBuf<double> hs_pos[2];
+    DBuf<float> hs_mass[2];
+    DBuf<unsigned char> hs_acc[2];
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+
     // graph
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -665,6 +673,23 @@ static RunCfg make_cfg(const greem_params &p, const double *pos, const float *ma
     return r;
 }
 
+// Device staging for the host-buffer calls: grown before any copy is in flight, and
+// never part of a captured graph.
+template <class T>
+static int ensure_staging(DBuf<T> &b, size_t n)
+{
+    if (b.n >= n && b.p) return GREEM_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    if (!cuda_ok(cudaMalloc((void **)&b.p, n * sizeof(T)))) {
+        b.p = nullptr;
+        return GREEM_ERR_OOM;
+    }
+    b.n = n;
+    return GREEM_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -719,6 +744,16 @@ void greem_destroy(greem_ctx *c)
     pm_plan_destroy(c->pm);
     release(c->pm_grid); release(c->pm_table); release(c->pm_spec); release(c->pm_tmp);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    for (cudaStream_t hs : {c->h2d, c->d2h})
+        if (hs) {
+            cudaStreamSynchronize(hs);
+            cudaStreamDestroy(hs);
+        }
+    for (int k = 0; k < 2; k++) {
+        if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+        if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
+        release(c->hs_pos[k]); release(c->hs_mass[k]); release(c->hs_acc[k]);
+    }
     if (c->aux) cudaStreamSynchronize(c->aux);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -755,6 +790,72 @@ int greem_short_force_ex(greem_ctx *c, const double *pos, const float *mass, int
     RunCfg r = make_cfg(*p, pos, mass, acc, (uint32_t)N, 1, true);
     r.soft = p->eps > 0;
     return run(c, r);
+}
+
+int greem_short_force_host(greem_ctx *c, int nstep, const double *const *pos, const float *const *mass,
+                           const int64_t *N, const greem_params *p, void *const *acc)
+{
+    if (!c || !p || nstep < 1 || !pos || !mass || !N || !acc || c->capturing) return GREEM_ERR_INVALID_ARG;
+    int64_t nmax = 0;
+    for (int k = 0; k < nstep; k++) {
+        if (!pos[k] || !mass[k] || !acc[k] || N[k] < 1 || N[k] >= (int64_t)0x7FFFFFF0) return GREEM_ERR_INVALID_ARG;
+        nmax = std::max(nmax, N[k]);
+    }
+    const size_t esz = p->precision == GREEM_F64 ? sizeof(double) : sizeof(float);
+    if (!c->h2d) {
+        if (!cuda_ok(cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking)) ||
+            !cuda_ok(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking)))
+            return GREEM_ERR_CUDA;
+        for (int k = 0; k < 2; k++)
+            if (!cuda_ok(cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming)) ||
+                !cuda_ok(cudaEventCreateWithFlags(&c->ev_out[k], cudaEventDisableTiming)))
+                return GREEM_ERR_CUDA;
+    }
+    // nothing may be in flight on the copy streams while the slots are resized
+    if (!cuda_ok(cudaStreamSynchronize(c->h2d)) || !cuda_ok(cudaStreamSynchronize(c->d2h))) return GREEM_ERR_CUDA;
+    int rc = GREEM_OK;
+    for (int k = 0; k < 2 && rc == GREEM_OK; k++)
+        (rc = ensure_staging(c->hs_pos[k], 3 * (size_t)nmax)) || (rc = ensure_staging(c->hs_mass[k], (size_t)nmax)) ||
+            (rc = ensure_staging(c->hs_acc[k], 3 * (size_t)nmax * esz));
+    if (rc) return rc;
+    // inputs of problem k into slot k & 1, on the copy-in stream
+    auto copy_in = [&](int k) {
+        const int s = k & 1;
+        const bool ok =
+            cuda_ok(cudaMemcpyAsync(c->hs_pos[s].p, pos[k], 3 * sizeof(double) * (size_t)N[k], cudaMemcpyHostToDevice,
+                                    c->h2d)) &&
+            cuda_ok(cudaMemcpyAsync(c->hs_mass[s].p, mass[k], sizeof(float) * (size_t)N[k], cudaMemcpyHostToDevice,
+                                    c->h2d)) &&
+            cuda_ok(cudaEventRecord(c->ev_in[s], c->h2d));
+        return ok;
+    };
+    if (!copy_in(0)) rc = GREEM_ERR_CUDA;
+    for (int k = 0; k < nstep && rc == GREEM_OK; k++) {
+        const int s = k & 1;
+        // the other slot's inputs were last read by problem k-1, which has finished
+        if (k + 1 < nstep && !copy_in(k + 1)) {
+            rc = GREEM_ERR_CUDA;
+            break;
+        }
+        // problem k starts when its inputs have landed and the result that last used this
+        // slot (problem k-2) has been copied out
+        if (!cuda_ok(cudaStreamWaitEvent(c->stream, c->ev_in[s], 0)) ||
+            (k >= 2 && !cuda_ok(cudaStreamWaitEvent(c->stream, c->ev_out[s], 0)))) {
+            rc = GREEM_ERR_CUDA;
+            break;
+        }
+        rc = greem_short_force_ex(c, c->hs_pos[s].p, c->hs_mass[s].p, N[k], p, c->hs_acc[s].p);
+        if (rc) break;
+        // the call waited for its stream: the result is complete; copy it out beside the
+        // next problem
+        if (!cuda_ok(cudaMemcpyAsync(acc[k], c->hs_acc[s].p, 3 * esz * (size_t)N[k], cudaMemcpyDeviceToHost, c->d2h)) ||
+            !cuda_ok(cudaEventRecord(c->ev_out[s], c->d2h)))
+            rc = GREEM_ERR_CUDA;
+    }
+    // the slots must be idle before the call returns, also after a failure
+    const bool idle = cuda_ok(cudaStreamSynchronize(c->h2d)) && cuda_ok(cudaStreamSynchronize(c->d2h));
+    if (rc == GREEM_OK && !idle) rc = GREEM_ERR_CUDA;
+    return rc;
 }
 
 static std::mutex g_def_mu;

@@ -86,6 +86,7 @@ def _lib():
             L.greem_short_force.argtypes = [vp, vp, i64, dbl, dbl, dbl, i32, vp]
             L.greem_short_force_ex.argtypes = [vp, vp, vp, i64, P, vp]
             L.greem_short_force_batched.argtypes = [vp, i32, vp, vp, vp, P, vp]
+            L.greem_short_force_host.argtypes = [vp, i32, vp, vp, vp, P, vp]
             L.greem_pm_force.argtypes = [vp, vp, vp, i64, dbl, i32, dbl, i32, vp]
             L.greem_graph_capture.argtypes = [vp, vp, vp, i64, P, vp]
             L.greem_graph_launch.argtypes = [vp]
@@ -104,7 +105,7 @@ def _lib():
             L.greem_strerror.argtypes = [i32]
             L.greem_strerror.restype = ctypes.c_char_p
             for f in ("greem_create", "greem_build_tree", "greem_short_force", "greem_short_force_ex",
-                      "greem_short_force_batched", "greem_pm_force", "greem_graph_capture", "greem_graph_launch",
+                      "greem_short_force_batched", "greem_short_force_host", "greem_pm_force", "greem_graph_capture", "greem_graph_launch",
                       "greem_get_stats", "greem_debug_dump", "greem_autotune", "greem_pair_force_f32",
                       "greem_peak_tflops", "greem_debug_dump_group_lists", "greem_kick", "greem_drift",
                       "greem_timestep", "greem_cosmo_factors"):
@@ -132,6 +133,19 @@ def _dev(t, dtype, shape=None, name="tensor"):
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a CPU torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
     return ctypes.c_void_p(t.data_ptr())
 
@@ -190,6 +204,34 @@ class Context:
                                            _dev(mass, torch.float32, (N,), "mass"), N, ctypes.byref(p),
                                            _dev(acc, dt, (N, 3), "acc")), "greem_short_force_ex")
         return acc
+
+    def short_force_host(self, pos, mass, p: Params, acc=None):
+        """greem_short_force_host: independent problems with inputs and results in HOST
+        memory (CPU torch tensors; pinned ones let the copies overlap the computation).
+        pos, mass: sequences of [N_k,3] float64 and [N_k] float32 tensors; acc: a sequence
+        of [N_k,3] tensors (float32, or float64 for F64 precision) or None to allocate
+        pinned ones.  Returns the list of acc tensors."""
+        import torch
+        n = len(pos)
+        if len(mass) != n or n < 1:
+            raise ValueError("pos and mass must be non-empty sequences of the same length")
+        dt = torch.float64 if p.precision == F64 else torch.float32
+        if acc is None:
+            acc = [torch.empty((x.shape[0], 3), dtype=dt).pin_memory() for x in pos]
+        if len(acc) != n:
+            raise ValueError("acc must have one tensor per problem")
+        vp = ctypes.c_void_p
+        ptr_pos, ptr_mass, ptr_acc = (vp * n)(), (vp * n)(), (vp * n)()
+        Ns = (ctypes.c_int64 * n)()
+        for k in range(n):
+            N = pos[k].shape[0]
+            ptr_pos[k] = _host(pos[k], torch.float64, (N, 3), "pos").value
+            ptr_mass[k] = _host(mass[k], torch.float32, (N,), "mass").value
+            ptr_acc[k] = _host(acc[k], dt, (N, 3), "acc").value
+            Ns[k] = N
+        _check(_lib().greem_short_force_host(self._h, n, ptr_pos, ptr_mass, Ns, ctypes.byref(p), ptr_acc),
+               "greem_short_force_host")
+        return list(acc)
 
     def short_force_batched(self, pos, mass, offsets, per_box, acc=None):
         import torch
