@@ -66,6 +66,7 @@ struct greem_ctx {
     DBuf<uint32_t> box_off, small;
     DBuf<DevStatus> st;
     DevStatus *st_host = nullptr;
+    DevStatus *st_host_dev = nullptr;  // the device's address of st_host (mapped), or null
     BoxPar *bps_host = nullptr;
     uint32_t *box_off_host = nullptr;
     int host_boxes_cap = 0;
@@ -415,6 +416,64 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
     return GREEM_OK;
 }
 
+// The per-call constants of up to kInlineBoxes boxes go to the device as a kernel
+// argument and the status word comes back through mapped host memory, so that a call
+// issues no copy of its own: a copy would queue on the copy engines behind the
+// multi-hundred-megabyte transfers that greem_short_force_host overlaps with the call.
+constexpr int kInlineBoxes = 4;
+static_assert(sizeof(DevStatus) % 4 == 0, "DevStatus is copied as 32-bit words");
+struct InlineBoxes {
+    BoxPar b[kInlineBoxes];
+    uint32_t off[kInlineBoxes + 1];
+    int nbox;
+};
+
+// Also clears the status word (a memset could sit on a copy engine too).
+__global__ void k_set_boxes(InlineBoxes ib, BoxPar *__restrict__ bps, uint32_t *__restrict__ box_off,
+                            DevStatus *__restrict__ st)
+{
+    const int t = threadIdx.x;
+    if (t < ib.nbox) bps[t] = ib.b[t];
+    if (t <= ib.nbox) box_off[t] = ib.off[t];
+    uint32_t *w = reinterpret_cast<uint32_t *>(st);
+    for (int i = t; i < (int)(sizeof(DevStatus) / 4); i += blockDim.x) w[i] = 0u;
+}
+
+__global__ void k_status_out(const DevStatus *__restrict__ src, DevStatus *dst)
+{
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    volatile uint32_t *d = reinterpret_cast<volatile uint32_t *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevStatus) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+// Clears the status word and uploads the per-box constants.
+static void upload_boxes(greem_ctx *c, int nbox, cudaStream_t s)
+{
+    if (nbox <= kInlineBoxes) {
+        InlineBoxes ib;
+        memset(&ib, 0, sizeof(ib));
+        ib.nbox = nbox;
+        for (int b = 0; b < nbox; b++) ib.b[b] = c->bps_host[b];
+        for (int b = 0; b <= nbox; b++) ib.off[b] = c->box_off_host[b];
+        k_set_boxes<<<1, 32, 0, s>>>(ib, c->bps.p, c->box_off.p, c->st.p);
+        greem::g_launches++;
+    } else {
+        cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s);
+        cudaMemcpyAsync(c->bps.p, c->bps_host, sizeof(BoxPar) * nbox, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(c->box_off.p, c->box_off_host, sizeof(uint32_t) * (nbox + 1), cudaMemcpyHostToDevice, s);
+    }
+}
+
+static void download_status(greem_ctx *c, cudaStream_t s)
+{
+    if (c->st_host_dev) {
+        k_status_out<<<1, 32, 0, s>>>(c->st.p, c->st_host_dev);
+        greem::g_launches++;
+    } else {
+        cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+    }
+}
+
 static void ev_record(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev, int i)
 {
     if (r.timing && !c->capturing) cudaEventRecord(ev[i], c->stream);
@@ -429,9 +488,7 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     const int nbox = r.nbox;
     const int nsm = c->nsm;
     const uint32_t ncap = (uint32_t)std::min<size_t>(c->node_cap, 0xFFFFFFF0u);
-    cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s);
-    cudaMemcpyAsync(c->bps.p, c->bps_host, sizeof(BoxPar) * nbox, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c->box_off.p, c->box_off_host, sizeof(uint32_t) * (nbox + 1), cudaMemcpyHostToDevice, s);
+    upload_boxes(c, nbox, s);
     ev_record(c, r, ev, 0);
     launch_keys(r.pos, N, c->box_off.p, nbox, c->bps.p, c->k0.p, c->st.p, s);
     ev_record(c, r, ev, 1);
@@ -543,7 +600,7 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
         }
         ev_record(c, r, ev, 6);
     }
-    cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+    download_status(c, s);
     c->ks = ks;
     c->perm = perm;
     if (!cuda_ok(cudaGetLastError())) return GREEM_ERR_CUDA;
@@ -726,6 +783,11 @@ int greem_create(greem_ctx **out, void *cuda_stream)
         return GREEM_ERR_OOM;
     }
     memset(c->st_host, 0, sizeof(DevStatus));
+    {
+        void *dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, c->st_host, 0) == cudaSuccess) c->st_host_dev = static_cast<DevStatus *>(dp);
+        else cudaGetLastError();  // not mapped: the status comes back by a copy
+    }
     if (!cuda_ok(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) ||
         !cuda_ok(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) ||
         !cuda_ok(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming))) {
