@@ -6,6 +6,10 @@ resident in HBM.  Workload: 256^3 particles (Zel'dovich P(k) ~ k^-2 grid, rms 0.
 spacing, plus 5000 NFW halos), L = 1, r_cut = 3/256, theta = 0.5, n_leaf = 10, n_crit
 autotuned (untimed, before the warm-up).  Inputs (470 MB) are larger than the 129 MB L2.
 
+The e2e figure runs the same steps through greem_short_force_host: each step copies its
+inputs in from pinned host memory and its result out, the copies overlapping the
+neighbouring steps' computation.
+
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (on the host
 cores, on a bounded sample of the same workload).
 """
