@@ -176,7 +176,9 @@ def reference_arm(args, rank, world):
     from paper_0910_0121_gb300 import synth
     pos, mass, prm = synth.config_zel256()
     N = len(pos)
-    T, t_tree = oracle_tree(pos, mass, prm, 128)
+    # the n_crit the GPU arm's autotuner settles on for this workload (its config line)
+    n_crit = args.n_crit or 192
+    T, t_tree = oracle_tree(pos, mass, prm, n_crit)
     times = []
     nth, ns = 1, 0
     for k in range(args.warmup + args.steps):
@@ -191,7 +193,7 @@ def reference_arm(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "N": N, "theta": prm["theta"], "r_cut": prm["r_cut"], "n_crit": 128,
+            "config": {"workload": WORKLOAD, "N": N, "theta": prm["theta"], "r_cut": prm["r_cut"], "n_crit": n_crit,
                        "n_leaf": 10},
             "cpu_baseline": {"value": v, "unit": "particles/s", "cores": nth, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -54,6 +54,15 @@ __device__ __forceinline__ uint32_t cell21_pow2(double r, int e)
     return (uint32_t)i;
 }
 
+// The general-L cell indices as a real call: inlined, the compiler may predicate its
+// FP64 work into the lanes of the power-of-two path, where it still occupies the FP64
+// pipe.
+static __device__ __noinline__ uint3 cells_general(double x, double y, double z, double L, double invL)
+{
+    return make_uint3(cell21(wrap_pos_fast(x, L), L, invL), cell21(wrap_pos_fast(y, L), L, invL),
+                      cell21(wrap_pos_fast(z, L), L, invL));
+}
+
 __global__ void __launch_bounds__(256) k_keys(const double *__restrict__ pos, uint32_t N,
                                               const uint32_t *__restrict__ box_off, int nbox,
                                               const BoxPar *__restrict__ bps, uint64_t *__restrict__ keys,
@@ -79,9 +88,10 @@ __global__ void __launch_bounds__(256) k_keys(const double *__restrict__ pos, ui
         cy = cell21_pow2(wrap_pos_fast(y, L), bp.pow2_e);
         cz = cell21_pow2(wrap_pos_fast(z, L), bp.pow2_e);
     } else {
-        cx = cell21(wrap_pos_fast(x, L), L, invL);
-        cy = cell21(wrap_pos_fast(y, L), L, invL);
-        cz = cell21(wrap_pos_fast(z, L), L, invL);
+        const uint3 c = cells_general(x, y, z, L, invL);
+        cx = c.x;
+        cy = c.y;
+        cz = c.z;
     }
     keys[i] = (spread3(cx) << 2) | (spread3(cy) << 1) | spread3(cz);
 }
