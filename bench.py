@@ -404,7 +404,7 @@ def gpu_arm(args, rank, world, local):
     ctx.short_force_host([hpos, hpos], [hmass, hmass], p, hacc)   # sizes the staging slots
     torch.cuda.synchronize()
     barrier()
-    e2 = max(3, args.steps // 2)
+    e2 = max(3, args.steps)
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     ctx.short_force_host([hpos] * e2, [hmass] * e2, p, [hacc[k & 1] for k in range(e2)])
