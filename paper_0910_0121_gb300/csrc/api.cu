@@ -55,7 +55,7 @@ struct greem_ctx {
     DBuf<float4> quad, qlist;
     DBuf<uint32_t> qcnt, qoff;
     size_t qcap = 0;  // quadrupole-list entries
-    DBuf<unsigned long long> pcell;
+    DBuf<unsigned long long> pcell, lbox;
     DBuf<int4> gbox;
     // S5-S6
     DBuf<float4> flist;
@@ -386,6 +386,7 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
     ENS(raw, nc);
     ENS(mom64, nc);
     ENS(noff, nc);
+    ENS(lbox, nc);
     ENS(gflag, nc);
     ENS(gidx, nc + 1);
     ENS(groups, nc);
@@ -517,6 +518,7 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     const uint32_t *n_groups = c->gidx.p + ncap;
     launch_group_fill(c->nodes.p, n_nodes, ncap, c->gflag.p, c->gidx.p, c->box_off.p, nbox, c->groups.p, s2, nsm);
     launch_group_box(c->groups.p, n_groups, c->pcell.p, c->gbox.p, s2, nsm);
+    launch_leaf_boxes(c->nodes.p, n_nodes, ncap, c->pcell.p, c->lbox.p, s2, nsm);
     launch_record_counts(n_nodes, n_groups, c->st.p, ncap, s2);
     cudaEventRecord(c->ev_join, s2);
     launch_moments(c->nodes.p, n_nodes, ncap, c->kids.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p, c->lvl.p,
@@ -543,6 +545,7 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
         la.poff = c->poff.p;
         la.noff = c->noff.p;
         la.pcell = c->pcell.p;
+        la.lbox = c->lbox.p;
         la.gbox = c->gbox.p;
         la.flist = c->flist.p;
         la.ilist = r.index_lists ? c->ilist.p : nullptr;
@@ -825,7 +828,7 @@ void greem_destroy(greem_ctx *c)
     release(c->xs); release(c->ys); release(c->zs); release(c->ms);
     release(c->d8); release(c->K8); release(c->nchild); release(c->own); release(c->base); release(c->ctr);
     release(c->gflag); release(c->gidx); release(c->nodes); release(c->raw); release(c->mom64); release(c->noff);
-    release(c->poff); release(c->pcell); release(c->irel); release(c->groups); release(c->gbox); release(c->quad);
+    release(c->poff); release(c->pcell); release(c->lbox); release(c->irel); release(c->groups); release(c->gbox); release(c->quad);
     release(c->flist); release(c->ilist); release(c->loff);
     release(c->llen); release(c->lraw); release(c->kids); release(c->stack); release(c->order); release(c->bins);
     release(c->lvl); release(c->bps); release(c->box_off); release(c->small); release(c->st);

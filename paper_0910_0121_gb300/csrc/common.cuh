@@ -182,6 +182,8 @@ void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_ca
 void launch_quadrupoles(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
                         const float4 *poff, const float4 *noff, const uint32_t *lvl, const uint32_t *inodes,
                         const uint32_t *box_off, int nbox, const BoxPar *bps, float4 *quad, cudaStream_t s, int nsm);
+void launch_leaf_boxes(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap,
+                       const unsigned long long *pcell, unsigned long long *lbox, cudaStream_t s, int nsm);
 void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, const uint32_t *box_off, int nbox,
                          const BoxPar *bps, const double *xs, const double *ys, const double *zs, const float *ms,
                          float4 *poff, unsigned long long *pcell, cudaStream_t s);
@@ -211,6 +213,7 @@ struct ListArgs {
     const float4 *poff;        // per sorted particle: offset from its leaf centre (r_cut units), mass
     const float4 *noff;        // per node: COM offset from its cell centre (r_cut units), mass
     const unsigned long long *pcell;  // per sorted particle: finest cell, x | y << 21 | z << 42
+    const unsigned long long *lbox;   // per leaf: its particles' box of finest cells (k_leaf_boxes)
     const int4 *gbox;          // per group: particle box centre minus cell centre, then half sides (u)
     float4 *flist;             // list pool, FP32 relative entries
     unsigned long long *ilist; // list pool, index entries (may be null)

@@ -232,12 +232,24 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
         if (leaf) {
             const int h = hn;
             const CellTest lc = cell_gap<INDEX>(ncx, ncy, ncz, h, gr, tb, th);
-            // a leaf whose whole cell lies within r_cut of the particle box keeps every
-            // particle (each particle's finest cell is inside the leaf's cell)
-            const int fx = max(0, abs(lc.dx - tb.x) + h - th.x), fy = max(0, abs(lc.dy - tb.y) + h - th.y),
-                      fz = max(0, abs(lc.dz - tb.z) + h - th.z);
+            // the box of the leaf's particles (finest cells, in slots of q; k_leaf_boxes),
+            // its centre relative to the group's cell centre in the leaf's image and its
+            // half sides (u): beyond r_cut of the group's particle box, no particle is
+            // kept; within it, every particle is (each particle's finest cell is inside)
+            const unsigned long long lb = __ldg(a.lbox + m);
+            const int q = h > 256 ? (h >> 8) : 1;
+            const int lx = (int)(lb & 255u), ly = (int)((lb >> 16) & 255u), lz = (int)((lb >> 32) & 255u);
+            const int ux = (int)((lb >> 8) & 255u), uy = (int)((lb >> 24) & 255u), uz = (int)((lb >> 40) & 255u);
+            const int bcx = lc.dx - h + (lx + ux + 1) * q - tb.x, bcy = lc.dy - h + (ly + uy + 1) * q - tb.y,
+                      bcz = lc.dz - h + (lz + uz + 1) * q - tb.z;
+            const int bhx = (ux + 1 - lx) * q, bhy = (uy + 1 - ly) * q, bhz = (uz + 1 - lz) * q;
+            const int gx = max(0, abs(bcx) - bhx - th.x), gy = max(0, abs(bcy) - bhy - th.y),
+                      gz = max(0, abs(bcz) - bhz - th.z);
+            const bool none = (long long)gx * gx + (long long)gy * gy + (long long)gz * gz > Tp;
+            const int fx = max(0, abs(bcx) + bhx - th.x), fy = max(0, abs(bcy) + bhy - th.y),
+                      fz = max(0, abs(bcz) + bhz - th.z);
             const bool test_each = (long long)fx * fx + (long long)fy * fy + (long long)fz * fz > Tp;
-            ne = nd.end - nd.begin;
+            ne = none ? 0u : nd.end - nd.begin;
             bx = __fmul_rn((float)lc.dx, kf);
             by = __fmul_rn((float)lc.dy, kf);
             bz = __fmul_rn((float)lc.dz, kf);

@@ -496,6 +496,48 @@ void launch_leaf_offsets(const uint64_t *keys, const uint8_t *K8, uint32_t N, co
     g_launches++;
 }
 
+// Per leaf, the box of its particles' finest cells, rounded outward to 1/256 of the leaf
+// cell's side: per axis the first and last occupied slot, slots of q = max(1, s/256)
+// finest cells (s = the cell side in finest cells), 8 bits each, packed as
+// x_lo | x_hi << 8 | y_lo << 16 | y_hi << 24 | z_lo << 32 | z_hi << 40.  The list builder
+// drops an opened leaf whose box lies beyond r_cut of the group and skips the
+// per-particle test of one whose box lies within it: both decisions are those of every
+// particle's own test, so the lists are unchanged.
+__global__ void __launch_bounds__(256) k_leaf_boxes(const Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
+                                                    uint32_t node_cap, const unsigned long long *__restrict__ pcell,
+                                                    unsigned long long *__restrict__ lbox)
+{
+    const uint32_t nn = node_count(n_nodes, node_cap);
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
+        const Node nd = nodes[n];
+        if (!(nd.lvl & 256u)) continue;
+        const int k = (int)(nd.lvl & 255u);
+        const uint32_t sh = (kMaxLevel - k) > 8 ? (uint32_t)(kMaxLevel - k - 8) : 0u;  // q = 2^sh
+        uint32_t lo[3] = {255u, 255u, 255u}, hi[3] = {0u, 0u, 0u};
+        const uint32_t org[3] = {nd.ix, nd.iy, nd.iz};
+        for (uint32_t j = nd.begin; j < nd.end; j++) {
+            const unsigned long long c = pcell[j];
+            const uint32_t f[3] = {(uint32_t)c & 0x1fffffu, (uint32_t)(c >> 21) & 0x1fffffu, (uint32_t)(c >> 42)};
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const uint32_t slot = (f[a] - org[a]) >> sh;
+                lo[a] = min(lo[a], slot);
+                hi[a] = max(hi[a], slot);
+            }
+        }
+        lbox[n] = (unsigned long long)lo[0] | ((unsigned long long)hi[0] << 8) | ((unsigned long long)lo[1] << 16) |
+                  ((unsigned long long)hi[1] << 24) | ((unsigned long long)lo[2] << 32) |
+                  ((unsigned long long)hi[2] << 40);
+    }
+}
+
+void launch_leaf_boxes(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap,
+                       const unsigned long long *pcell, unsigned long long *lbox, cudaStream_t s, int nsm)
+{
+    k_leaf_boxes<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, pcell, lbox);
+    g_launches++;
+}
+
 // COM offset from the cell centre for a general L (FP64), as a real call (see
 // leaf_offset_fp64).
 static __device__ __noinline__ float4 node_offset_fp64(double cx, double cy, double cz, float m, uint32_t ux,
