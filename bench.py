@@ -30,7 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("short-range tree force particles/s & interactions/s at θ=0.5, % FP32 peak, FP32 vs FP64")
 WORKLOAD = "zeldovich256+5000nfw_theta0.5"
-FLOPS_PER_INTERACTION = 42          # S6 formulation count (FMA = 2), see the design notes
+# FP32 flops credited per interaction (FMA = 2): 3 subtractions, 5 for r^2, 1 for r, 1 for R,
+# 12 for the inner polynomial of Eq. 2, 10 for its (R-1)^6 correction, 4 for m g / r^3, 6 to accumulate
+FLOPS_PER_INTERACTION = 42
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
