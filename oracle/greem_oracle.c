@@ -23,34 +23,35 @@
  *   list force with g_P3M                [Eq. 1 and Eq. 2]
  *   brute-force minimum-image sum        [Eq. 1, Eq. 2; Sec. 1: image particles]
  *
- * Readings of points the paper leaves open (each also listed in the design notes):
- *   - wrap: r = x - L*floor(x/L); r<0 -> r+L; r>=L -> r-L; anything outside [0,L) -> 0.
- *   - key: ix = min(floor((r/L)*2^21), 2^21-1) per axis, 21 bits per axis, the x bit
+ * Readings of points the paper leaves open; the tag in brackets is the reading's
+ * number (C1-C19, R1-R4), the same on the CUDA side:
+ *   - [C9, R2] wrap: r = x - L*floor(x/L); r<0 -> r+L; r>=L -> r-L; anything outside [0,L) -> 0.
+ *   - [C9] key: ix = min(floor((r/L)*2^21), 2^21-1) per axis, 21 bits per axis, the x bit
  *     is the most significant bit of each 3-bit digit.
- *   - l_min = smallest level k with L*2^-k < L/2 - r_cut; nodes above l_min are always
+ *   - [C4] l_min = smallest level k with L*2^-k < L/2 - r_cut; nodes above l_min are always
  *     split and never accepted, groups live at level >= l_min.  This keeps every
  *     per-node image shift equal to the per-pair minimum image for pairs within r_cut.
- *   - leaf iff count < n_leaf or level 21 (levels < l_min always split).
- *   - group = first node in preorder with level >= l_min and (count <= n_crit or leaf).
- *   - integer geometry in units u = L/2^22: a level-k cell with index i has centre
+ *   - [C5] leaf iff count < n_leaf or level 21 (levels < l_min always split).
+ *   - [C6] group = first node in preorder with level >= l_min and (count <= n_crit or leaf).
+ *   - [C1, C2] integer geometry in units u = L/2^22: a level-k cell with index i has centre
  *     (2i+1)*2^(21-k) and half side 2^(21-k); the period is 2^22.
- *   - node-to-group offset wrapped into [-2^21, 2^21).
- *   - prune iff (double)S_gap * (u*u) > r_cut*r_cut, S_gap = sum of squared per-axis
+ *   - [C4] node-to-group offset wrapped into [-2^21, 2^21).
+ *   - [C2] prune iff (double)S_gap * (u*u) > r_cut*r_cut, S_gap = sum of squared per-axis
  *     gaps (exact integers) between the node's cell and the group's particle box: the
  *     smallest box of finest-level (level 21) cells that holds every particle of the
  *     group.  A particle of an opened leaf is tested the same way with its own finest
  *     cell and is left out when the test holds.  Either way the left-out mass lies
  *     farther than r_cut from every particle of the group, where Eq. 2 is exactly 0.
- *   - distance-dependent opening angle (Sec. 4.1, Eq. 12), when selected: theta(d) =
+ *   - [C17] distance-dependent opening angle (Sec. 4.1, Eq. 12), when selected: theta(d) =
  *     min(theta_max, theta0 / sqrt(R g(R))) with R = d/eta (the distance in units of eta,
  *     which makes theta0 dimensionless) and theta(d) = theta_max where R g(R) = 0; the
  *     accept test below then uses theta(d)^2 in place of theta^2.
- *   - accept iff level >= l_min and (double)(l*l) < (theta*theta) * (double)S_d,
+ *   - [C1] accept iff level >= l_min and (double)(l*l) < (theta*theta) * (double)S_d,
  *     l = node side, S_d = squared distance from node centre to the nearest point of
  *     the group cell (both in u).  Prune is tested first.
- *   - Plummer softening: acc = m g(r/eta) d / (r^2+eps^2)^(3/2); pairs with r^2 == 0
+ *   - [C7, C8] Plummer softening: acc = m g(r/eta) d / (r^2+eps^2)^(3/2); pairs with r^2 == 0
  *     are skipped.  eps = 0 gives Eq. 1 exactly.
- *   - minimum image per pair: d -= L while d > L/2; d += L while d < -L/2.
+ *   - [C4] minimum image per pair: d -= L while d > L/2; d += L while d < -L/2.
  */
 #include <math.h>
 #include <stdint.h>

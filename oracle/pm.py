@@ -97,7 +97,7 @@ def pm_accel(pos, mass, L, n, r_cut, scheme=TSC):
     for a in range(3):
         ka = ks[a].copy()
         ka[np.isclose(np.abs(ka), nyq)] = 0.0
-        grid = np.fft.irfftn(-1j * ka * phik, s=(n, n, n))
+        grid = np.fft.irfftn(-1j * ka * phik, s=(n, n, n), axes=(0, 1, 2))
         for i, wi in zip(ix, wx):
             for j, wj in zip(iy, wy):
                 for k, wk in zip(iz, wz):

@@ -596,3 +596,79 @@ def test_quadrupole_lowers_the_tree_error():
     r0, p0 = err(t.list_force_input_order())
     r1, p1 = err(t.list_force_input_order(quad=True))
     assert r1 < r0 / 3 and p1 < p0 / 3, (r0, r1, p0, p1)
+
+
+# --------------------------------------------------------------------------- second moments
+_QSLOTS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+
+
+def _qmat(q):
+    """3x3 symmetric matrix from the six slots xx, yy, zz, xy, xz, yz."""
+    out = np.zeros((3, 3))
+    for k, (a, b) in enumerate(_QSLOTS):
+        out[a, b] = out[b, a] = q[k]
+    return out
+
+
+def test_second_moments_match_their_definition_on_every_node():
+    """Sec. 4.1 second-order terms: Q of each node is sum m (x - COM)(x - COM)^T over the
+    node's particles, with the COM recomputed here from the sorted particles (not taken
+    from the oracle), on a clustered set whose nodes span every level from the root to
+    the leaves."""
+    pos, m = _clustered(3000, 41)
+    t = oracle.Tree(pos, m, 1.0, 0.1, n_crit=24)
+    _, _, xyz, ms = t.sorted()
+    nodes, Q = t.nodes(), t.quadrupoles()
+    assert Q.shape == (len(nodes), 6)
+    mm = ms.astype(np.float64)
+    for n in range(len(nodes)):
+        b, e = nodes[n, 4], nodes[n, 5]
+        w = mm[b:e]
+        com = (w[:, None] * xyz[b:e]).sum(0) / w.sum()
+        d = xyz[b:e] - com
+        ref = np.einsum("i,ia,ib->ab", w, d, d)
+        scale = w.sum() * max(np.abs(d).max(), 1e-300) ** 2
+        assert np.abs(_qmat(Q[n]) - ref).max() <= 1e-12 * scale, n
+
+
+def test_second_moments_obey_the_parallel_axis_identity():
+    """The second moments of a parent about its COM equal the sum over its children of
+    Q_c + M_c (c_c - c_p)(c_c - c_p)^T: holds only if every node's Q is taken about its
+    own centre of mass with the slots in the same order."""
+    pos, m = _clustered(2500, 43)
+    t = oracle.Tree(pos, m, 1.0, 0.1, n_crit=24)
+    nodes, mom, Q = t.nodes(), t.moments(), t.quadrupoles()
+    checked = 0
+    for p in range(len(nodes)):
+        if nodes[p, 7]:  # leaf
+            continue
+        kids, c = [], p + 1
+        while c < nodes[p, 6]:
+            kids.append(c)
+            c = nodes[c, 6]
+        acc = np.zeros((3, 3))
+        for c in kids:
+            d = mom[c, 1:] - mom[p, 1:]
+            acc += _qmat(Q[c]) + mom[c, 0] * np.outer(d, d)
+        ref = _qmat(Q[p])
+        assert np.abs(acc - ref).max() <= 1e-11 * max(np.abs(ref).max(), 1e-300), p
+        checked += 1
+    assert checked > 50
+
+
+def test_second_moments_of_a_point_symmetric_cloud_in_closed_form():
+    """Four equal masses m at c +- v1 and c +- v2 have their COM at c and second moments
+    2 m (v1 v1^T + v2 v2^T).  With v1 = (a, b, 0) and v2 = (0, g, h) every slot differs
+    (xy = 2 m a b, xz = 0, yz = 2 m g h), so a swapped slot or a moment taken about the
+    cell centre instead of the COM fails.  Exact dyadic inputs: the sums are exact."""
+    a, b, g, h = 2.0 ** -6, 3 * 2.0 ** -7, 5 * 2.0 ** -8, 2.0 ** -5
+    c = np.array([0.3125, 0.59375, 0.4375])   # not the centre of any cell holding the cloud
+    v1, v2 = np.array([a, b, 0.0]), np.array([0.0, g, h])
+    pos = np.array([c + v1, c - v1, c + v2, c - v2])
+    m = np.full(4, 0.25, np.float32)
+    t = oracle.Tree(pos, m, 1.0, 0.1, n_crit=4, n_leaf=10)
+    mom, Q = t.moments(), t.quadrupoles()
+    assert np.array_equal(mom[0, 1:], c)
+    want = 2 * 0.25 * (np.outer(v1, v1) + np.outer(v2, v2))
+    assert np.array_equal(_qmat(Q[0]), want)
+    assert Q[0, 3] == 2 * 0.25 * a * b and Q[0, 4] == 0.0 and Q[0, 5] == 2 * 0.25 * g * h
