@@ -43,8 +43,9 @@ extern "C" {
                                       NaN or of magnitude >= 2^38 seen on the device */
 #define GREEM_ERR_CUDA -2          /* a CUDA runtime call failed */
 #define GREEM_ERR_OOM -3           /* device or host allocation failed */
-#define GREEM_ERR_CAPACITY -4      /* a device buffer overflowed (only from graph replays; direct
-                                      calls grow their buffers and retry) */
+#define GREEM_ERR_CAPACITY -4      /* a device buffer overflowed: from graph replays, or from a
+                                      direct call still overflowing after its retries (direct
+                                      calls grow their buffers and retry, 6 attempts in all) */
 #define GREEM_ERR_TIMEOUT -5       /* a bounded device wait gave up; the context stays usable */
 #define GREEM_ERR_NOT_IMPLEMENTED -6
 
@@ -233,6 +234,46 @@ int greem_debug_dump(greem_ctx *ctx, int what, void *host_buf, int64_t cap_bytes
 int greem_debug_dump_group_lists(greem_ctx *ctx, const int64_t *groups, int64_t ngroups, int64_t *offsets,
                                  int64_t *entries, int64_t cap_entries, int64_t *n_entries);
 
+/* Failure-path controls, for tests of the error handling described above.  The paper
+ * has no counterpart: they exist so that every recovery path (capacity growth and
+ * retry, the retry bound, a bounded device wait that gives up) can be exercised without
+ * a GPU fault.  Each applies to this context only:
+ *   GREEM_DEBUG_WAIT_POLLS    the polls each list-chunk wait of the FP32 force kernel makes
+ *                             before it gives up (default 2^22): with 0 every call that
+ *                             streams a list returns GREEM_ERR_TIMEOUT, after the warp has
+ *                             let its copies land, and the context stays usable; value < 0
+ *                             restores the default.  Stays in effect until changed.
+ *   GREEM_DEBUG_NODE_CAP      starting tree-node capacity of the NEXT call (> 0)
+ *   GREEM_DEBUG_LIST_CAP      starting list-pool capacity, in entries, of the NEXT call (> 0)
+ *   GREEM_DEBUG_STACK_CAP     starting traversal-stack entries per list warp, from the NEXT
+ *                             call on (> 0)
+ *                             (a call that overflows a capacity grows it and retries, as it
+ *                             does from the usual first guesses; greem_stats.retries counts)
+ *   GREEM_DEBUG_MAX_ATTEMPTS  attempts per call before GREEM_ERR_CAPACITY is returned
+ *                             (default 6; value < 1 restores it).  Stays in effect.
+ * Errors: INVALID_ARG (NULL ctx, unknown what, value out of range). */
+#define GREEM_DEBUG_WAIT_POLLS 0
+#define GREEM_DEBUG_NODE_CAP 1
+#define GREEM_DEBUG_LIST_CAP 2
+#define GREEM_DEBUG_STACK_CAP 3
+#define GREEM_DEBUG_MAX_ATTEMPTS 4
+int greem_debug_set(greem_ctx *ctx, int what, int64_t value);
+
+/* The FP32 list entries of selected groups exactly as the force kernel reads them, for
+ * entry-level checks of the list builder as the FP32 force runs it (Sec. 3.1.1: positions
+ * relative to the group's centre; Sec. 2.2 step 5: one list per group).  Works after any
+ * force call.  Per group the unpadded list in the builder's own order (not sorted):
+ * entries is HOST float32 [cap_entries, 4], each (x, y, z) = the entry's position (a
+ * particle, or a node's centre of mass, shifted by its periodic image) minus the centre of
+ * the group's cell, in units of r_cut, and w = the mass.  index_entries, when not NULL,
+ * gets the matching HOST int64 [cap_entries, 5] entries (as GREEM_DUMP_LISTS) in the same
+ * order; it needs a last call with GREEM_FLAG_INDEX_LISTS.  groups, offsets and
+ * *n_entries as greem_debug_dump_group_lists.  Errors: INVALID_ARG (no lists, index
+ * entries asked for without index lists, bad group index, cap_entries too small), CUDA. */
+int greem_debug_dump_group_entries(greem_ctx *ctx, const int64_t *groups, int64_t ngroups, int64_t *offsets,
+                                   float *entries, int64_t *index_entries, int64_t cap_entries,
+                                   int64_t *n_entries);
+
 /* Picks n_crit from candidates[0..ncand) (ncand = 0 -> 32, 48, 64, 96, 128, 192, 256, 384,
  * 512) at p's list_chunk and block_shape, then list_chunk and block_shape at that n_crit,
  * then re-times the neighbouring n_crit candidates at the chosen shape; each setting is
@@ -252,12 +293,13 @@ int greem_pair_force_f32(greem_ctx *ctx, const double *x_g, const double *x_i, c
 
 /* The pairwise FP32 force of greem_pair_force_f32 for callers that cannot allocate
  * device memory (a library whose allocator policy forbids driver allocations, work that
- * must not synchronise the way cudaMalloc/cudaFree can, a process whose free memory
- * belongs to another allocator).  The paper has no counterpart: it is a deployment
- * variant.  It allocates nothing: its scratch is a file-scope device array sized for at
- * most 32768 pairs (about 6.5 MB, held on every GPU that loads the library until exit).
- * The caller passes inputs and output as for greem_pair_force_f32, plus the stream to
- * run on (NULL = legacy default stream); the call waits for that stream.  The first
+ * must not be held up by the device-wide synchronisation cudaMalloc/cudaFree can
+ * impose, a process whose free memory belongs to another allocator).  The paper has no
+ * counterpart: it is a deployment variant.  It allocates nothing: its scratch is a
+ * file-scope device array sized for at most 32768 pairs (about 6.5 MB, held on every GPU
+ * that loads the library until exit).  The caller passes inputs and output as for
+ * greem_pair_force_f32, plus the stream to run on (NULL = legacy default stream).  Every
+ * call waits for that stream, and only that stream, to read its status word.  The first
  * call on each device looks up the array's device address and should come before any
  * stream capture.  All calls on a device share the array (it keeps the last call's
  * contents); calls that overlap on the GPU race, so serialise them.

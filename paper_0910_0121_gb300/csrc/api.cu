@@ -19,6 +19,16 @@
 
 namespace greem {
 thread_local long long g_launches = 0;
+
+int current_device_index()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return dev >= 0 && dev < kMaxDevices ? dev : -1;
+}
 }
 
 using namespace greem;
@@ -76,6 +86,12 @@ struct greem_ctx {
     size_t list_cap = 0;
     uint32_t page = 0;
     uint32_t stack_cap = 4096;
+    // failure tests (greem_debug_set): starting capacities of the next call (0 = the
+    // usual first guess), attempts per call, and the force kernel's wait limit
+    size_t next_node_cap = 0, next_list_cap = 0;
+    uint32_t next_stack_cap = 0;
+    int max_attempts = 6;
+    uint32_t wait_polls1 = 0;
 
     // results of the last call
     uint64_t *ks = nullptr;
@@ -562,6 +578,7 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
         ev_record(c, r, ev, 5);
         launch_force_order(c->groups.p, n_groups, c->bins.p, c->order.p, s, nsm);
         ForceArgs fa = {};
+        fa.wait_polls1 = c->wait_polls1;
         fa.groups = c->groups.p;
         fa.n_groups = n_groups;
         fa.order = c->order.p;
@@ -670,21 +687,26 @@ static int run(greem_ctx *c, RunCfg r)
 {
     c->have_tree = c->have_lists = c->have_index = c->have_quad = false;
     // first guesses; an overflow grows them and the call is retried
-    if (c->node_cap < (size_t)(r.N * 0.5) + 4096u * r.nbox) c->node_cap = (size_t)(r.N * 0.75) + 4096u * r.nbox;
+    if (c->next_node_cap) c->node_cap = c->next_node_cap;
+    else if (c->node_cap < (size_t)(r.N * 0.5) + 4096u * r.nbox) c->node_cap = (size_t)(r.N * 0.75) + 4096u * r.nbox;
+    if (c->next_stack_cap) c->stack_cap = c->next_stack_cap;
     uint32_t pg = choose_page(r.N, c->nsm);
     if (pg > c->page) c->page = pg;
     if (r.lists_force) {
         const size_t warps = (size_t)c->nsm * kListBlocksPerSM * kListWarps;
-        c->list_cap = std::max<size_t>(c->list_cap, (size_t)r.N * 32 + warps * c->page);
+        if (c->next_list_cap) c->list_cap = c->next_list_cap;
+        else c->list_cap = std::max<size_t>(c->list_cap, (size_t)r.N * 32 + warps * c->page);
         // accepted nodes are a minority of the entries: a first guess of 4 per particle
         if (r.quad) c->qcap = std::max<size_t>(c->qcap, (size_t)r.N * 4 + 4096);
     }
+    c->next_node_cap = c->next_list_cap = 0;
+    c->next_stack_cap = 0;
     cudaEvent_t ev[7] = {};
     if (r.timing)
         for (auto &e : ev) cudaEventCreate(&e);
     int rc = GREEM_OK;
     c->stats.retries = 0;
-    for (int attempt = 0; attempt < 6; attempt++) {
+    for (int attempt = 0; attempt < c->max_attempts; attempt++) {
         greem::g_launches = 0;
         rc = enqueue(c, r, ev);
         if (rc == GREEM_OK) rc = finish(c, r, ev);
@@ -1225,16 +1247,19 @@ int greem_debug_dump_group_lists(greem_ctx *c, const int64_t *groups, int64_t ng
     if (!c->have_lists || !c->have_index) return GREEM_ERR_INVALID_ARG;
     const int64_t G = c->stats.n_groups;
     if (!cuda_ok(cudaStreamSynchronize(c->stream))) return GREEM_ERR_CUDA;
+    for (int64_t k = 0; k < ngroups; k++)
+        if (groups[k] < 0 || groups[k] >= G) return GREEM_ERR_INVALID_ARG;
+    std::vector<uint32_t> raw_all((size_t)G);
+    std::vector<unsigned long long> off_all((size_t)G);
+    if (G && (!cuda_ok(cudaMemcpy(raw_all.data(), c->lraw.p, (size_t)G * 4, cudaMemcpyDeviceToHost)) ||
+              !cuda_ok(cudaMemcpy(off_all.data(), c->loff.p, (size_t)G * 8, cudaMemcpyDeviceToHost))))
+        return GREEM_ERR_CUDA;
     std::vector<uint32_t> raw(ngroups);
     std::vector<unsigned long long> off(ngroups);
-    std::vector<Group> grp(ngroups);
     int64_t tot = 0;
     for (int64_t k = 0; k < ngroups; k++) {
-        const int64_t g = groups[k];
-        if (g < 0 || g >= G) return GREEM_ERR_INVALID_ARG;
-        if (!cuda_ok(cudaMemcpy(&raw[k], c->lraw.p + g, 4, cudaMemcpyDeviceToHost)) ||
-            !cuda_ok(cudaMemcpy(&off[k], c->loff.p + g, 8, cudaMemcpyDeviceToHost)))
-            return GREEM_ERR_CUDA;
+        raw[k] = raw_all[(size_t)groups[k]];
+        off[k] = off_all[(size_t)groups[k]];
         offsets[k] = tot;
         tot += raw[k];
     }
@@ -1242,22 +1267,25 @@ int greem_debug_dump_group_lists(greem_ctx *c, const int64_t *groups, int64_t ng
     *n_entries = tot;
     if (!entries || cap_entries < tot) return tot ? GREEM_ERR_INVALID_ARG : GREEM_OK;
     auto dec = [](unsigned v) -> int64_t { return v == 1u ? 1 : (v == 2u ? -1 : 0); };
+    // first particle of each entry (node begin for nodes) gives preorder: the nodes come
+    // to the host in one copy
+    const size_t nn = (size_t)c->stats.n_nodes;
+    std::vector<Node> nodes(nn);
+    if (nn && !cuda_ok(cudaMemcpy(nodes.data(), c->nodes.p, nn * sizeof(Node), cudaMemcpyDeviceToHost)))
+        return GREEM_ERR_CUDA;
     std::vector<unsigned long long> buf;
     int64_t e = 0;
     for (int64_t k = 0; k < ngroups; k++) {
         buf.resize(raw[k]);
         if (raw[k] && !cuda_ok(cudaMemcpy(buf.data(), c->ilist.p + off[k], (size_t)raw[k] * 8, cudaMemcpyDeviceToHost)))
             return GREEM_ERR_CUDA;
-        // first particle of each entry (node begin for nodes) gives preorder
         std::vector<std::pair<uint64_t, unsigned long long>> keyed(raw[k]);
         for (uint32_t t = 0; t < raw[k]; t++) {
             const unsigned long long v = buf[t];
             uint64_t first = (uint32_t)v;
             if ((v >> 32) & 1ull) {
-                Node nd;
-                if (!cuda_ok(cudaMemcpy(&nd, c->nodes.p + (uint32_t)v, sizeof(Node), cudaMemcpyDeviceToHost)))
-                    return GREEM_ERR_CUDA;
-                first = nd.begin;
+                if ((uint32_t)v >= nn) return GREEM_ERR_INVALID_ARG;
+                first = nodes[(uint32_t)v].begin;
             }
             keyed[t] = {first, v};
         }
@@ -1270,6 +1298,57 @@ int greem_debug_dump_group_lists(greem_ctx *c, const int64_t *groups, int64_t ng
             entries[5 * e + 2] = dec(code & 3u);
             entries[5 * e + 3] = dec((code >> 2) & 3u);
             entries[5 * e + 4] = dec((code >> 4) & 3u);
+        }
+    }
+    return GREEM_OK;
+}
+
+int greem_debug_dump_group_entries(greem_ctx *c, const int64_t *groups, int64_t ngroups, int64_t *offsets,
+                                   float *entries, int64_t *index_entries, int64_t cap_entries, int64_t *n_entries)
+{
+    if (!c || !groups || !offsets || !n_entries || ngroups < 0) return GREEM_ERR_INVALID_ARG;
+    *n_entries = 0;
+    if (!c->have_lists || (index_entries && !c->have_index)) return GREEM_ERR_INVALID_ARG;
+    const int64_t G = c->stats.n_groups;
+    if (!cuda_ok(cudaStreamSynchronize(c->stream))) return GREEM_ERR_CUDA;
+    for (int64_t k = 0; k < ngroups; k++)
+        if (groups[k] < 0 || groups[k] >= G) return GREEM_ERR_INVALID_ARG;
+    // list lengths and offsets of every group in one copy each
+    std::vector<uint32_t> raw_all((size_t)G);
+    std::vector<unsigned long long> off_all((size_t)G);
+    if (G && (!cuda_ok(cudaMemcpy(raw_all.data(), c->lraw.p, (size_t)G * 4, cudaMemcpyDeviceToHost)) ||
+              !cuda_ok(cudaMemcpy(off_all.data(), c->loff.p, (size_t)G * 8, cudaMemcpyDeviceToHost))))
+        return GREEM_ERR_CUDA;
+    int64_t tot = 0;
+    for (int64_t k = 0; k < ngroups; k++) {
+        offsets[k] = tot;
+        tot += raw_all[(size_t)groups[k]];
+    }
+    offsets[ngroups] = tot;
+    *n_entries = tot;
+    if (!entries || cap_entries < tot) return tot ? GREEM_ERR_INVALID_ARG : GREEM_OK;
+    auto dec = [](unsigned v) -> int64_t { return v == 1u ? 1 : (v == 2u ? -1 : 0); };
+    std::vector<unsigned long long> buf;
+    for (int64_t k = 0; k < ngroups; k++) {
+        const size_t g = (size_t)groups[k];
+        const uint32_t n = raw_all[g];
+        if (!n) continue;
+        if (!cuda_ok(cudaMemcpy(entries + 4 * offsets[k], c->flist.p + off_all[g], (size_t)n * sizeof(float4),
+                                cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        if (!index_entries) continue;
+        buf.resize(n);
+        if (!cuda_ok(cudaMemcpy(buf.data(), c->ilist.p + off_all[g], (size_t)n * 8, cudaMemcpyDeviceToHost)))
+            return GREEM_ERR_CUDA;
+        for (uint32_t t = 0; t < n; t++) {
+            const unsigned long long v = buf[t];
+            const unsigned code = (unsigned)(v >> 33) & 63u;
+            int64_t *o = index_entries + 5 * (offsets[k] + t);
+            o[0] = (int64_t)((v >> 32) & 1ull);
+            o[1] = (int64_t)(uint32_t)v;
+            o[2] = dec(code & 3u);
+            o[3] = dec((code >> 2) & 3u);
+            o[4] = dec((code >> 4) & 3u);
         }
     }
     return GREEM_OK;
@@ -1383,12 +1462,14 @@ int greem_pair_force_f32(greem_ctx *c, const double *x_g, const double *x_i, con
     bp.eps2 = (float)((eps / r_cut) * (eps / r_cut));
     cudaStream_t s = c->stream;
     greem::g_launches = 0;
-    cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s);
-    cudaMemcpyAsync(c->bps.p, c->bps_host, sizeof(BoxPar), cudaMemcpyHostToDevice, s);
+    if (!cuda_ok(cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s)) ||
+        !cuda_ok(cudaMemcpyAsync(c->bps.p, c->bps_host, sizeof(BoxPar), cudaMemcpyHostToDevice, s)))
+        return GREEM_ERR_CUDA;
     launch_pair_setup(x_g, x_i, x_j, m_j, (uint32_t)np, bp.inv_rc, c->groups.p, c->irel.p, c->flist.p, c->loff.p,
                       c->llen.p, c->lraw.p, c->v0.p, c->small.p, s);
-    ForceArgs fa;
-    memset(&fa, 0, sizeof(fa));
+    if (!cuda_ok(cudaGetLastError())) return GREEM_ERR_CUDA;
+    ForceArgs fa = {};
+    fa.wait_polls1 = c->wait_polls1;
     fa.groups = c->groups.p;
     fa.n_groups = c->small.p;
     fa.order = nullptr;
@@ -1404,8 +1485,10 @@ int greem_pair_force_f32(greem_ctx *c, const double *x_g, const double *x_i, con
     fa.chunk = 256;
     fa.warps = 8;
     launch_force_f32(fa, s, c->nsm, eps > 0);
-    cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
-    if (!cuda_ok(cudaStreamSynchronize(s))) return GREEM_ERR_CUDA;
+    if (!cuda_ok(cudaGetLastError())) return GREEM_ERR_CUDA;
+    if (!cuda_ok(cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s)) ||
+        !cuda_ok(cudaStreamSynchronize(s)))
+        return GREEM_ERR_CUDA;
     c->have_tree = c->have_lists = c->have_index = c->have_quad = false;
     if (c->st_host->flags & ST_TIMEOUT) return GREEM_ERR_TIMEOUT;
     return GREEM_OK;
@@ -1472,6 +1555,35 @@ int greem_peak_tflops(greem_ctx *c, int which, double *tflops)
     int err = 0;
     *tflops = peak_tflops(which, c->nsm, c->stream, &err);
     return err;
+}
+
+int greem_debug_set(greem_ctx *c, int what, int64_t value)
+{
+    if (!c) return GREEM_ERR_INVALID_ARG;
+    switch (what) {
+    case GREEM_DEBUG_WAIT_POLLS:
+        if (value > (int64_t)kWaitPolls) return GREEM_ERR_INVALID_ARG;
+        c->wait_polls1 = value < 0 ? 0u : (uint32_t)value + 1u;
+        return GREEM_OK;
+    case GREEM_DEBUG_NODE_CAP:
+        if (value < 1 || value > (int64_t)0xFFFFFFF0) return GREEM_ERR_INVALID_ARG;
+        c->next_node_cap = (size_t)value;
+        return GREEM_OK;
+    case GREEM_DEBUG_LIST_CAP:
+        if (value < 1) return GREEM_ERR_INVALID_ARG;
+        c->next_list_cap = (size_t)value;
+        return GREEM_OK;
+    case GREEM_DEBUG_STACK_CAP:
+        if (value < 1 || value > (1 << 24)) return GREEM_ERR_INVALID_ARG;
+        c->next_stack_cap = (uint32_t)value;
+        return GREEM_OK;
+    case GREEM_DEBUG_MAX_ATTEMPTS:
+        if (value > 64) return GREEM_ERR_INVALID_ARG;
+        c->max_attempts = value < 1 ? 6 : (int)value;
+        return GREEM_OK;
+    default:
+        return GREEM_ERR_INVALID_ARG;
+    }
 }
 
 const char *greem_strerror(int code)

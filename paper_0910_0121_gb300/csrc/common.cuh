@@ -59,6 +59,15 @@ struct BoxPar {
 };
 constexpr int kNotPow2 = -100000;
 
+// Polls of a bounded device wait before it gives up and records ST_TIMEOUT.
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+// Launch state that the runtime keeps per device (a kernel's shared-memory opt-in, an
+// occupancy query) is cached per device index below this bound; devices beyond it are
+// not cached (the attribute is set and the occupancy queried on every launch).
+constexpr int kMaxDevices = 64;
+int current_device_index();  // the current device, or -1 when it is not cached
+
 // Device status word and counters, cleared at the start of every call.
 struct DevStatus {
     unsigned int flags;
@@ -253,6 +262,9 @@ struct ForceArgs {
     DevStatus *st;
     int chunk;                 // list entries per staged chunk
     int warps;                 // warps per block
+    // polls of each list-chunk wait, plus one (0: kWaitPolls); only a failure test
+    // lowers it, through greem_debug_set
+    uint32_t wait_polls1 = 0;
 };
 void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t *bins, uint32_t *order,
                         cudaStream_t s, int nsm);

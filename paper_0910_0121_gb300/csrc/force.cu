@@ -30,6 +30,8 @@
 // The group's list streams through a per-warp double buffer in shared memory filled by
 // 1-D bulk asynchronous copies (cp.async.bulk, the TMA engine) that complete on an
 // mbarrier; every entry is read by the part's lanes as one broadcast 16-byte load.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace greem {
@@ -73,10 +75,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait on a phase; false after the iteration limit (the caller records a timeout).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Bounded wait on a phase; false after `polls` polls (the caller records a timeout).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t polls)
 {
-    for (uint32_t it = 0; it < (1u << 22); ++it)
+    for (uint32_t it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -482,22 +484,22 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
         }
     }
     const uint32_t nch = (len + ce - 1) / ce;
+    const uint32_t polls = a.wait_polls1 ? a.wait_polls1 - 1u : kWaitPolls;
     if (nch) issue_chunk(src, ce, stride, wp, 0, lo, 0, len, lane);
     bool ok = true;
     for (uint32_t c = 0; c < nch; c++) {
         const int b = (int)(c & 1u);
         if (c + 1 < nch) issue_chunk(src, ce, stride, wp, b ^ 1, lo, c + 1, len, lane);
-        const bool got = mbar_wait_bounded(&wp.bar[b], wp.ph[b]);
-        wp.ph[b] ^= 1u;
+        const bool got = mbar_wait_bounded(&wp.bar[b], wp.ph[b], polls);
         if (!__all_sync(FULL, got)) {
             ok = false;
-            // let a copy that is still in flight land before the warp leaves
-            if (c + 1 < nch) {
-                mbar_wait_bounded(&wp.bar[b ^ 1], wp.ph[b ^ 1]);
-                wp.ph[b ^ 1] ^= 1u;
-            }
+            // the warp leaves the kernel: let every copy it has in flight land first, the
+            // chunk it gave up on and the prefetched one (at the full poll limit)
+            mbar_wait_bounded(&wp.bar[b], wp.ph[b], kWaitPolls);
+            if (c + 1 < nch) mbar_wait_bounded(&wp.bar[b ^ 1], wp.ph[b ^ 1], kWaitPolls);
             break;
         }
+        wp.ph[b] ^= 1u;
         const float4 *buf = wp.buf[b];
         const uint32_t nj = min(ce, len - c * ce);
         if constexpr (QUAD) {
@@ -769,7 +771,13 @@ void launch_force_order(const Group *groups, const uint32_t *n_groups, uint32_t 
     g_launches += 3;
 }
 
-static int g_force_smem_set[3] = {0, 0, 0};
+// Per device: the shared-memory opt-in of each force-kernel instantiation, and its
+// occupancy per block shape as (smem << 8) | blocks per SM (0 = not queried yet).
+struct ForceLaunchCache {
+    std::atomic<int> smem_set[3];
+    std::atomic<long long> occ[3][17];
+};
+static ForceLaunchCache g_force_cache[kMaxDevices];
 
 // Dynamic shared memory of the FP32 force kernel: two chunk buffers per warp.
 size_t force_smem_bytes(int chunk, int warps)
@@ -783,19 +791,24 @@ void launch_force_f32(const ForceArgs &a, cudaStream_t s, int nsm, bool soft, bo
     const size_t smem = force_smem_bytes(a.chunk, a.warps);
     auto kern = quad ? k_force_f32<false, true> : (soft ? k_force_f32<true, false> : k_force_f32<false, false>);
     const int which = quad ? 2 : (soft ? 1 : 0);
-    if (g_force_smem_set[which] < (int)smem) {
+    // the opt-in applies to the current device only; the occupancy is queried once per
+    // device and shape (not while a stream is being captured)
+    const int dev = current_device_index();
+    ForceLaunchCache *fc = dev >= 0 ? &g_force_cache[dev] : nullptr;
+    if (!fc || fc->smem_set[which].load() < (int)smem) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForceSmemMax);
-        g_force_smem_set[which] = (int)kForceSmemMax;
+        if (fc) fc->smem_set[which].store((int)kForceSmemMax);
     }
-    // occupancy is queried once per shape (not while a stream is being captured)
-    static int cached[3][17][2] = {};
-    static size_t cached_smem[3][17] = {};
-    int &per_sm = cached[which][a.warps][0];
-    if (cached_smem[which][a.warps] != smem || per_sm == 0) {
+    const long long key = (long long)smem << 8;
+    long long occ = fc ? fc->occ[which][a.warps].load() : 0;
+    if ((occ & ~0xffll) != key || (occ & 0xff) == 0) {
+        int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-        if (per_sm < 1) per_sm = 1;
-        cached_smem[which][a.warps] = smem;
+        per_sm = per_sm < 1 ? 1 : (per_sm > 255 ? 255 : per_sm);
+        occ = key | per_sm;
+        if (fc) fc->occ[which][a.warps].store(occ);
     }
+    const int per_sm = (int)(occ & 0xff);
     kern<<<nsm * per_sm, threads, smem, s>>>(a);
     g_launches++;
 }
@@ -940,10 +953,13 @@ __global__ void __launch_bounds__(256) k_force_f64(ForceArgs a)
 
 void launch_force_f64(const ForceArgs &a, cudaStream_t s, int nsm)
 {
-    static int per_sm = 0;
+    static std::atomic<int> cached[kMaxDevices];
+    const int dev = current_device_index();
+    int per_sm = dev >= 0 ? cached[dev].load() : 0;
     if (per_sm == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_f64, 256, 0);
         if (per_sm < 1) per_sm = 1;
+        if (dev >= 0) cached[dev].store(per_sm);
     }
     k_force_f64<<<nsm * per_sm, 256, 0, s>>>(a);
     g_launches++;

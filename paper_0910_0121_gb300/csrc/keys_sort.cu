@@ -5,6 +5,8 @@
 // to 2^21-1, and the three indices are bit-interleaved with x as the high bit of each
 // 3-bit digit.  Every FP64 step uses explicit round-to-nearest intrinsics so that no
 // multiply-add is fused: the key is a pure function of the IEEE inputs.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace greem {
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(kRsThreads, GREEM_RS_MINB) k_rs_onesweep(const
                 const unsigned long long *w8 = status + (size_t)j * 256 + tid;
                 uint32_t it = 0;
                 while ((ld_relaxed_u64(w8) >> 62) == 0ull) {
-                    if (++it >= (1u << 22)) {
+                    if (++it >= kWaitPolls) {
                         atomicOr(&st->flags, ST_TIMEOUT);
                         timeout = true;
                         break;
@@ -365,11 +367,13 @@ void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t
                 const uint32_t *box_off, int nbox, uint32_t *hist, unsigned long long *status, DevStatus *st,
                 uint64_t **k_out, uint32_t **v_out, cudaStream_t s, int nsm)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
+    // the shared-memory opt-in applies to the current device only: set once per device
+    static std::atomic<bool> attr_set[kMaxDevices];
+    const int dev = current_device_index();
+    if (dev < 0 || !attr_set[dev].load()) {
         cudaFuncSetAttribute(k_rs_onesweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem);
         cudaFuncSetAttribute(k_rs_onesweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem);
-        attr_set = true;
+        if (dev >= 0) attr_set[dev].store(true);
     }
     const uint32_t ntile = rs_tiles(n);
     const int passes = key_passes + box_passes;

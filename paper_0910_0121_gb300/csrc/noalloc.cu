@@ -2,8 +2,9 @@
 // callers that cannot allocate device memory.
 //
 // Who needs it: code that runs where cudaMalloc is not allowed or not wanted, e.g. a
-// host library whose allocator policy forbids driver allocations, a caller recording
-// work into a stream that must not synchronise (cudaMalloc and cudaFree can), or a
+// host library whose allocator policy forbids driver allocations, a caller that must
+// not be held up by the device-wide synchronisation that cudaMalloc and cudaFree can
+// impose (this call waits only for its own stream, to read its status word), or a
 // process that has handed all free device memory to another allocator.  Such callers
 // still own the inputs and the output; only the scratch is provided here.
 //
@@ -42,13 +43,24 @@ constexpr size_t kScratchBytes = align256(kOffPerm + sizeof(uint32_t) * kNoAlloc
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Writes the one box of constants the force kernel reads (no host staging buffer).
-__global__ void k_noalloc_box(BoxPar *bp, float inv_rc2, float eps2)
+// Writes the one box of constants the force kernel reads (no host staging buffer) and
+// clears the status word (flags and work-queue counters), which must start at zero on
+// every call.
+__global__ void k_noalloc_box(BoxPar *bp, DevStatus *st, float inv_rc2, float eps2)
 {
-    BoxPar b = {};
-    b.inv_rc2 = inv_rc2;
-    b.eps2 = eps2;
-    *bp = b;
+    if (threadIdx.x == 0) {
+        BoxPar b = {};
+        b.inv_rc2 = inv_rc2;
+        b.eps2 = eps2;
+        *bp = b;
+    }
+    uint32_t *w = reinterpret_cast<uint32_t *>(st);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevStatus) / 4); i += blockDim.x) w[i] = 0u;
+}
+
+static int launch_failed()
+{
+    return cudaGetLastError() != cudaSuccess;
 }
 
 static std::mutex g_noalloc_mu;
@@ -94,11 +106,13 @@ extern "C" int greem_pair_force_f32_noalloc(const double *x_g, const double *x_i
     uint32_t *perm = reinterpret_cast<uint32_t *>(base + kOffPerm);
 
     const double inv_rc = 1.0 / r_cut;
-    // the status word (flags and work-queue counters) must start at zero on every call
-    cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
-    k_noalloc_box<<<1, 1, 0, s>>>(bp, (float)(inv_rc * inv_rc), (float)((eps / r_cut) * (eps / r_cut)));
+    // an error left by earlier work on this thread is not this call's
+    cudaGetLastError();
+    k_noalloc_box<<<1, 32, 0, s>>>(bp, st, (float)(inv_rc * inv_rc), (float)((eps / r_cut) * (eps / r_cut)));
+    if (launch_failed()) return GREEM_ERR_CUDA;
     launch_pair_setup(x_g, x_i, x_j, m_j, (uint32_t)npairs, inv_rc, groups, irel, flist, loff, llen, lraw, perm, ng,
                       s);
+    if (launch_failed()) return GREEM_ERR_CUDA;
     ForceArgs fa = {};
     fa.groups = groups;
     fa.n_groups = ng;
@@ -120,6 +134,7 @@ extern "C" int greem_pair_force_f32_noalloc(const double *x_g, const double *x_i
         return GREEM_ERR_CUDA;
     }
     launch_force_f32(fa, s, nsm, eps > 0);
+    if (launch_failed()) return GREEM_ERR_CUDA;
     unsigned int flags = 0;
     if (cudaMemcpyAsync(&flags, &st->flags, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

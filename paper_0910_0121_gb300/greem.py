@@ -33,6 +33,8 @@ FLAG_QUADRUPOLE = 16
 ASSIGN_CIC = 0
 ASSIGN_TSC = 1
 
+DEBUG_WAIT_POLLS, DEBUG_NODE_CAP, DEBUG_LIST_CAP, DEBUG_STACK_CAP, DEBUG_MAX_ATTEMPTS = range(5)
+
 DUMP_KEYS, DUMP_PERM, DUMP_NODES, DUMP_MOMENTS, DUMP_GROUPS, DUMP_LIST_OFFSETS, DUMP_LISTS, DUMP_QUADRUPOLES = range(8)
 
 
@@ -102,13 +104,16 @@ def _lib():
             L.greem_softening.argtypes = [dbl, dbl, dbl]
             L.greem_softening.restype = dbl
             L.greem_cosmo_factors.argtypes = [dbl, dbl, dbl, dbl, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+            L.greem_debug_set.argtypes = [vp, i32, i64]
+            L.greem_debug_dump_group_entries.argtypes = [vp, vp, i64, vp, vp, vp, i64, ctypes.POINTER(i64)]
             L.greem_strerror.argtypes = [i32]
             L.greem_strerror.restype = ctypes.c_char_p
             for f in ("greem_create", "greem_build_tree", "greem_short_force", "greem_short_force_ex",
                       "greem_short_force_batched", "greem_short_force_host", "greem_pm_force", "greem_graph_capture", "greem_graph_launch",
                       "greem_get_stats", "greem_debug_dump", "greem_autotune", "greem_pair_force_f32",
                       "greem_peak_tflops", "greem_debug_dump_group_lists", "greem_kick", "greem_drift",
-                      "greem_timestep", "greem_cosmo_factors"):
+                      "greem_timestep", "greem_cosmo_factors", "greem_debug_set",
+                      "greem_debug_dump_group_entries"):
                 getattr(L, f).restype = i32
             _L = L
     return _L
@@ -325,6 +330,10 @@ class Context:
         _check(_lib().greem_peak_tflops(self._h, int(which), ctypes.byref(v)), "greem_peak_tflops")
         return v.value
 
+    def debug_set(self, what: int, value: int):
+        """greem_debug_set: failure-path controls (DEBUG_* constants)."""
+        _check(_lib().greem_debug_set(self._h, int(what), int(value)), "greem_debug_set")
+
     def stats(self) -> dict:
         s = Stats()
         _check(_lib().greem_get_stats(self._h, ctypes.byref(s)), "greem_get_stats")
@@ -345,6 +354,25 @@ class Context:
                                                    ent.ctypes.data_as(vp), n.value, ctypes.byref(n)),
                "greem_debug_dump_group_lists")
         return off, ent[: n.value]
+
+    def dump_group_entries(self, groups, index: bool = False):
+        """(offsets [n+1], FP32 entries [E,4], index entries [E,5] or None) of the selected
+        groups' lists in the builder's own order (greem_debug_dump_group_entries)."""
+        g = np.ascontiguousarray(groups, dtype=np.int64)
+        off = np.zeros(g.shape[0] + 1, np.int64)
+        n = ctypes.c_int64()
+        vp = ctypes.c_void_p
+        rc = _lib().greem_debug_dump_group_entries(self._h, g.ctypes.data_as(vp), g.shape[0], off.ctypes.data_as(vp),
+                                                  None, None, 0, ctypes.byref(n))
+        if rc != OK and n.value == 0:
+            raise GreemError(rc, "greem_debug_dump_group_entries")
+        ent = np.zeros((max(n.value, 1), 4), np.float32)
+        idx = np.zeros((max(n.value, 1), 5), np.int64) if index else None
+        _check(_lib().greem_debug_dump_group_entries(self._h, g.ctypes.data_as(vp), g.shape[0],
+                                                     off.ctypes.data_as(vp), ent.ctypes.data_as(vp),
+                                                     None if idx is None else idx.ctypes.data_as(vp), n.value,
+                                                     ctypes.byref(n)), "greem_debug_dump_group_entries")
+        return off, ent[: n.value], (None if idx is None else idx[: n.value])
 
     def dump(self, what: int) -> np.ndarray:
         n = ctypes.c_int64()

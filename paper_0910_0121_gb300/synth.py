@@ -116,7 +116,7 @@ def zeldovich(n: int, rms_spacing: float, rng: np.random.Generator) -> np.ndarra
     inv = 1.0 / k2
     psi = np.empty((n, n, n, 3), dtype=np.float64)
     for a, ka in enumerate((kx, ky, kz)):
-        psi[..., a] = np.fft.irfftn(1j * ka * delta * inv, s=(n, n, n))
+        psi[..., a] = np.fft.irfftn(1j * ka * delta * inv, s=(n, n, n), axes=(0, 1, 2))
     psi = psi.reshape(-1, 3)
     rms = np.sqrt(np.mean(np.sum(psi * psi, axis=1)))
     psi *= (rms_spacing / n) / rms
