@@ -67,6 +67,8 @@ def lib():
             L.or_lmin.argtypes = [_dbl, _dbl]
             L.or_direct.restype = ctypes.c_int
             L.or_direct.argtypes = [_vp, _vp, _i64, _dbl, _dbl, _dbl, _vp, ctypes.c_int]
+            L.or_direct_at.restype = ctypes.c_int
+            L.or_direct_at.argtypes = [_vp, _vp, _i64, _dbl, _dbl, _dbl, _vp, _i64, _vp, ctypes.c_int]
             L.or_tree_build.restype = _vp
             L.or_tree_build.argtypes = [_vp, _vp, _i64, _dbl, _dbl, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int)]
@@ -174,6 +176,18 @@ def direct(pos, mass, L: float, r_cut: float, eps: float = 0.0, nthreads: int = 
     acc = np.zeros((p.shape[0], 3))
     rc = lib().or_direct(_ptr(p), _ptr(m), p.shape[0], float(L), float(r_cut), float(eps), _ptr(acc),
                          int(nthreads))
+    if rc:
+        raise ValueError(f"oracle direct sum rejected arguments ({rc})")
+    return acc
+
+
+def direct_at(pos, mass, L: float, r_cut: float, idx, eps: float = 0.0, nthreads: int = 0) -> np.ndarray:
+    """The brute-force sum of ``direct`` for the particles idx only ([len(idx), 3])."""
+    p, m = _pos(pos), _mass(mass)
+    ii = np.ascontiguousarray(idx, dtype=np.int64)
+    acc = np.zeros((ii.shape[0], 3))
+    rc = lib().or_direct_at(_ptr(p), _ptr(m), p.shape[0], float(L), float(r_cut), float(eps), _ptr(ii),
+                            ii.shape[0], _ptr(acc), int(nthreads))
     if rc:
         raise ValueError(f"oracle direct sum rejected arguments ({rc})")
     return acc

@@ -198,6 +198,26 @@ static double min_image(double d, double L)
     return d;
 }
 
+/* Eq. 1 summed over every other particle j (minimum image, index order) for particle i
+ * of the wrapped positions w. */
+static void direct_one(const double *w, const float *mass, int64_t N, double L, double eta, double eps, int64_t i,
+                       double *out)
+{
+    double a[3] = {0, 0, 0};
+    for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double d[3], f[3];
+        for (int c = 0; c < 3; c++) d[c] = min_image(w[3 * j + c] - w[3 * i + c], L);
+        or_pair_accel(d, (double)mass[j], eta, eps, f);
+        a[0] += f[0];
+        a[1] += f[1];
+        a[2] += f[2];
+    }
+    out[0] = a[0];
+    out[1] = a[1];
+    out[2] = a[2];
+}
+
 int or_direct(const double *pos, const float *mass, int64_t N, double L, double r_cut, double eps,
               double *acc, int nthreads)
 {
@@ -210,21 +230,28 @@ int or_direct(const double *pos, const float *mass, int64_t N, double L, double 
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 64)
 #endif
-    for (int64_t i = 0; i < N; i++) {
-        double a[3] = {0, 0, 0};
-        for (int64_t j = 0; j < N; j++) {
-            if (j == i) continue;
-            double d[3], f[3];
-            for (int c = 0; c < 3; c++) d[c] = min_image(w[3 * j + c] - w[3 * i + c], L);
-            or_pair_accel(d, (double)mass[j], eta, eps, f);
-            a[0] += f[0];
-            a[1] += f[1];
-            a[2] += f[2];
-        }
-        acc[3 * i + 0] = a[0];
-        acc[3 * i + 1] = a[1];
-        acc[3 * i + 2] = a[2];
-    }
+    for (int64_t i = 0; i < N; i++) direct_one(w, mass, N, L, eta, eps, i, acc + 3 * i);
+    free(w);
+    return 0;
+}
+
+/* The same sum for the particles idx[0..nt) only (acc [nt,3]): O(N) per particle, for the
+ * tree-against-direct error on sets too large for the whole O(N^2) sum. */
+int or_direct_at(const double *pos, const float *mass, int64_t N, double L, double r_cut, double eps,
+                 const int64_t *idx, int64_t nt, double *acc, int nthreads)
+{
+    if (N < 1 || nt < 0 || !(L > 0) || !(r_cut > 0) || !(r_cut < 0.5 * L)) return -1;
+    for (int64_t k = 0; k < nt; k++)
+        if (idx[k] < 0 || idx[k] >= N) return -1;
+    double eta = 0.5 * r_cut;
+    double *w = (double *)malloc(sizeof(double) * 3 * N);
+    if (!w) return -3;
+    for (int64_t i = 0; i < 3 * N; i++) w[i] = or_wrap(pos[i], L);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t k = 0; k < nt; k++) direct_one(w, mass, N, L, eta, eps, idx[k], acc + 3 * k);
     free(w);
     return 0;
 }

@@ -5,11 +5,17 @@ same autotuner over the same candidates).
 Whole-array checks where the oracle computes everything cheaply (keys, permutation,
 tree nodes, groups: bit-exact; moments to summation order); per-group checks on a
 seeded sample of groups for what the oracle computes one group at a time (lists
-bit-exact, FP32 force within median 1e-5 / 99.9th percentile 1e-4, FP64 form 1e-11).
+bit-exact, the FP32 entries of the timed launch entry by entry, FP32 force within
+median 1e-5 / 99.9th percentile 1e-4, FP64 form 1e-11).  The sample is at least 2% of
+the groups, stratified by interaction count (group size x list length), plus the
+heaviest groups (the dense halo cores, whose lists are longest).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
+import listcheck
 import oracle
 from paper_0910_0121_gb300 import synth
 
@@ -25,7 +31,29 @@ _build.build()
 from paper_0910_0121_gb300 import greem  # noqa: E402
 
 BENCH_CANDIDATES = [48, 64, 96, 128, 192, 256]   # the candidates bench.py autotunes over
-NSAMPLE = 300
+FRAC, NSTRATA, NHEAVY = 0.02, 10, 64
+
+
+def _list_lengths(ctx, n_groups):
+    """Unpadded list length of every group of the last call (offsets only, no entries)."""
+    g = np.arange(n_groups, dtype=np.int64)
+    off = np.zeros(n_groups + 1, np.int64)
+    n = ctypes.c_int64()
+    vp = ctypes.c_void_p
+    greem.lib().greem_debug_dump_group_entries(ctx._h, g.ctypes.data_as(vp), n_groups, off.ctypes.data_as(vp),
+                                               None, None, 0, ctypes.byref(n))
+    assert n.value == off[-1]
+    return np.diff(off)
+
+
+def _stratified_sample(weight, rng):
+    """FRAC of the groups from each of NSTRATA strata of equal size by weight, plus the
+    NHEAVY heaviest; sorted and unique."""
+    order = np.argsort(weight, kind="stable")
+    parts = [rng.choice(st, size=max(1, int(np.ceil(FRAC * len(st)))), replace=False)
+             for st in np.array_split(order, NSTRATA)]
+    parts.append(order[-NHEAVY:])
+    return np.unique(np.concatenate(parts))
 
 
 def _rel(a, ref):
@@ -54,16 +82,20 @@ def full(request):
                       list_chunk=best.list_chunk, block_shape=best.block_shape)
     acc_plain = ctx.short_force(P, M, pf, acc).cpu().numpy().astype(np.float64)
     stats_plain = ctx.stats()
+    # the sample, stratified by interaction count, and the FP32 entries of the timed launch
+    nodes, grp = ctx.dump(greem.DUMP_NODES), ctx.dump(greem.DUMP_GROUPS)
+    count = nodes[grp, 5] - nodes[grp, 4]
+    rng = np.random.default_rng(20240 + len(request.param))
+    sel = _stratified_sample(count * _list_lengths(ctx, len(grp)), rng)
+    ent_plain = ctx.dump_group_entries(sel)
     acc = ctx.short_force(P, M, p, acc)
     torch.cuda.synchronize()
     out = dict(name=request.param, pos=pos, mass=mass, prm=prm, p=p, ctx=ctx, P=P, M=M,
                acc=acc.cpu().numpy().astype(np.float64), acc_plain=acc_plain, stats_plain=stats_plain,
-               stats_index=ctx.stats())
+               stats_index=ctx.stats(), ent_plain=ent_plain, ent_index=ctx.dump_group_entries(sel, index=True))
     for w in (greem.DUMP_KEYS, greem.DUMP_PERM, greem.DUMP_NODES, greem.DUMP_MOMENTS, greem.DUMP_GROUPS):
         out[w] = ctx.dump(w)
     T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=p.n_crit, n_leaf=p.n_leaf)
-    rng = np.random.default_rng(20240 + len(request.param))
-    sel = np.sort(rng.choice(T.n_groups, size=min(NSAMPLE, T.n_groups), replace=False))
     T.build_lists(prm["theta"], sel)
     out.update(T=T, sel=sel)
     yield out
@@ -98,6 +130,28 @@ def test_sampled_lists_bit_exact(full):
     assert np.array_equal(gent[:, 0], kind.astype(np.int64))
     assert np.array_equal(gent[:, 1], idx)
     assert np.array_equal(gent[:, 2:], sh.astype(np.int64))
+
+
+def test_sample_covers_two_percent_and_the_heaviest_groups(full):
+    G = full["stats_plain"]["n_groups"]
+    assert len(full["sel"]) >= FRAC * G
+    print(f"{full['name']}: {len(full['sel'])} of {G} groups sampled, {len(full['ent_plain'][1])} list entries")
+
+
+def test_sampled_fp32_entries_of_the_timed_launch(full):
+    """The FP32 entries written by the list builder of the launch bench.py times (no
+    index lists), entry by entry: bitwise equal to those of the index-list launch, which
+    match the oracle-derived positions and masses (tests/listcheck.py)."""
+    off0, f0, _ = full["ent_plain"]
+    off1, f1, ix = full["ent_index"]
+    assert np.array_equal(off0, off1)
+    assert np.array_equal(f0.view(np.uint32), f1.view(np.uint32))
+    rel, mass, kind = listcheck.expected_entries(full["T"], full["prm"]["L"], full["prm"]["r_cut"], full["sel"],
+                                                 off1, ix)
+    worst = listcheck.check_entries(f0, rel, mass, kind)
+    print(f"{full['name']}: {len(f0)} FP32 entries, worst {worst:.3f} of the tolerance")
+    toff = full["T"].lists()[0]
+    assert np.array_equal(off1, toff)
 
 
 def test_sampled_force_fp32_and_fp64(full):

@@ -8,6 +8,7 @@ oracle's FP64 force on identical lists; the FP64 form to 1e-11.
 import numpy as np
 import pytest
 
+import listcheck
 import oracle
 from paper_0910_0121_gb300 import synth
 
@@ -82,14 +83,17 @@ def case(request, ctx):
         prm["n_crit"] = 64
     acc_plain = gpu_force(ctx, pos, mass, prm, flags=0)   # no index lists: the launch bench.py times
     stats_plain = ctx.stats()
+    allg = np.arange(stats_plain["n_groups"])
+    ent_plain = ctx.dump_group_entries(allg)              # the FP32 lists of that launch
     acc32 = gpu_force(ctx, pos, mass, prm)
     stats_index = ctx.stats()
+    ent_index = ctx.dump_group_entries(allg, index=True)
     dumps = {w: ctx.dump(w) for w in (greem.DUMP_KEYS, greem.DUMP_PERM, greem.DUMP_NODES, greem.DUMP_MOMENTS,
                                       greem.DUMP_GROUPS, greem.DUMP_LIST_OFFSETS, greem.DUMP_LISTS)}
     T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm.get("n_leaf", 10))
     T.build_lists(prm["theta"])
     return dict(name=request.param, pos=pos, mass=mass, prm=prm, acc32=acc32, acc_plain=acc_plain, dumps=dumps, T=T,
-                stats_plain=stats_plain, stats_index=stats_index)
+                stats_plain=stats_plain, stats_index=stats_index, ent_plain=ent_plain, ent_index=ent_index)
 
 
 def test_keys_and_sort_bit_exact(case):
@@ -133,6 +137,30 @@ def test_lists_bit_exact(case):
     assert np.array_equal(gl[:, 0], kind.astype(np.int64))
     assert np.array_equal(gl[:, 1], idx)
     assert np.array_equal(gl[:, 2:], sh.astype(np.int64))
+
+
+def test_fp32_list_entries(case):
+    """The FP32 entries the force kernel reads, element by element.  The list builder
+    without index lists (the instantiation the bench times) writes exactly the FP32
+    entries of the index-list instantiation, in the same order; those match the oracle's
+    FP64 positions relative to the group's cell centre (r_cut units) within a few FP32
+    roundings, with the masses, entry by entry in the builder's order."""
+    off0, f0, _ = case["ent_plain"]
+    off1, f1, ix = case["ent_index"]
+    assert np.array_equal(off0, off1)
+    assert np.array_equal(f0.view(np.uint32), f1.view(np.uint32))
+    prm = case["prm"]
+    groups = np.arange(len(off1) - 1)
+    rel, mass, kind = listcheck.expected_entries(case["T"], prm["L"], prm["r_cut"], groups, off1, ix)
+    worst = listcheck.check_entries(f0, rel, mass, kind)
+    print(f"{case['name']}: {len(f0)} entries, worst {worst:.3f} of the tolerance")
+    # the builder's order holds the same entries as the oracle's preorder lists
+    toff, tkind, tidx, _ = case["T"].lists()
+    assert np.array_equal(off1, toff)
+    for g in range(len(off1) - 1):
+        a = ix[off1[g]:off1[g + 1], :2]
+        b = np.stack([tkind[toff[g]:toff[g + 1]], tidx[toff[g]:toff[g + 1]]], axis=1)
+        assert np.array_equal(a[np.lexsort(a.T[::-1])], b[np.lexsort(b.T[::-1])])
 
 
 def test_force_f32_within_bounds(case):

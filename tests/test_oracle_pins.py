@@ -122,6 +122,19 @@ def test_momentum_conservation_direct():
     assert np.all(np.abs(p) < 1e-13 * scale)
 
 
+def test_direct_sum_at_selected_particles_is_the_direct_sum():
+    """direct_at (the O(N)-per-particle sum used for the tree-against-direct error at full
+    size) returns exactly the rows of the pinned all-pairs sum, in the order asked."""
+    rng = np.random.default_rng(3)
+    pos = rng.random((700, 3)) * 2.0 - 0.5          # some outside [0, L): wrapped
+    m = rng.uniform(0.5, 1.5, 700).astype(np.float32)
+    full = oracle.direct(pos, m, 1.0, 0.2, eps=1e-3)
+    idx = np.array([699, 0, 350, 17, 17])
+    assert np.array_equal(oracle.direct_at(pos, m, 1.0, 0.2, idx, eps=1e-3), full[idx])
+    with pytest.raises(ValueError):
+        oracle.direct_at(pos, m, 1.0, 0.2, [700])
+
+
 def test_lattice_zero_force():
     """A perfect periodic n^3 lattice has zero short-range force by symmetry."""
     n = 10
