@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the graph, theta-scan and batched lines")
     ap.add_argument("--config5", action="store_true",
                     help="time the 512^3 full TreePM step (PP + TSC PM on 512^3) in one CUDA graph instead")
+    ap.add_argument("--no-config5", action="store_true",
+                    help="leave the 512^3 TreePM graph out of the default line's extras")
+    ap.add_argument("--no-direct", action="store_true",
+                    help="leave out the tree-against-direct error (oracle direct sums for sampled particles)")
     ap.add_argument("--quad", action="store_true",
                     help="with --profile-case: add the second-order (quadrupole) terms, theta = 0.7")
     ap.add_argument("--profile-case", choices=["nfw128", "zel256", "zel256tree"], default=None,
@@ -162,14 +166,37 @@ def oracle_force_sample(T, prm, frac, seed):
     return t_sample, float(cnt.sum()) / float(cnt[sel].sum()), ns, nthreads
 
 
-def oracle_sample(pos, mass, prm, n_crit, frac=0.02, seed=7):
-    """One oracle step on a bounded sample: S1-S4 on everything, S5-S6 on a group sample
-    scaled to all groups.  Returns (seconds for the whole step, description, threads)."""
+# The paper's own rate, for context only: the whole TreePM step at theta = 0.5 ran at about
+# 5e4 particles/s per core on the Cray XT4 (2.2 GHz quad-core Opteron; abstract, Sec. 5),
+# for a 512^3 LCDM run with more than 1e6 particles per core.
+PAPER_RATE = {"value": 5.0e4, "unit": "particles/s per core",
+              "hardware": "Cray XT4, quad-core Opteron 2.2 GHz (FP64 storage, single-precision pair kernel)",
+              "workload": "whole TreePM step, 512^3 LCDM, theta = 0.5, > 1e6 particles per core",
+              "source": "abstract; Sec. 5", "kind": "context, not the target"}
+
+
+def oracle_sample(pos, mass, prm, n_crit, frac=0.02, seed=7, frac1=0.0025):
+    """One oracle step on a bounded sample: S1-S4 on everything (one thread), S5-S6 on a
+    group sample on all host cores scaled to all groups, and again on a smaller sample on
+    one thread.  Returns (seconds for the whole step, description, threads, seconds for the
+    whole step on one thread)."""
     T, t_tree = oracle_tree(pos, mass, prm, n_crit)
     t_s, scale, ns, nth = oracle_force_sample(T, prm, frac, seed)
+    import oracle
+    G = T.n_groups
+    rng = np.random.default_rng(seed + 1)
+    sel1 = np.sort(rng.choice(G, size=max(8, int(G * frac1)), replace=False))
+    t1 = time.perf_counter()
+    T.build_lists(prm["theta"], sel1)
+    T.list_force(0.0, 1)
+    t_1 = time.perf_counter() - t1
+    nodes, grp = T.nodes(), T.groups()
+    cnt = nodes[grp, 5] - nodes[grp, 4]
+    scale1 = float(cnt.sum()) / float(cnt[sel1].sum())
     desc = (f"S1-S4 on all {len(pos)} particles ({t_tree:.1f} s, 1 thread); lists+force on a seeded "
-            f"{ns}/{T.n_groups} group sample ({t_s:.2f} s, {nth} threads) scaled x{scale:.0f} by particle count")
-    return t_tree + t_s * scale, desc, nth
+            f"{ns}/{G} group sample ({t_s:.2f} s, {nth} threads) scaled x{scale:.0f} by particle count; "
+            f"1-thread leg: lists+force on {len(sel1)} groups ({t_1:.2f} s) scaled x{scale1:.0f}")
+    return t_tree + t_s * scale, desc, nth, t_tree + t_1 * scale1
 
 
 def reference_arm(args, rank, world):
@@ -180,16 +207,21 @@ def reference_arm(args, rank, world):
     N = len(pos)
     # the n_crit the GPU arm's autotuner settles on for this workload (its config line)
     n_crit = args.n_crit or 192
-    T, t_tree = oracle_tree(pos, mass, prm, n_crit)
-    times = []
-    nth, ns = 1, 0
+    times, walls, trees = [], [], []
+    nth, ns, G = 1, 0, 0
     for k in range(args.warmup + args.steps):
+        w0 = time.perf_counter()
+        T, t_tree = oracle_tree(pos, mass, prm, n_crit)
         t_s, scale, ns, nth = oracle_force_sample(T, prm, 0.0005, 100 + k)
+        G = T.n_groups
+        del T
         if k >= args.warmup:
             times.append(t_tree + t_s * scale)
-    desc = (f"S1-S4 on all {N} particles timed once ({t_tree:.1f} s, 1 thread) and added to every step; "
-            f"per step lists+force on a fresh seeded {ns}/{T.n_groups} group sample ({nth} threads) "
-            f"scaled to all groups by particle count")
+            walls.append(time.perf_counter() - w0)
+            trees.append(t_tree)
+    desc = (f"every step: S1-S4 on all {N} particles (1 thread, {statistics.mean(trees):.1f} s) and lists+force on "
+            f"a fresh seeded {ns}/{G} group sample ({nth} threads), scaled to all groups by particle count; "
+            f"ms_per_step is that projection, sample_wall_ms_per_step the measured time of the sampled step")
     v = N / statistics.mean(times)
     line = {"metric": METRIC, "value": v, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
@@ -198,6 +230,7 @@ def reference_arm(args, rank, world):
             "config": {"workload": WORKLOAD, "N": N, "theta": prm["theta"], "r_cut": prm["r_cut"], "n_crit": n_crit,
                        "n_leaf": 10},
             "cpu_baseline": {"value": v, "unit": "particles/s", "cores": nth, "kind": "oracle", "sample": desc},
+            "projected": True, "sample_wall_ms_per_step": 1e3 * statistics.mean(walls),
             "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -218,7 +251,7 @@ def traffic_per_launch(list_entries):
         return None
 
 
-def extras(ctx, P, M, p, prm, acc, stream):
+def extras(ctx, P, M, p, prm, acc, stream, rows=None, tvd_dev=None):
     """Context numbers beside the headline: CUDA-graph replay of the same step, the
     opening-angle scan, the distance-dependent opening angle of Eq. 12, the integration
     kernels, the second-order terms, and the 64-box batched workload (one call vs per-box
@@ -256,6 +289,8 @@ def extras(ctx, P, M, p, prm, acc, stream):
         b.record(stream)
         torch.cuda.synchronize()
         s = ctx.stats()
+        if rows is not None:
+            rows[f"theta{th}"] = acc[tvd_dev].double().cpu().numpy()
         scan[str(th)] = {"ms_per_step": a.elapsed_time(b), "N_int": s["n_interactions"] / N,
                          "force_tflops": FLOPS_PER_INTERACTION * s["n_interactions"] / (s["ms_force"] * 1e-3) / 1e12}
     out["theta_scan"] = scan
@@ -270,6 +305,8 @@ def extras(ctx, P, M, p, prm, acc, stream):
     b.record(stream)
     torch.cuda.synchronize()
     s = ctx.stats()
+    if rows is not None:
+        rows["eq12_theta0_0.25_max0.7"] = acc[tvd_dev].double().cpu().numpy()
     out["theta_eq12"] = {"theta0": 0.25, "theta_max": 0.7, "ms_per_step": a.elapsed_time(b),
                          "N_int": s["n_interactions"] / N, "lists_ms": s["ms_lists"], "force_ms": s["ms_force"]}
     # the integration around the force (Sec. 2.2 steps 1, 6, 7; Eq. 7): kick, drift and the
@@ -298,6 +335,8 @@ def extras(ctx, P, M, p, prm, acc, stream):
         b.record(stream)
         torch.cuda.synchronize()
         s = ctx.stats()
+        if rows is not None:
+            rows[f"quadrupole_theta{th}"] = acc[tvd_dev].double().cpu().numpy()
         quad[str(th)] = {"ms_per_step": a.elapsed_time(b), "N_int": s["n_interactions"] / N, "force_ms": s["ms_force"]}
     out["quadrupole"] = quad
     # 64 independent boxes: one batched call vs one call per box (FP32) and per-box FP64 calls
@@ -335,6 +374,148 @@ def extras(ctx, P, M, p, prm, acc, stream):
                         "per_box_fp64_ms": t64, "batched_particles_per_s": NB / (t_batched * 1e-3),
                         "speedup_vs_per_box_fp32": t_single / t_batched, "speedup_vs_per_box_fp64": t64 / t_batched}
     return out
+
+
+N_DIRECT, SEED_DIRECT = 512, 9100777
+
+
+def guarded(fn, *a, **kw):
+    """A context leg of the line: its dict, or its error, without losing the line."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 - reported in the line
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+def error_stats(a, ref):
+    """Relative error |a - ref| / |ref| per particle; particles with |ref| below 1e-6 of the
+    median are left out (reading C13)."""
+    n = np.linalg.norm(ref, axis=1)
+    keep = n > 1e-6 * np.median(n[n > 0])
+    e = np.linalg.norm(a - ref, axis=1)[keep] / n[keep]
+    return {"median": float(np.median(e)), "p90": float(np.quantile(e, 0.9)), "p99": float(np.quantile(e, 0.99)),
+            "p999": float(np.quantile(e, 0.999)), "max": float(e.max()), "n": int(keep.sum())}
+
+
+def tree_vs_direct(pos, mass, prm, rows):
+    """The error of the GPU tree force (FP32) against the brute-force minimum-image sum of
+    Eq. 1-2 over all N particles (the oracle's FP64 direct sum, O(N) per particle) at a
+    seeded sample of particles: the tree approximation error of Sec. 3.1.2, reported, not
+    bounded."""
+    import oracle
+    idx = rows["idx"]
+    t0 = time.perf_counter()
+    ref = oracle.direct_at(pos, mass, prm["L"], prm["r_cut"], idx)
+    out = {"particles": len(idx), "seed": SEED_DIRECT, "direct_s": time.perf_counter() - t0,
+           "reference": "oracle direct_at: FP64 brute-force minimum-image sum over all N",
+           "denominator": "|a_direct|, particles below 1e-6 of the median left out"}
+    for k, v in rows.items():
+        if k != "idx":
+            out[k] = error_stats(v, ref)
+    return out
+
+
+def config2_leg(ctx, stream, steps=5):
+    """The 128^3 NFW mix (half uniform, half in 1000 NFW halos), r_cut = 3/128, theta = 0.5,
+    n_crit = 64: the FP32 relative-coordinate force against the plain FP64 form, step and
+    force times, and each form's error against the oracle's FP64 list force on a seeded
+    2% group sample."""
+    import torch
+    import oracle
+    from paper_0910_0121_gb300 import greem, synth
+    pos, mass, prm = synth.config_nfw128()
+    N = len(pos)
+    P, M = torch.from_numpy(pos).cuda(), torch.from_numpy(mass).cuda()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"workload": "nfw128: 128^3, 50% uniform + 1000 NFW halos", "N": N, "r_cut": prm["r_cut"],
+           "theta": prm["theta"], "n_crit": prm["n_crit"], "n_leaf": prm["n_leaf"]}
+    accs = {}
+    for name, prec, dt, reps in (("fp32", greem.F32_REL, torch.float32, steps), ("fp64", greem.F64, torch.float64, 2)):
+        q = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=prm["n_crit"],
+                         n_leaf=prm["n_leaf"], precision=prec, flags=greem.FLAG_STAGE_TIMES)
+        acc = torch.empty((N, 3), dtype=dt, device="cuda")
+        ctx.short_force(P, M, q, acc)
+        a, b = ev(), ev()
+        fms = []
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            ctx.short_force(P, M, q, acc)
+            fms.append(ctx.stats()["ms_force"])
+        b.record(stream)
+        torch.cuda.synchronize()
+        s = ctx.stats()
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"ms_per_step": ms, "particles_per_s": N / (ms * 1e-3), "force_kernel_ms": statistics.mean(fms),
+                     "N_int": s["n_interactions"] / N}
+        accs[name] = acc.double().cpu().numpy()
+    out["fp32"]["force_tflops"] = (FLOPS_PER_INTERACTION * out["fp32"]["N_int"] * N
+                                   / (out["fp32"]["force_kernel_ms"] * 1e-3) / 1e12)
+    out["force_speedup_fp32_vs_fp64"] = out["fp64"]["force_kernel_ms"] / out["fp32"]["force_kernel_ms"]
+    out["step_speedup_fp32_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32"]["ms_per_step"]
+    T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm["n_leaf"])
+    G = T.n_groups
+    sel = np.sort(np.random.default_rng(SEED_DIRECT + 2).choice(G, size=max(8, int(0.02 * G)), replace=False))
+    T.build_lists(prm["theta"], sel)
+    ref_sorted = T.list_force()
+    _, perm, _, _ = T.sorted()
+    nodes, grp = T.nodes(), T.groups()
+    srt = np.concatenate([np.arange(nodes[grp[g], 4], nodes[grp[g], 5]) for g in sel])
+    ref = ref_sorted[srt]
+    for name in ("fp32", "fp64"):
+        out[name]["error_vs_oracle"] = error_stats(accs[name][perm[srt]], ref)
+    out["oracle_sample"] = f"FP64 list force on identical lists, {len(sel)}/{G} seeded groups, {len(srt)} particles"
+    return out
+
+
+def config5_leg(args):
+    """512^3 Zel'dovich (rms 1 spacing) + 20000 NFW halos, theta = 0.5, r_cut = 3/512: the
+    whole TreePM force (short-range tree force plus PM with TSC on 512^3) replayed as one
+    CUDA graph.  Returns its line (a dict)."""
+    import torch
+    from paper_0910_0121_gb300 import greem, synth
+    t0 = time.time()
+    pos, mass, prm = synth.config_zel512()
+    gen_s = time.time() - t0
+    N = len(pos)
+    P = torch.from_numpy(pos).cuda()
+    M = torch.from_numpy(mass).cuda()
+    del pos
+    acc = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = greem.Context(stream)
+    nc = args.n_crit or 192
+    p = greem.params(L=1.0, r_cut=prm["r_cut"], theta=0.5, n_crit=nc, flags=greem.FLAG_ADD_PM, n_pm=512,
+                     assign=greem.ASSIGN_TSC)
+    try:
+        ctx.graph_capture(P, M, p, acc)
+        st = ctx.stats()
+        for _ in range(max(3, args.warmup)):
+            ctx.graph_launch()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                rc = ctx.graph_launch()
+                if rc != greem.OK:
+                    raise greem.GreemError(rc, "greem_graph_launch")
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        s = ctx.stats()
+        free, total = torch.cuda.mem_get_info()
+        return {"metric": "full TreePM step particles/s (short-range tree force + PM)", "value": N / (ms * 1e-3),
+                "unit": "particles/s", "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+                "workload": "zeldovich512+20000nfw_theta0.5_pm512_tsc", "N": N, "r_cut": prm["r_cut"], "theta": 0.5,
+                "n_crit": nc, "n_pm": 512, "assign": "TSC", "graph": True,
+                "N_int": s["n_interactions"] / N, "n_groups": s["n_groups"], "n_nodes": s["n_nodes"],
+                "list_capacity_entries": s["list_capacity"], "kernel_launches_per_step": st["kernel_launches"],
+                "device_mem_gb": (total - free) / 1e9, "generation_s": gen_s, "clocks": clk.summary()}
+    finally:
+        ctx.close()
+        del P, M, acc
+        torch.cuda.empty_cache()
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -396,6 +577,11 @@ def gpu_arm(args, rank, world, local):
     barrier()
     ms, value = across_ranks(e0.elapsed_time(e1) / args.steps, N, dist, "cuda")
     clocks = clk.summary()
+    # the particles whose tree force is compared with the direct sum (Sec. 3.1.2), and the
+    # accelerations of the timed call (theta = 0.5) at them
+    tvd_idx = np.sort(np.random.default_rng(SEED_DIRECT).choice(N, size=N_DIRECT, replace=False))
+    tvd_dev = torch.from_numpy(tvd_idx).cuda()
+    rows = {"idx": tvd_idx, "theta0.5": acc[tvd_dev].double().cpu().numpy()}
 
     # ---- end to end through the public API with host buffers: greem_short_force_host
     # copies every step's inputs in (pinned host -> device) and its result out (device ->
@@ -467,12 +653,23 @@ def gpu_arm(args, rank, world, local):
         "clocks": clocks,
     }
     if not args.no_extras:
-        line["extras"] = extras(ctx, P, M, p, prm, acc, stream)
+        line["extras"] = extras(ctx, P, M, p, prm, acc, stream, rows, tvd_dev)
+    if rank == 0 and not args.no_direct:
+        line["tree_vs_direct"] = tree_vs_direct(pos, mass, prm, rows)
+    if rank == 0 and not args.no_extras:
+        line["extras"]["config2"] = guarded(config2_leg, ctx, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_cpu, desc, nth = oracle_sample(pos, mass, prm, n_crit=p.n_crit)
+        t_cpu, desc, nth, t_cpu1 = oracle_sample(pos, mass, prm, n_crit=p.n_crit)
         line["cpu_baseline"] = {"value": N / t_cpu, "unit": "particles/s", "cores": nth, "kind": "oracle",
-                                "sample": desc}
+                                "sample": desc, "one_thread": {"value": N / t_cpu1, "unit": "particles/s",
+                                                               "cores": 1},
+                                "paper_context": dict(PAPER_RATE, gpu_equivalent_cores=value / PAPER_RATE["value"])}
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_extras and not args.no_config5:
+        # the 512^3 TreePM step holds about 135 GB: the 256^3 buffers go first
+        del P, M, acc, acc64
+        torch.cuda.empty_cache()
+        line["extras"]["config5"] = guarded(config5_leg, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -480,54 +677,18 @@ def gpu_arm(args, rank, world, local):
 
 
 def config5_arm(args):
-    """512^3 Zel'dovich (rms 1 spacing) + 20000 NFW halos, theta = 0.5, r_cut = 3/512: the
-    whole TreePM force (short-range tree force plus PM with TSC on 512^3) as one graph."""
-    import torch
+    """--config5: the 512^3 TreePM graph of config5_leg as a line of its own."""
     from paper_0910_0121_gb300 import build as _build
-    from paper_0910_0121_gb300 import greem, synth
 
     _build.build()
-    t0 = time.time()
-    pos, mass, prm = synth.config_zel512()
-    gen_s = time.time() - t0
-    N = len(pos)
-    P = torch.from_numpy(pos).cuda()
-    M = torch.from_numpy(mass).cuda()
-    del pos
-    acc = torch.empty((N, 3), dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    ctx = greem.Context(stream)
-    nc = args.n_crit or 192
-    p = greem.params(L=1.0, r_cut=prm["r_cut"], theta=0.5, n_crit=nc, flags=greem.FLAG_ADD_PM, n_pm=512,
-                     assign=greem.ASSIGN_TSC)
-    ctx.graph_capture(P, M, p, acc)
-    st = ctx.stats()
-    for _ in range(max(3, args.warmup)):
-        ctx.graph_launch()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            rc = ctx.graph_launch()
-            if rc != greem.OK:
-                raise greem.GreemError(rc, "greem_graph_launch")
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    s = ctx.stats()
-    line = {"metric": "full TreePM step particles/s (short-range tree force + PM)", "value": N / (ms * 1e-3),
-            "unit": "particles/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "zeldovich512+20000nfw_theta0.5_pm512_tsc", "N": N, "r_cut": prm["r_cut"],
-                       "theta": 0.5, "n_crit": nc, "n_pm": 512, "assign": "TSC", "graph": True},
-            "N_int": s["n_interactions"] / N, "n_groups": s["n_groups"], "n_nodes": s["n_nodes"],
-            "list_capacity_entries": s["list_capacity"], "kernel_launches_per_step": st["kernel_launches"],
-            "device_mem_gb": torch.cuda.mem_get_info()[1] / 1e9 - torch.cuda.mem_get_info()[0] / 1e9,
-            "generation_s": gen_s, "clocks": clk.summary()}
+    leg = config5_leg(args)
+    line = {k: leg[k] for k in ("metric", "value", "unit", "steps", "warmup", "ms_per_step")}
+    line.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                 "data": "synthetic",
+                 "config": {k: leg[k] for k in ("workload", "N", "r_cut", "theta", "n_crit", "n_pm", "assign",
+                                                 "graph")}})
+    line.update({k: v for k, v in leg.items() if k not in line and k not in line["config"]})
     print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def profile_case(args):
