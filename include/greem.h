@@ -308,6 +308,78 @@ int greem_pair_force_f32(greem_ctx *ctx, const double *x_g, const double *x_i, c
 int greem_pair_force_f32_noalloc(const double *x_g, const double *x_i, const double *x_j, const float *m_j,
                                  int64_t npairs, double r_cut, double eps, float *acc, void *cuda_stream);
 
+/* ---- Several processes on one box (Sec. 2.2 steps 3, 4 and 7; Sec. 2.3.1) -----------------
+ * The paper divides the periodic box into p subboxes by recursive multisection, one per
+ * process, with boundaries set by sampled particles (Sec. 2.3.1).  Each process builds the
+ * tree of its own particles, sends every other process the local essential tree (LET) that
+ * process needs, and computes the force on its particles from a tree of its particles and
+ * the items it received (steps 3-5).  The calls below are the per-process pieces; the data
+ * exchange between processes is the caller's (an all-to-all of the counts and items).
+ *
+ * A domain box is int32 [6] = (xlo, xhi, ylo, yhi, zlo, zhi) in finest cells (L/2^21, the
+ * cells of the Morton key), half-open per axis, 0 <= lo <= hi <= 2^21; a particle belongs
+ * to the box that holds its finest cell.  A set of boxes (at most 1024) must tile the
+ * periodic box. */
+
+/* Eq. 3-5: the number of particles a process samples for the next decomposition.
+ * n_samp = N R f with f = t_local / t_sum (Eq. 4, the process's share of the measured
+ * force time; f = 1/nproc when t_sum <= 0, before any time is measured), raised to
+ * n_local R / (1 + alpha) when that is larger (Eq. 5; alpha < 0 leaves the lower limit
+ * out), rounded, and capped at n_local.  Host only.  Returns the count, or -1 for invalid
+ * arguments (n_total < 0, n_local outside [0, n_total], nproc < 1, rate < 0 or not finite). */
+int64_t greem_sample_count(int64_t n_total, int64_t n_local, int nproc, double rate, double t_local, double t_sum,
+                           double alpha);
+
+/* Recursive multisection of the sampled particles (Sec. 2.2; Sec. 2.3.1): cells (HOST int32
+ * [n, 3], the samples' finest cells, from greem_cell_index on every process, gathered) are
+ * cut along x into px slabs holding equal numbers of samples, each slab along y into py
+ * columns, each column along z into pz boxes.  A cut lies between the two samples that the
+ * equal split separates (rounded up, so equal cells stay on one side); a part with no
+ * samples is cut evenly.  boxes: HOST int32 [px*py*pz, 6], box (a, b, c) at index
+ * (a*py + b)*pz + c.  The same samples give the same boxes on every process.  Host only.
+ * Errors: INVALID_ARG (n < 0, px, py or pz < 1, more than 1024 boxes, a cell outside
+ * [0, 2^21)). */
+int greem_domain_boxes(const int32_t *cells, int64_t n, int px, int py, int pz, int32_t *boxes);
+
+/* The finest cells (reading of the Morton key: wrap into [0, L), floor((x/L) 2^21) clamped
+ * to 2^21 - 1) of the particles idx[0..n) of pos [N, 3] (all device; idx NULL = the first n
+ * particles): cells DEVICE int32 [n, 3].  Waits for the stream.  Errors: INVALID_ARG (bad
+ * sizes, L <= 0, an index outside [0, N), a NaN/Inf coordinate), CUDA. */
+int greem_cell_index(greem_ctx *ctx, const double *pos, int64_t N, double L, const int64_t *idx, int64_t n,
+                     int32_t *cells);
+
+/* Particles packed by destination domain for their redistribution (Sec. 2.2 step 7): each
+ * particle's domain is the box (HOST boxes [ndom, 6]) holding its finest cell; pos_out
+ * (wrapped into [0, L)), mass_out and ids_out (ids[i], or i when ids is NULL) receive the
+ * particles of domain 0, then 1, ..., each in input order (stable); counts (HOST int64
+ * [ndom]) gets the number per domain.  All arrays but boxes and counts are DEVICE, N rows,
+ * owned by the caller.  Waits for the stream.  Errors: INVALID_ARG (bad sizes, boxes out of
+ * range, a particle in no box or with a NaN/Inf coordinate), CUDA, OOM. */
+int greem_domain_pack(greem_ctx *ctx, const double *pos, const float *mass, const int64_t *ids, int64_t N, double L,
+                      const int32_t *boxes, int ndom, int64_t *counts, double *pos_out, float *mass_out,
+                      int64_t *ids_out);
+
+/* The local essential trees (Sec. 2.2 step 3; Eq. 10) of the tree built by the last
+ * greem_build_tree (or force) call of this context, one box, for every domain d != self
+ * of boxes (HOST [ndom, 6]): in node preorder, each accepted node as one item (its centre
+ * of mass and mass) and the particles of each opened leaf that lie within r_cut of domain
+ * d.  A node is visited when every ancestor was opened; it is pruned when its cell lies
+ * farther than r_cut from the box (reading C2, the box in place of the group's particle
+ * box), accepted when its level is at least l_min and the squared distance from its cell
+ * centre to the nearest point of the box passes the opening test of the build's theta
+ * (reading C1, or Eq. 12 when the build used it), and opened otherwise.  Items go out
+ * packed by domain: pos_out DEVICE float64 [cap, 3] (absolute, wrapped), mass_out DEVICE
+ * float32 [cap], ref_out DEVICE int64 [cap] or NULL (the sorted particle index, or
+ * -1 - node for a node); counts HOST int64 [ndom] (0 for self and empty boxes); *total =
+ * the items needed.  Each item is 28 bytes (Eq. 10 counts 16; the positions stay FP64
+ * because the receiving process subtracts its group centres in FP64, Sec. 3.1.1).  At
+ * theta = 0 no node is accepted and the items are exactly the particles within r_cut.
+ * Waits for the stream.  Errors: INVALID_ARG (no tree, a multi-box call, bad boxes,
+ * self >= ndom), CAPACITY (*total > cap: nothing past cap is written; call again with
+ * cap >= *total), CUDA, OOM. */
+int greem_let_export(greem_ctx *ctx, const int32_t *boxes, int ndom, int self, int64_t *counts, double *pos_out,
+                     float *mass_out, int64_t *ref_out, int64_t cap, int64_t *total);
+
 /* ---- Time integration (Sec. 2.2 steps 1, 6, 7; Sec. 2.4) --------------------------------
  * The paper kicks the velocities with the PM and then the PP force of the step (it keeps
  * no accelerations) and then drifts the positions; with the total force of one call that

@@ -95,6 +95,8 @@ def lib():
             L.or_short_force.restype = ctypes.c_int
             L.or_short_force.argtypes = [_vp, _vp, _i64, _dbl, _dbl, _dbl, ctypes.c_int, ctypes.c_int,
                                          _dbl, _vp, ctypes.c_int]
+            L.or_let_export.restype = _i64
+            L.or_let_export.argtypes = [_vp, _vp, _dbl, _vp, _vp, _i64]
             L.or_max_threads.restype = ctypes.c_int
             L.or_max_threads.argtypes = []
             _lib = L
@@ -283,6 +285,19 @@ class Tree:
         sh = np.zeros((ne, 3), np.int8)
         lib().or_lists_get(self._h, _ptr(off), _ptr(kind), _ptr(idx), _ptr(sh))
         return off, kind, idx, sh
+
+    def let_export(self, box, theta: float):
+        """Local essential tree for the domain box (int [6]: xlo, xhi, ylo, yhi, zlo, zhi in
+        finest cells, half-open) at opening angle theta (Sec. 2.2 step 3): (kind [n] 1 node /
+        0 particle, index [n] node or sorted particle), in preorder."""
+        b = np.ascontiguousarray(box, dtype=np.int32)
+        n = lib().or_let_export(self._h, _ptr(b), float(theta), None, None, 0)
+        if n < 0:
+            raise ValueError("oracle LET rejected arguments")
+        kind = np.zeros(max(n, 1), np.int64)
+        idx = np.zeros(max(n, 1), np.int64)
+        lib().or_let_export(self._h, _ptr(b), float(theta), _ptr(kind), _ptr(idx), n)
+        return kind[:n], idx[:n]
 
     def list_force(self, eps: float = 0.0, nthreads: int = 0, quad: bool = False) -> np.ndarray:
         """FP64 list force in SORTED order ([N,3]; particles of groups without lists are 0);

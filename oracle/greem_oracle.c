@@ -631,6 +631,105 @@ static int walk_rec(walk_t *W, int64_t n)
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Local essential tree for one receiving domain (Sec. 2.2 step 3): walk the tree in
+ * preorder; a node whose cell lies farther than r_cut from the domain box is skipped, a
+ * node that satisfies the opening criterion from the box (level >= l_min, l^2 < theta^2 d^2
+ * with d the distance from its cell centre to the nearest point of the box) is sent as
+ * one item, a leaf that is opened sends its particles whose finest cell lies within r_cut
+ * of the box, and any other node is opened.  The same tests as the list walk (readings C1,
+ * C2, C4) with the box in place of the group's cell and particle box.  The box is
+ * [lo, hi) per axis in finest cells, i.e. [2 lo, 2 hi) in u; distances are periodic. */
+typedef struct {
+    const or_tree *t;
+    int64_t cb[3], hb[3]; /* box centre and half sides, units u */
+    double uu, rc2, th2;
+    int64_t *kind, *idx;  /* output: kind 1 node / 0 particle, index */
+    int64_t n, cap;
+} let_t;
+
+static int64_t per_gap(int64_t cbox, int64_t c, int64_t hsum)
+{
+    const int64_t P = (int64_t)1 << 22, H = (int64_t)1 << 21;
+    int64_t d = cbox - c;
+    if (d >= H) d -= P;
+    else if (d < -H) d += P;
+    if (d < 0) d = -d;
+    d -= hsum;
+    return d > 0 ? d : 0;
+}
+
+static int let_push(let_t *W, int64_t kind, int64_t idx)
+{
+    if (W->n < W->cap) {
+        W->kind[W->n] = kind;
+        W->idx[W->n] = idx;
+    }
+    W->n++;
+    return 0;
+}
+
+static void let_rec(let_t *W, int64_t n)
+{
+    const or_tree *t = W->t;
+    int k = t->lvl[n];
+    int64_t hn = (int64_t)1 << (21 - k);
+    int64_t cn[3] = {(2 * t->ix[n] + 1) * hn, (2 * t->iy[n] + 1) * hn, (2 * t->iz[n] + 1) * hn};
+    int64_t sgap = 0, sd = 0;
+    for (int c = 0; c < 3; c++) {
+        int64_t g = per_gap(W->cb[c], cn[c], hn + W->hb[c]);
+        int64_t e = per_gap(W->cb[c], cn[c], W->hb[c]);
+        sgap += g * g;
+        sd += e * e;
+    }
+    if ((double)sgap * W->uu > W->rc2) return;
+    int64_t l = 2 * hn;
+    if (k >= t->lmin && (double)(l * l) < W->th2 * (double)sd) {
+        let_push(W, 1, n);
+        return;
+    }
+    if (t->leaf[n]) {
+        for (int64_t j = t->beg[n]; j < t->end[n]; j++) {
+            int64_t cj[3] = {2 * or_cell_index(t->x[j], t->L) + 1, 2 * or_cell_index(t->y[j], t->L) + 1,
+                             2 * or_cell_index(t->z[j], t->L) + 1};
+            int64_t s2 = 0;
+            for (int c = 0; c < 3; c++) {
+                int64_t g = per_gap(W->cb[c], cj[c], 1 + W->hb[c]);
+                s2 += g * g;
+            }
+            if ((double)s2 * W->uu > W->rc2) continue;
+            let_push(W, 0, j);
+        }
+        return;
+    }
+    for (int64_t c = n + 1; c < t->skip[n]; c = t->skip[c]) let_rec(W, c);
+}
+
+/* Items of the LET for box[6] at opening angle theta: kind/idx [cap]; returns the number
+ * of items (those beyond cap are counted, not written), or -1 for a bad box. */
+int64_t or_let_export(const or_tree *t, const int32_t box[6], double theta, int64_t *kind, int64_t *idx, int64_t cap)
+{
+    if (!(theta >= 0)) return -1;
+    let_t W;
+    W.t = t;
+    for (int c = 0; c < 3; c++) {
+        int64_t lo = box[2 * c], hi = box[2 * c + 1];
+        if (lo < 0 || hi > ((int64_t)1 << 21) || lo > hi) return -1;
+        if (lo == hi) return 0;
+        W.cb[c] = lo + hi;
+        W.hb[c] = hi - lo;
+    }
+    W.uu = t->u * t->u;
+    W.rc2 = t->r_cut * t->r_cut;
+    W.th2 = theta * theta;
+    W.kind = kind;
+    W.idx = idx;
+    W.n = 0;
+    W.cap = cap;
+    let_rec(&W, 0);
+    return W.n;
+}
+
 /* Build lists for groups gsel[0..ns) (all groups when gsel == NULL). */
 static int lists_build(or_tree *t, double theta, int eq12, double theta0, const int64_t *gsel, int64_t ns);
 

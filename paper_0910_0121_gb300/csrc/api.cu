@@ -116,6 +116,12 @@ struct greem_ctx {
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
 
+    // domains and local essential trees
+    DBuf<int32_t> dom_boxes;
+    DBuf<uint32_t> dom, dom_cnt;
+    DBuf<uint8_t> let_flag;
+    DBuf<uint32_t> let_cnt;
+
     // graph
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -854,6 +860,8 @@ void greem_destroy(greem_ctx *c)
     release(c->flist); release(c->ilist); release(c->loff);
     release(c->llen); release(c->lraw); release(c->kids); release(c->stack); release(c->order); release(c->bins);
     release(c->lvl); release(c->bps); release(c->box_off); release(c->small); release(c->st);
+    release(c->qlist); release(c->qcnt); release(c->qoff);
+    release(c->dom_boxes); release(c->dom); release(c->dom_cnt); release(c->let_flag); release(c->let_cnt);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->bps_host) cudaFreeHost(c->bps_host);
     if (c->box_off_host) cudaFreeHost(c->box_off_host);
@@ -1555,6 +1563,137 @@ int greem_peak_tflops(greem_ctx *c, int which, double *tflops)
     int err = 0;
     *tflops = peak_tflops(which, c->nsm, c->stream, &err);
     return err;
+}
+
+// ------------------------------------------------------------------ domains and LETs
+static bool boxes_valid(const int32_t *boxes, int ndom)
+{
+    for (int d = 0; d < ndom; d++)
+        for (int a = 0; a < 3; a++) {
+            const int32_t lo = boxes[6 * d + 2 * a], hi = boxes[6 * d + 2 * a + 1];
+            if (lo < 0 || hi > (1 << 21) || lo > hi) return false;
+        }
+    return true;
+}
+
+int greem_cell_index(greem_ctx *c, const double *pos, int64_t N, double L, const int64_t *idx, int64_t n,
+                     int32_t *cells)
+{
+    if (!c || !pos || !cells || N < 1 || N >= (int64_t)0x7FFFFFF0 || n < 0 || n >= (int64_t)0x7FFFFFF0 ||
+        (!idx && n > N) || !(L > 0) || !std::isfinite(L))
+        return GREEM_ERR_INVALID_ARG;
+    if (n == 0) return GREEM_OK;
+    int rc;
+    if ((rc = ensure(c, c->st, 1))) return rc;
+    greem_params p;
+    greem_params_default(&p);
+    p.L = L;
+    p.r_cut = 0.25 * L;
+    BoxPar bp;
+    if ((rc = derive_box(p, 0, 0, bp, false))) return rc;
+    greem::g_launches = 0;
+    cudaStream_t s = c->stream;
+    if (!cuda_ok(cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s))) return GREEM_ERR_CUDA;
+    launch_cells(pos, (uint32_t)N, idx, (uint32_t)n, L, bp.pow2_e, cells, c->st.p, s);
+    unsigned flags = 0;
+    if (!cuda_ok(cudaGetLastError()) ||
+        !cuda_ok(cudaMemcpyAsync(&flags, &c->st.p->flags, sizeof(flags), cudaMemcpyDeviceToHost, s)) ||
+        !cuda_ok(cudaStreamSynchronize(s)))
+        return GREEM_ERR_CUDA;
+    c->stats.kernel_launches = greem::g_launches;
+    return (flags & ST_NONFINITE) ? GREEM_ERR_INVALID_ARG : GREEM_OK;
+}
+
+int greem_domain_pack(greem_ctx *c, const double *pos, const float *mass, const int64_t *ids, int64_t N, double L,
+                      const int32_t *boxes, int ndom, int64_t *counts, double *pos_out, float *mass_out,
+                      int64_t *ids_out)
+{
+    if (!c || !boxes || !counts || ndom < 1 || ndom > kMaxDomains || N < 0 || N >= (int64_t)0x7FFFFFF0 ||
+        !(L > 0) || !std::isfinite(L) || !boxes_valid(boxes, ndom))
+        return GREEM_ERR_INVALID_ARG;
+    for (int d = 0; d < ndom; d++) counts[d] = 0;
+    if (N == 0) return GREEM_OK;
+    if (!pos || !mass || !pos_out || !mass_out || !ids_out) return GREEM_ERR_INVALID_ARG;
+    greem_params p;
+    greem_params_default(&p);
+    p.L = L;
+    p.r_cut = 0.25 * L;
+    BoxPar bp;
+    int rc;
+    if ((rc = derive_box(p, 0, 0, bp, false))) return rc;
+    const uint32_t n = (uint32_t)N, nblk = dom_blocks(n);
+    const size_t ncnt = (size_t)ndom * nblk;
+    if ((rc = ensure(c, c->st, 1)) || (rc = ensure(c, c->dom_boxes, (size_t)ndom * 6)) || (rc = ensure(c, c->dom, n)) ||
+        (rc = ensure(c, c->dom_cnt, ncnt + 1)) || (rc = ensure(c, c->scratch, scan_scratch_elems(ncnt + 1) + 64)))
+        return rc;
+    greem::g_launches = 0;
+    cudaStream_t s = c->stream;
+    if (!cuda_ok(cudaMemsetAsync(c->st.p, 0, sizeof(DevStatus), s)) ||
+        !cuda_ok(cudaMemcpyAsync(c->dom_boxes.p, boxes, sizeof(int32_t) * 6 * ndom, cudaMemcpyHostToDevice, s)))
+        return GREEM_ERR_CUDA;
+    launch_dom_count(pos, n, L, bp.pow2_e, c->dom_boxes.p, ndom, c->dom.p, c->dom_cnt.p, c->st.p, s);
+    scan_u32(c->dom_cnt.p, c->dom_cnt.p, ncnt, c->scratch.p, s);
+    launch_dom_scatter(pos, mass, ids, n, L, c->dom.p, c->dom_cnt.p, ndom, pos_out, mass_out, ids_out, s);
+    std::vector<uint32_t> off(ncnt + 1);
+    unsigned flags = 0;
+    if (!cuda_ok(cudaGetLastError()) ||
+        !cuda_ok(cudaMemcpyAsync(off.data(), c->dom_cnt.p, sizeof(uint32_t) * (ncnt + 1), cudaMemcpyDeviceToHost, s)) ||
+        !cuda_ok(cudaMemcpyAsync(&flags, &c->st.p->flags, sizeof(flags), cudaMemcpyDeviceToHost, s)) ||
+        !cuda_ok(cudaStreamSynchronize(s)))
+        return GREEM_ERR_CUDA;
+    c->stats.kernel_launches = greem::g_launches;
+    if (flags & ST_NONFINITE) return GREEM_ERR_INVALID_ARG;
+    for (int d = 0; d < ndom; d++) counts[d] = (int64_t)off[(size_t)(d + 1) * nblk] - (int64_t)off[(size_t)d * nblk];
+    return GREEM_OK;
+}
+
+int greem_let_export(greem_ctx *c, const int32_t *boxes, int ndom, int self, int64_t *counts, double *pos_out,
+                     float *mass_out, int64_t *ref_out, int64_t cap, int64_t *total)
+{
+    if (!c || !boxes || !counts || !total || ndom < 1 || ndom > kMaxDomains || self >= ndom || cap < 0 ||
+        !boxes_valid(boxes, ndom))
+        return GREEM_ERR_INVALID_ARG;
+    *total = 0;
+    if (!c->have_tree || c->last_nbox != 1) return GREEM_ERR_INVALID_ARG;
+    if (cap > 0 && (!pos_out || !mass_out)) return GREEM_ERR_INVALID_ARG;
+    const uint32_t N = c->last_N;
+    const uint32_t ncap = (uint32_t)std::min<size_t>(c->node_cap, 0xFFFFFFF0u);
+    int rc;
+    if ((rc = ensure(c, c->let_flag, ncap)) || (rc = ensure(c, c->let_cnt, (size_t)ncap + 1)) ||
+        (rc = ensure(c, c->scratch, scan_scratch_elems((size_t)ncap + 1) + 64)))
+        return rc;
+    const uint32_t *n_nodes = c->base.p + N;
+    cudaStream_t s = c->stream;
+    greem::g_launches = 0;
+    int64_t run = 0;
+    for (int d = 0; d < ndom; d++) {
+        counts[d] = 0;
+        if (d == self) continue;
+        LetBox b;
+        for (int a = 0; a < 3; a++) {
+            const long long lo = boxes[6 * d + 2 * a], hi = boxes[6 * d + 2 * a + 1];
+            b.c[a] = lo + hi;  // [2 lo, 2 hi) in u
+            b.h[a] = hi - lo;
+        }
+        if (b.h[0] == 0 || b.h[1] == 0 || b.h[2] == 0) continue;  // an empty domain imports nothing
+        launch_let_count(c->nodes.p, n_nodes, ncap, b, c->bps.p, c->pcell.p, c->let_flag.p, c->let_cnt.p, s, c->nsm);
+        scan_u32(c->let_cnt.p, c->let_cnt.p, ncap, c->scratch.p, s);
+        uint32_t tot = 0;
+        if (!cuda_ok(cudaGetLastError()) ||
+            !cuda_ok(cudaMemcpyAsync(&tot, c->let_cnt.p + ncap, sizeof(tot), cudaMemcpyDeviceToHost, s)) ||
+            !cuda_ok(cudaStreamSynchronize(s)))
+            return GREEM_ERR_CUDA;
+        counts[d] = tot;
+        if (run + (int64_t)tot <= cap && tot)
+            launch_let_fill(c->nodes.p, n_nodes, ncap, b, c->bps.p, c->pcell.p, c->let_flag.p, c->let_cnt.p, c->xs.p,
+                            c->ys.p, c->zs.p, c->ms.p, c->mom64.p, pos_out, mass_out, ref_out,
+                            (unsigned long long)run, s, c->nsm);
+        run += tot;
+    }
+    *total = run;
+    if (!cuda_ok(cudaGetLastError()) || !cuda_ok(cudaStreamSynchronize(s))) return GREEM_ERR_CUDA;
+    c->stats.kernel_launches = greem::g_launches;
+    return run > cap ? GREEM_ERR_CAPACITY : GREEM_OK;
 }
 
 int greem_debug_set(greem_ctx *c, int what, int64_t value)

@@ -280,6 +280,29 @@ void launch_pair_setup(const double *xg, const double *xi, const double *xj, con
                        uint32_t *llen, uint32_t *lraw, uint32_t *perm, uint32_t *n_groups, cudaStream_t s);
 double peak_tflops(int which, int nsm, cudaStream_t s, int *err);
 
+// Domains and local essential trees (domain.cu)
+struct LetBox {
+    long long c[3];  // centre of a domain box, units u = L/2^22
+    long long h[3];  // half sides, units u
+};
+constexpr int kMaxDomains = 1024;
+void launch_cells(const double *pos, uint32_t npos, const int64_t *idx, uint32_t n, double L, int pow2_e,
+                  int32_t *cells, DevStatus *st, cudaStream_t s);
+size_t dom_count_smem(int ndom);
+size_t dom_scatter_smem(int ndom);
+uint32_t dom_blocks(uint32_t N);
+void launch_dom_count(const double *pos, uint32_t N, double L, int pow2_e, const int32_t *boxes, int ndom,
+                      uint32_t *dom, uint32_t *cnt, DevStatus *st, cudaStream_t s);
+void launch_dom_scatter(const double *pos, const float *mass, const int64_t *ids, uint32_t N, double L,
+                        const uint32_t *dom, const uint32_t *off, int ndom, double *pos_out, float *mass_out,
+                        int64_t *ids_out, cudaStream_t s);
+void launch_let_count(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox &b, const BoxPar *bps,
+                      const unsigned long long *pcell, uint8_t *flag, uint32_t *cnt, cudaStream_t s, int nsm);
+void launch_let_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox &b, const BoxPar *bps,
+                     const unsigned long long *pcell, const uint8_t *flag, const uint32_t *off, const double *xs,
+                     const double *ys, const double *zs, const float *ms, const Dbl4 *mom64, double *pos_out,
+                     float *mass_out, int64_t *ref_out, unsigned long long base, cudaStream_t s, int nsm);
+
 // PM (pm.cu)
 void launch_pm_table(int n, double L, double r_cut, int scheme, float *table, cudaStream_t s, int nsm);
 

@@ -105,6 +105,12 @@ def _lib():
             L.greem_softening.restype = dbl
             L.greem_cosmo_factors.argtypes = [dbl, dbl, dbl, dbl, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
             L.greem_debug_set.argtypes = [vp, i32, i64]
+            L.greem_sample_count.argtypes = [i64, i64, i32, dbl, dbl, dbl, dbl]
+            L.greem_sample_count.restype = i64
+            L.greem_domain_boxes.argtypes = [vp, i64, i32, i32, i32, vp]
+            L.greem_cell_index.argtypes = [vp, vp, i64, dbl, vp, i64, vp]
+            L.greem_domain_pack.argtypes = [vp, vp, vp, vp, i64, dbl, vp, i32, vp, vp, vp, vp]
+            L.greem_let_export.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
             L.greem_debug_dump_group_entries.argtypes = [vp, vp, i64, vp, vp, vp, i64, ctypes.POINTER(i64)]
             L.greem_strerror.argtypes = [i32]
             L.greem_strerror.restype = ctypes.c_char_p
@@ -113,7 +119,8 @@ def _lib():
                       "greem_get_stats", "greem_debug_dump", "greem_autotune", "greem_pair_force_f32",
                       "greem_peak_tflops", "greem_debug_dump_group_lists", "greem_kick", "greem_drift",
                       "greem_timestep", "greem_cosmo_factors", "greem_debug_set",
-                      "greem_debug_dump_group_entries"):
+                      "greem_debug_dump_group_entries", "greem_domain_boxes", "greem_cell_index",
+                      "greem_domain_pack", "greem_let_export"):
                 getattr(L, f).restype = i32
             _L = L
     return _L
@@ -330,6 +337,62 @@ class Context:
         _check(_lib().greem_peak_tflops(self._h, int(which), ctypes.byref(v)), "greem_peak_tflops")
         return v.value
 
+    def cell_index(self, pos, L: float, idx=None):
+        """greem_cell_index: finest cells (int32 [n,3], device) of pos[idx] (or of all of pos)."""
+        import torch
+        N = pos.shape[0]
+        n = N if idx is None else idx.shape[0]
+        cells = torch.empty((n, 3), dtype=torch.int32, device=pos.device)
+        if n == 0:
+            return cells
+        _check(_lib().greem_cell_index(self._h, _dev(pos, torch.float64, (N, 3), "pos"), N, float(L),
+                                       None if idx is None else _dev(idx, torch.int64, (n,), "idx"), n,
+                                       _dev(cells, torch.int32, (n, 3), "cells")), "greem_cell_index")
+        return cells
+
+    def domain_pack(self, pos, mass, ids, L: float, boxes):
+        """greem_domain_pack: (pos, mass, ids, counts) packed by destination domain."""
+        import torch
+        N = pos.shape[0]
+        b = np.ascontiguousarray(boxes, dtype=np.int32)
+        counts = np.zeros(b.shape[0], np.int64)
+        po = torch.empty((N, 3), dtype=torch.float64, device=pos.device)
+        mo = torch.empty((N,), dtype=torch.float32, device=pos.device)
+        io = torch.empty((N,), dtype=torch.int64, device=pos.device)
+        if N:
+            _check(_lib().greem_domain_pack(self._h, _dev(pos, torch.float64, (N, 3), "pos"),
+                                            _dev(mass, torch.float32, (N,), "mass"),
+                                            None if ids is None else _dev(ids, torch.int64, (N,), "ids"), N,
+                                            float(L), b.ctypes.data_as(ctypes.c_void_p), b.shape[0],
+                                            counts.ctypes.data_as(ctypes.c_void_p), _dev(po, torch.float64),
+                                            _dev(mo, torch.float32), _dev(io, torch.int64)), "greem_domain_pack")
+        return po, mo, io, counts
+
+    def let_export(self, boxes, self_index: int, with_refs: bool = False):
+        """greem_let_export on the last tree: (pos [n,3] f64, mass [n] f32, refs [n] i64 or
+        None, counts [ndom]) of the items for every other domain, packed by domain."""
+        import torch
+        b = np.ascontiguousarray(boxes, dtype=np.int32)
+        counts = np.zeros(b.shape[0], np.int64)
+        tot = ctypes.c_int64()
+        vp = ctypes.c_void_p
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cap = getattr(self, "_let_cap", 0)
+        while True:
+            po = torch.empty((max(cap, 1), 3), dtype=torch.float64, device=dev)
+            mo = torch.empty((max(cap, 1),), dtype=torch.float32, device=dev)
+            ro = torch.empty((max(cap, 1),), dtype=torch.int64, device=dev) if with_refs else None
+            rc = _lib().greem_let_export(self._h, b.ctypes.data_as(vp), b.shape[0], int(self_index),
+                                         counts.ctypes.data_as(vp), vp(po.data_ptr()), vp(mo.data_ptr()),
+                                         None if ro is None else vp(ro.data_ptr()), cap, ctypes.byref(tot))
+            if rc == ERR_CAPACITY and tot.value > cap:
+                cap = int(tot.value * 1.25) + 1024
+                self._let_cap = cap
+                continue
+            _check(rc, "greem_let_export")
+            n = tot.value
+            return po[:n], mo[:n], (None if ro is None else ro[:n]), counts
+
     def debug_set(self, what: int, value: int):
         """greem_debug_set: failure-path controls (DEBUG_* constants)."""
         _check(_lib().greem_debug_set(self._h, int(what), int(value)), "greem_debug_set")
@@ -412,6 +475,27 @@ def short_force(pos, mass, L: float, r_cut: float, theta: float, n_crit: int, ac
                                     N, float(L), float(r_cut), float(theta), int(n_crit),
                                     _dev(acc, torch.float32, (N, 3), "acc")), "greem_short_force")
     return acc
+
+
+def sample_count(n_total: int, n_local: int, nproc: int, rate: float, t_local: float, t_sum: float,
+                 alpha: float) -> int:
+    """greem_sample_count: particles to sample for the decomposition (Eq. 3-5)."""
+    n = _lib().greem_sample_count(int(n_total), int(n_local), int(nproc), float(rate), float(t_local), float(t_sum),
+                                  float(alpha))
+    if n < 0:
+        raise GreemError(ERR_INVALID_ARG, "greem_sample_count")
+    return int(n)
+
+
+def domain_boxes(cells, grid) -> np.ndarray:
+    """greem_domain_boxes: recursive multisection of the sampled cells (int [n,3]) into
+    px*py*pz boxes (int32 [p,6])."""
+    c = np.ascontiguousarray(cells, dtype=np.int32).reshape(-1, 3)
+    px, py, pz = (int(g) for g in grid)
+    out = np.zeros((px * py * pz, 6), np.int32)
+    _check(_lib().greem_domain_boxes(c.ctypes.data_as(ctypes.c_void_p), c.shape[0], px, py, pz,
+                                     out.ctypes.data_as(ctypes.c_void_p)), "greem_domain_boxes")
+    return out
 
 
 def softening(eps_fin: float, z_crit: float, z: float) -> float:

@@ -685,3 +685,75 @@ def test_second_moments_of_a_point_symmetric_cloud_in_closed_form():
     want = 2 * 0.25 * (np.outer(v1, v1) + np.outer(v2, v2))
     assert np.array_equal(_qmat(Q[0]), want)
     assert Q[0, 3] == 2 * 0.25 * a * b and Q[0, 4] == 0.0 and Q[0, 5] == 2 * 0.25 * g * h
+
+
+# --------------------------------------------------------------------------- local essential trees
+def _img_gap2(lo_a, hi_a, lo_b, hi_b, P):
+    """Squared distance between boxes [lo_a, hi_a] and [lo_b, hi_b] (per-axis closed
+    intervals) in a periodic box of side P: the smallest over the 27 images of b."""
+    best = None
+    for sx in (-P, 0, P):
+        for sy in (-P, 0, P):
+            for sz in (-P, 0, P):
+                s = np.array([sx, sy, sz])
+                g = np.maximum(0, np.maximum(lo_b + s - hi_a, lo_a - (hi_b + s)))
+                v = float(np.sum(g.astype(np.float64) ** 2))
+                best = v if best is None else min(best, v)
+    return best
+
+
+LET_BOX = np.array([300000, 1300000, 0, 2097152, 900000, 1700000], np.int32)
+
+
+def test_let_at_theta_zero_is_every_particle_whose_cell_lies_within_rcut():
+    """theta = 0 accepts no node, so the LET must be exactly the particles whose finest
+    cell lies within r_cut of the box (distance taken over the periodic images)."""
+    pos, m = _clustered(2500, 61)
+    L, rc = 1.0, 0.11
+    T = oracle.Tree(pos, m, L, rc, n_crit=32)
+    kind, idx = T.let_export(LET_BOX, 0.0)
+    assert np.all(kind == 0) and np.all(np.diff(idx) > 0)
+    _, _, xyz, _ = T.sorted()
+    f = L / 2 ** 21
+    blo, bhi = LET_BOX[0::2] * f, LET_BOX[1::2] * f
+    want = []
+    for j in range(len(xyz)):
+        c = np.array([oracle.cell_index(x, L) for x in xyz[j]])
+        if _img_gap2(c * f, (c + 1) * f, blo, bhi, L) <= rc * rc:
+            want.append(j)
+    assert np.array_equal(idx, np.array(want))
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.8])
+def test_let_covers_every_particle_within_rcut_once_and_accepts_by_the_criterion(theta):
+    pos, m = _clustered(2500, 62)
+    L, rc = 1.0, 0.2
+    T = oracle.Tree(pos, m, L, rc, n_crit=32)
+    kind, idx = T.let_export(LET_BOX, theta)
+    assert (kind == 1).sum() > 10 and (kind == 0).sum() > 10
+    nodes = T.nodes()
+    _, _, xyz, _ = T.sorted()
+    cover = np.zeros(len(xyz), np.int64)
+    f = L / 2 ** 21
+    blo, bhi = LET_BOX[0::2] * f, LET_BOX[1::2] * f
+    for k, i in zip(kind, idx):
+        if k == 0:
+            cover[i] += 1
+            continue
+        lvl = nodes[i, 0]
+        side = L / 2 ** lvl
+        lo = nodes[i, 1:4] * side
+        centre = lo + side / 2
+        d2 = _img_gap2(centre, centre, blo, bhi, L)
+        assert side * side < theta * theta * d2 * (1 + 1e-12)       # accepted by the criterion
+        assert _img_gap2(lo, lo + side, blo, bhi, L) <= rc * rc     # not beyond r_cut
+        cover[nodes[i, 4]:nodes[i, 5]] += 1
+    assert cover.max() <= 1                                          # disjoint
+    near = np.array([_img_gap2(p, p, blo, bhi, L) <= rc * rc for p in xyz])
+    assert np.all(cover[near] == 1)                                  # complete within r_cut
+    # no accepted node has an accepted ancestor: ancestors were opened
+    acc_nodes = set(idx[kind == 1].tolist())
+    for i in acc_nodes:
+        for a in acc_nodes:
+            if a != i:
+                assert not (nodes[a, 4] <= nodes[i, 4] and nodes[i, 5] <= nodes[a, 5] and a < i)
