@@ -10,6 +10,11 @@ The e2e figure runs the same steps through greem_short_force_host: each step cop
 inputs in from pinned host memory and its result out, the copies overlapping the
 neighbouring steps' computation.
 
+With N > 1 processes (torchrun) the same box is split over them as the paper does it
+(recursive multisection from sampled particles, local essential trees exchanged by one
+all-to-all-v per step; paper_0910_0121_gb300/domain.py): strong scaling, each step timed
+on every process and the slowest taken.
+
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (on the host
 cores, on a bounded sample of the same workload).
 """
@@ -51,6 +56,8 @@ def parse():
                     help="time the 512^3 full TreePM step (PP + TSC PM on 512^3) in one CUDA graph instead")
     ap.add_argument("--no-config5", action="store_true",
                     help="leave the 512^3 TreePM graph out of the default line's extras")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="N > 1: the collective backend of the domain exchange (gloo stages through the host)")
     ap.add_argument("--no-direct", action="store_true",
                     help="leave out the tree-against-direct error (oracle direct sums for sampled particles)")
     ap.add_argument("--quad", action="store_true",
@@ -518,6 +525,152 @@ def config5_leg(args):
         torch.cuda.empty_cache()
 
 
+def domain_grid(p: int):
+    """px, py, pz with px*py*pz = p, as even as the factors allow (largest factor to the
+    axis with the fewest cuts so far)."""
+    fac, n, q = [], p, 2
+    while n > 1:
+        while n % q == 0:
+            fac.append(q)
+            n //= q
+        q += 1
+    g = [1, 1, 1]
+    for f in sorted(fac, reverse=True):
+        g[g.index(min(g))] *= f
+    return tuple(sorted(g, reverse=True))
+
+
+class CountingCompute:
+    """domain.GpuCompute that adds up the kernel launches of every library call."""
+
+    def __init__(self, ctx):
+        from paper_0910_0121_gb300 import domain
+        self.inner = domain.GpuCompute(ctx)
+        self.ctx = ctx
+        self.launches = 0
+
+    def _count(self, out):
+        self.launches += self.ctx.stats()["kernel_launches"]
+        return out
+
+    def cells(self, *a):
+        return self._count(self.inner.cells(*a))
+
+    def pack(self, *a):
+        return self._count(self.inner.pack(*a))
+
+    def let_export(self, pos, mass, prm, boxes, self_index):
+        from paper_0910_0121_gb300 import greem
+        self.ctx.build_tree(pos, mass, greem.params(**prm))
+        self.launches += self.ctx.stats()["kernel_launches"]
+        po, mo, _, counts = self.ctx.let_export(boxes, self_index)
+        self.launches += self.ctx.stats()["kernel_launches"]
+        return po, mo, counts
+
+    def short_force(self, *a):
+        return self._count(self.inner.short_force(*a))
+
+
+def domain_arm(args, rank, world, local):
+    """N > 1: the 256^3 box split over the processes as the paper does it (Sec. 2.2 steps
+    3-5 and 7, Sec. 2.3.1): recursive multisection from sampled particles, first by
+    particle count, then by the measured force times (Eq. 4); each timed step is every
+    process's tree, LET export, LET all-to-all-v and force.  Strong scaling: the whole
+    job is the one box, its time the slowest process's."""
+    import torch
+    import torch.distributed as dist
+    from paper_0910_0121_gb300 import build as _build
+    from paper_0910_0121_gb300 import domain, greem, synth
+
+    _build.build()
+    # NCCL takes one GPU per process; gloo exchanges through the host, so its processes
+    # may share the GPUs there are
+    torch.cuda.set_device(local if args.dist_backend == "nccl" else local % torch.cuda.device_count())
+    local = torch.cuda.current_device()
+    if args.dist_backend == "nccl":
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        comm = domain.TorchComm("cuda")
+    else:
+        dist.init_process_group("gloo")
+        comm = domain.TorchComm("cpu")
+    grid = domain_grid(world)
+    pos, mass, prm = synth.config_zel256()
+    N = len(pos)
+    mine = np.arange(rank, N, world)
+    P = torch.from_numpy(pos[mine].copy()).cuda()
+    M = torch.from_numpy(mass[mine].copy()).cuda()
+    I = torch.from_numpy(mine.astype(np.int64)).cuda()
+    del mine
+    stream = torch.cuda.current_stream()
+    ctx = greem.Context(stream)
+    comp = CountingCompute(ctx)
+    fprm = dict(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=args.n_crit or 192, n_leaf=10,
+                list_chunk=256, block_shape=16)
+    step = domain.DomainStep(comm, comp, fprm, grid, rate=4e-4, alpha=0.2, seed=synth.SEED0)
+    P, M, I = step.decompose(P, M, I, N)       # by particle count
+    step.force(P, M)
+    P, M, I = step.decompose(P, M, I, N)       # by the measured force times (Eq. 4)
+    for _ in range(max(3, args.warmup)):
+        step.force(P, M)
+    torch.cuda.synchronize()
+    comp.launches = 0
+    info = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            acc = step.force(P, M)
+            info.append(dict(step.info))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    launches = comp.launches
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms = max(comm.allgather_float(ms_local))
+    # end to end: each step's particles in from pinned host memory and accelerations out
+    hp, hm = P.cpu().pin_memory(), M.cpu().pin_memory()
+    ha = torch.empty((P.shape[0], 3), dtype=torch.float32).pin_memory()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    f0.record(stream)
+    for _ in range(args.steps):
+        P.copy_(hp, non_blocking=True)
+        M.copy_(hm, non_blocking=True)
+        acc = step.force(P, M)
+        ha.copy_(acc, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max(comm.allgather_float(f0.elapsed_time(f1) / args.steps))
+    per = {k: comm.allgather_float(statistics.mean(x[k] for x in info))
+           for k in ("n_local", "n_import", "force_ms", "let_bytes_sent")}
+    n_local_max = max(per["n_local"])
+    line = {
+        "metric": METRIC, "value": N / (ms * 1e-3), "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "L": 1.0, "r_cut": fprm["r_cut"], "theta": fprm["theta"],
+                   "n_crit": fprm["n_crit"], "n_leaf": 10, "list_chunk": 256, "block_shape": 16,
+                   "l2": "inputs larger than L2, no flush", "parallelism": f"domains {grid[0]}x{grid[1]}x{grid[2]}",
+                   "dist_backend": args.dist_backend},
+        "domains": {"grid": list(grid), "n_local": per["n_local"], "n_import": per["n_import"],
+                    "force_ms": per["force_ms"], "let_bytes_sent": per["let_bytes_sent"],
+                    "load_balance_max_over_mean_force": max(per["force_ms"]) / statistics.mean(per["force_ms"]),
+                    "particles_max_over_mean": n_local_max / (N / world)},
+        "e2e": {"value": N / (ms_e2e * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": N * (24 + 4),
+                "d2h_bytes_per_step": N * 12, "ms_per_step": ms_e2e,
+                "call": "domain.DomainStep.force per process, local particles copied in and out"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def gpu_arm(args, rank, world, local):
     import torch
@@ -624,11 +777,11 @@ def gpu_arm(args, rank, world, local):
 
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "L": 1.0, "r_cut": p.r_cut, "theta": p.theta, "n_crit": p.n_crit,
                    "n_leaf": p.n_leaf, "list_chunk": p.list_chunk, "block_shape": p.block_shape,
-                   "l2": "inputs (470 MB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+                   "l2": "inputs (470 MB) larger than L2, no flush", "parallelism": "domains 1x1x1"},
         "interactions_per_s": world * inter / (ms * 1e-3),
         "N_int": inter / N,
         "force_kernel_ms": fms, "lists_kernel_ms": statistics.mean(lists_ms),
@@ -728,6 +881,8 @@ def main():
         return
     if args.impl == "reference":
         reference_arm(args, rank, world)
+    elif world > 1:
+        domain_arm(args, rank, world, local)
     else:
         gpu_arm(args, rank, world, local)
 
