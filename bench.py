@@ -475,6 +475,72 @@ def config2_leg(ctx, stream, steps=5):
     return out
 
 
+def domains8_leg(P, M, p, stream, nproc=8, seed=91001):
+    """The 256^3 set split into 2x2x2 boxes as the multi-process step does it, emulated on
+    this one GPU: the boxes from a seeded sample (Eq. 3 at R = 4e-4, recursive multisection),
+    the particles packed by box, then per box its tree and LET export for the other boxes
+    and its force over its particles and the items the other boxes sent it, each call timed
+    on the device.  There is no exchange here (the items are sliced on this device); the
+    per-process compute of the split is what is measured.  Also the split accelerations
+    against the one-process ones."""
+    import torch
+    from paper_0910_0121_gb300 import domain, greem
+    N = P.shape[0]
+    grid = domain_grid(nproc)
+    ctx = greem.Context(stream)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    try:
+        prm = dict(L=p.L, r_cut=p.r_cut, theta=p.theta, n_crit=p.n_crit, n_leaf=p.n_leaf, list_chunk=p.list_chunk,
+                   block_shape=p.block_shape)
+        one = ctx.short_force(P, M, greem.params(**prm)).clone()
+        ns = greem.sample_count(N, N, 1, 4e-4, 0.0, 0.0, 0.2)
+        idx = torch.from_numpy(np.sort(np.random.default_rng(seed).choice(N, size=ns, replace=False))).cuda()
+        boxes = greem.domain_boxes(ctx.cell_index(P, p.L, idx).cpu().numpy(), grid)
+        ids = torch.arange(N, dtype=torch.int64, device="cuda")
+        po, mo, io, counts = ctx.domain_pack(P, M, ids, p.L, boxes)
+        off = np.concatenate([[0], np.cumsum(counts)])
+        exports, t_let, t_force, n_imp = [], [], [], []
+        for d in range(nproc):
+            a, b = ev(), ev()
+            a.record(stream)
+            ctx.build_tree(po[off[d]:off[d + 1]], mo[off[d]:off[d + 1]], greem.params(**prm))
+            ip, im, _, c = ctx.let_export(boxes, d)
+            b.record(stream)
+            b.synchronize()
+            t_let.append(a.elapsed_time(b))
+            exports.append((ip.clone(), im.clone(), np.concatenate([[0], np.cumsum(c)])))
+        acc = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+        for d in range(nproc):
+            rp = [e[0][e[2][d]:e[2][d + 1]] for s_, e in enumerate(exports) if s_ != d]
+            rm = [e[1][e[2][d]:e[2][d + 1]] for s_, e in enumerate(exports) if s_ != d]
+            n_imp.append(int(sum(x.shape[0] for x in rp)))
+            allp = torch.cat([po[off[d]:off[d + 1]]] + rp)
+            allm = torch.cat([mo[off[d]:off[d + 1]]] + rm)
+            a, b = ev(), ev()
+            a.record(stream)
+            ad = ctx.short_force(allp, allm, greem.params(**prm))
+            b.record(stream)
+            b.synchronize()
+            t_force.append(a.elapsed_time(b))
+            acc[io[off[d]:off[d + 1]]] = ad[: off[d + 1] - off[d]]
+        torch.cuda.synchronize()
+        split = acc.double().cpu().numpy()
+        ref = one.double().cpu().numpy()
+        n = np.linalg.norm(ref, axis=1)
+        keep = n > 1e-6 * np.median(n)
+        dif = np.linalg.norm(split - ref, axis=1)[keep] / n[keep]
+        per = [a_ + b_ for a_, b_ in zip(t_let, t_force)]
+        return {"grid": list(grid), "samples": ns, "n_local": [int(x) for x in counts], "n_import": n_imp,
+                "let_bytes": [28 * int(e[2][-1]) for e in exports],
+                "tree_and_let_ms": t_let, "force_ms": t_force, "slowest_domain_ms": max(per),
+                "sum_over_domains_ms": sum(per),
+                "split_vs_one_process": {"median": float(np.median(dif)), "p99": float(np.quantile(dif, 0.99)),
+                                         "p999": float(np.quantile(dif, 0.999))},
+                "note": "per-process compute of the 2x2x2 split, run one box after another on one GPU; no exchange"}
+    finally:
+        ctx.close()
+
+
 def config5_leg(args):
     """512^3 Zel'dovich (rms 1 spacing) + 20000 NFW halos, theta = 0.5, r_cut = 3/512: the
     whole TreePM force (short-range tree force plus PM with TSC on 512^3) replayed as one
@@ -811,6 +877,7 @@ def gpu_arm(args, rank, world, local):
         line["tree_vs_direct"] = tree_vs_direct(pos, mass, prm, rows)
     if rank == 0 and not args.no_extras:
         line["extras"]["config2"] = guarded(config2_leg, ctx, stream)
+        line["extras"]["domains8"] = guarded(domains8_leg, P, M, p, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, desc, nth, t_cpu1 = oracle_sample(pos, mass, prm, n_crit=p.n_crit)
         line["cpu_baseline"] = {"value": N / t_cpu, "unit": "particles/s", "cores": nth, "kind": "oracle",
