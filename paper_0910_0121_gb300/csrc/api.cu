@@ -119,8 +119,7 @@ struct greem_ctx {
     // domains and local essential trees
     DBuf<int32_t> dom_boxes;
     DBuf<uint32_t> dom, dom_cnt;
-    DBuf<uint8_t> let_flag;
-    DBuf<uint32_t> let_cnt;
+    DBuf<uint32_t> let_flag, let_cnt, let_ends;
 
     // graph
     cudaGraphExec_t exec = nullptr;
@@ -862,6 +861,7 @@ void greem_destroy(greem_ctx *c)
     release(c->lvl); release(c->bps); release(c->box_off); release(c->small); release(c->st);
     release(c->qlist); release(c->qcnt); release(c->qoff);
     release(c->dom_boxes); release(c->dom); release(c->dom_cnt); release(c->let_flag); release(c->let_cnt);
+    release(c->let_ends);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->bps_host) cudaFreeHost(c->bps_host);
     if (c->box_off_host) cudaFreeHost(c->box_off_host);
@@ -1658,42 +1658,57 @@ int greem_let_export(greem_ctx *c, const int32_t *boxes, int ndom, int self, int
     if (cap > 0 && (!pos_out || !mass_out)) return GREEM_ERR_INVALID_ARG;
     const uint32_t N = c->last_N;
     const uint32_t ncap = (uint32_t)std::min<size_t>(c->node_cap, 0xFFFFFFF0u);
-    int rc;
-    if ((rc = ensure(c, c->let_flag, ncap)) || (rc = ensure(c, c->let_cnt, (size_t)ncap + 1)) ||
-        (rc = ensure(c, c->scratch, scan_scratch_elems((size_t)ncap + 1) + 64)))
-        return rc;
-    const uint32_t *n_nodes = c->base.p + N;
-    cudaStream_t s = c->stream;
-    greem::g_launches = 0;
-    int64_t run = 0;
+    // the receiving boxes: every box but self and the empty ones
+    std::vector<int> recv;
+    std::vector<LetBox> lb;
     for (int d = 0; d < ndom; d++) {
         counts[d] = 0;
-        if (d == self) continue;
         LetBox b;
         for (int a = 0; a < 3; a++) {
             const long long lo = boxes[6 * d + 2 * a], hi = boxes[6 * d + 2 * a + 1];
             b.c[a] = lo + hi;  // [2 lo, 2 hi) in u
             b.h[a] = hi - lo;
         }
-        if (b.h[0] == 0 || b.h[1] == 0 || b.h[2] == 0) continue;  // an empty domain imports nothing
-        launch_let_count(c->nodes.p, n_nodes, ncap, b, c->bps.p, c->pcell.p, c->let_flag.p, c->let_cnt.p, s, c->nsm);
-        scan_u32(c->let_cnt.p, c->let_cnt.p, ncap, c->scratch.p, s);
-        uint32_t tot = 0;
+        if (d == self || b.h[0] == 0 || b.h[1] == 0 || b.h[2] == 0) continue;  // an empty box imports nothing
+        recv.push_back(d);
+        lb.push_back(b);
+    }
+    const int nrecv = (int)recv.size();
+    const int chunk = std::min(nrecv, kLetChunk);
+    const size_t run = (size_t)ncap + 1;
+    int rc;
+    if (chunk > 0 &&
+        ((rc = ensure(c, c->let_flag, ncap)) || (rc = ensure(c, c->let_cnt, run * chunk + 1)) ||
+         (rc = ensure(c, c->let_ends, (size_t)kLetChunk + 1)) ||
+         (rc = ensure(c, c->scratch, scan_scratch_elems(run * chunk + 1) + 64))))
+        return rc;
+    const uint32_t *n_nodes = c->base.p + N;
+    cudaStream_t s = c->stream;
+    greem::g_launches = 0;
+    int64_t run_items = 0;
+    for (int j0 = 0; j0 < nrecv; j0 += kLetChunk) {
+        const int nb = std::min(kLetChunk, nrecv - j0);
+        launch_let_count(c->nodes.p, n_nodes, ncap, lb.data() + j0, nb, c->bps.p, c->pcell.p, c->let_flag.p,
+                         c->let_cnt.p, s, c->nsm);
+        scan_u32(c->let_cnt.p, c->let_cnt.p, run * nb, c->scratch.p, s);
+        launch_let_ends(c->let_cnt.p, ncap, nb, c->let_ends.p, s);
+        uint32_t ends[kLetChunk + 1];
         if (!cuda_ok(cudaGetLastError()) ||
-            !cuda_ok(cudaMemcpyAsync(&tot, c->let_cnt.p + ncap, sizeof(tot), cudaMemcpyDeviceToHost, s)) ||
+            !cuda_ok(cudaMemcpyAsync(ends, c->let_ends.p, sizeof(uint32_t) * (nb + 1), cudaMemcpyDeviceToHost, s)) ||
             !cuda_ok(cudaStreamSynchronize(s)))
             return GREEM_ERR_CUDA;
-        counts[d] = tot;
-        if (run + (int64_t)tot <= cap && tot)
-            launch_let_fill(c->nodes.p, n_nodes, ncap, b, c->bps.p, c->pcell.p, c->let_flag.p, c->let_cnt.p, c->xs.p,
-                            c->ys.p, c->zs.p, c->ms.p, c->mom64.p, pos_out, mass_out, ref_out,
-                            (unsigned long long)run, s, c->nsm);
-        run += tot;
+        for (int j = 0; j < nb; j++) counts[recv[j0 + j]] = (int64_t)ends[j + 1] - (int64_t)ends[j];
+        const int64_t tot = ends[nb];
+        if (run_items + tot <= cap && tot)
+            launch_let_fill(c->nodes.p, n_nodes, ncap, lb.data() + j0, nb, c->bps.p, c->pcell.p, c->let_flag.p,
+                            c->let_cnt.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->mom64.p, pos_out, mass_out, ref_out,
+                            (unsigned long long)run_items, s, c->nsm);
+        run_items += tot;
     }
-    *total = run;
+    *total = run_items;
     if (!cuda_ok(cudaGetLastError()) || !cuda_ok(cudaStreamSynchronize(s))) return GREEM_ERR_CUDA;
     c->stats.kernel_launches = greem::g_launches;
-    return run > cap ? GREEM_ERR_CAPACITY : GREEM_OK;
+    return run_items > cap ? GREEM_ERR_CAPACITY : GREEM_OK;
 }
 
 int greem_debug_set(greem_ctx *c, int what, int64_t value)

@@ -286,6 +286,7 @@ struct LetBox {
     long long h[3];  // half sides, units u
 };
 constexpr int kMaxDomains = 1024;
+constexpr int kLetChunk = 16;  // receiving boxes handled by one set of LET passes
 void launch_cells(const double *pos, uint32_t npos, const int64_t *idx, uint32_t n, double L, int pow2_e,
                   int32_t *cells, DevStatus *st, cudaStream_t s);
 size_t dom_count_smem(int ndom);
@@ -296,12 +297,15 @@ void launch_dom_count(const double *pos, uint32_t N, double L, int pow2_e, const
 void launch_dom_scatter(const double *pos, const float *mass, const int64_t *ids, uint32_t N, double L,
                         const uint32_t *dom, const uint32_t *off, int ndom, double *pos_out, float *mass_out,
                         int64_t *ids_out, cudaStream_t s);
-void launch_let_count(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox &b, const BoxPar *bps,
-                      const unsigned long long *pcell, uint8_t *flag, uint32_t *cnt, cudaStream_t s, int nsm);
-void launch_let_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox &b, const BoxPar *bps,
-                     const unsigned long long *pcell, const uint8_t *flag, const uint32_t *off, const double *xs,
-                     const double *ys, const double *zs, const float *ms, const Dbl4 *mom64, double *pos_out,
-                     float *mass_out, int64_t *ref_out, unsigned long long base, cudaStream_t s, int nsm);
+void launch_let_count(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox *b, int nb,
+                      const BoxPar *bps, const unsigned long long *pcell, uint32_t *flag, uint32_t *cnt, cudaStream_t s,
+                      int nsm);
+void launch_let_ends(const uint32_t *off, uint32_t ncap, int nb, uint32_t *ends, cudaStream_t s);
+void launch_let_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox *b, int nb,
+                     const BoxPar *bps, const unsigned long long *pcell, const uint32_t *flag, const uint32_t *off,
+                     const double *xs, const double *ys, const double *zs, const float *ms, const Dbl4 *mom64,
+                     double *pos_out, float *mass_out, int64_t *ref_out, unsigned long long base, cudaStream_t s,
+                     int nsm);
 
 // PM (pm.cu)
 void launch_pm_table(int n, double L, double r_cut, int scheme, float *table, cudaStream_t s, int nsm);

@@ -209,50 +209,75 @@ __device__ __forceinline__ bool let_particle_in(unsigned long long pc, const Let
     return let_gap2(b, 2 * fx + 1, 2 * fy + 1, 2 * fz + 1, 1) <= bp.T_prune;
 }
 
+// Up to kLetChunk receiving boxes are handled by one set of passes: a node's status for
+// box j sits in bits 2j..2j+1 of its flag word.
+struct LetBoxes {
+    LetBox b[kLetChunk];
+    int n;
+};
+
 __global__ void __launch_bounds__(256) k_let_flags(const Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
-                                                   uint32_t ncap, LetBox b, const BoxPar *__restrict__ bps,
-                                                   uint8_t *__restrict__ flag)
+                                                   uint32_t ncap, LetBoxes bx, const BoxPar *__restrict__ bps,
+                                                   uint32_t *__restrict__ flag)
 {
     const uint32_t nn = min(*n_nodes, ncap);
     const BoxPar &bp = bps[0];
-    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x)
-        flag[n] = let_status(nodes[n], b, bp);
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
+        const Node nd = nodes[n];
+        uint32_t f = 0;
+        for (int j = 0; j < bx.n; j++) f |= (uint32_t)let_status(nd, bx.b[j], bp) << (2 * j);
+        flag[n] = f;
+    }
 }
 
-// Items each node contributes: 1 for an accepted node, the particles within r_cut for an
-// opened leaf, 0 otherwise or when an ancestor was not opened.  cnt covers [0, ncap).
+// Boxes (bit j) whose status in the flag word is "opened" (2).
+__device__ __forceinline__ uint32_t opened_boxes(uint32_t f, int nb)
+{
+    uint32_t m = 0;
+    for (int j = 0; j < nb; j++) m |= (((f >> (2 * j)) & 3u) == 2u ? 1u : 0u) << j;
+    return m;
+}
+
+// Items each node contributes to each box, box-major: cnt[j * (ncap + 1) + n].  A node is
+// visited for box j when every ancestor was opened for j; then it contributes 1 if it was
+// accepted, its particles within r_cut if it is an opened leaf, 0 otherwise.  Entries at
+// n >= n_nodes and the last entry of each box's run are 0, so one scan over the whole array
+// gives every item its final place, the boxes packed in order.
 __global__ void __launch_bounds__(256) k_let_count(const Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
-                                                   uint32_t ncap, const uint8_t *__restrict__ flag,
-                                                   const unsigned long long *__restrict__ pcell, LetBox b,
+                                                   uint32_t ncap, const uint32_t *__restrict__ flag,
+                                                   const unsigned long long *__restrict__ pcell, LetBoxes bx,
                                                    const BoxPar *__restrict__ bps, uint32_t *__restrict__ cnt)
 {
     const uint32_t nn = min(*n_nodes, ncap);
     const BoxPar &bp = bps[0];
-    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < ncap; n += gridDim.x * blockDim.x) {
-        uint32_t c = 0;
-        const uint8_t f = n < nn ? flag[n] : 0;
-        if (f != 0) {
-            const Node nd = nodes[n];
-            bool visited = true;
-            for (uint32_t q = nd.parent; q != kNone; q = nodes[q].parent)
-                if (flag[q] != 2) {
-                    visited = false;
-                    break;
-                }
-            if (visited) {
-                if (f == 1) c = 1;
-                else if (nd.lvl & 256u)
-                    for (uint32_t j = nd.begin; j < nd.end; j++) c += let_particle_in(pcell[j], b, bp) ? 1u : 0u;
-            }
+    const size_t run = (size_t)ncap + 1;
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n <= ncap; n += gridDim.x * blockDim.x) {
+        uint32_t vis = 0;
+        Node nd;
+        uint32_t f = 0;
+        if (n < nn) {
+            nd = nodes[n];
+            f = flag[n];
+            vis = (bx.n >= 32 ? 0xffffffffu : ((1u << bx.n) - 1u));
+            for (uint32_t q = nd.parent; q != kNone && vis; q = nodes[q].parent) vis &= opened_boxes(flag[q], bx.n);
         }
-        cnt[n] = c;
+        for (int j = 0; j < bx.n; j++) {
+            uint32_t c = 0;
+            if ((vis >> j) & 1u) {
+                const uint32_t s = (f >> (2 * j)) & 3u;
+                if (s == 1u) c = 1;
+                else if (s == 2u && (nd.lvl & 256u))
+                    for (uint32_t i = nd.begin; i < nd.end; i++) c += let_particle_in(pcell[i], bx.b[j], bp) ? 1u : 0u;
+            }
+            cnt[(size_t)j * run + n] = c;
+        }
     }
 }
 
 __global__ void __launch_bounds__(256) k_let_fill(const Node *__restrict__ nodes, const uint32_t *__restrict__ n_nodes,
-                                                  uint32_t ncap, const uint8_t *__restrict__ flag,
+                                                  uint32_t ncap, const uint32_t *__restrict__ flag,
                                                   const uint32_t *__restrict__ off,
-                                                  const unsigned long long *__restrict__ pcell, LetBox b,
+                                                  const unsigned long long *__restrict__ pcell, LetBoxes bx,
                                                   const BoxPar *__restrict__ bps, const double *__restrict__ xs,
                                                   const double *__restrict__ ys, const double *__restrict__ zs,
                                                   const float *__restrict__ ms, const Dbl4 *__restrict__ mom64,
@@ -261,47 +286,72 @@ __global__ void __launch_bounds__(256) k_let_fill(const Node *__restrict__ nodes
 {
     const uint32_t nn = min(*n_nodes, ncap);
     const BoxPar &bp = bps[0];
+    const size_t run = (size_t)ncap + 1;
     for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
-        const uint32_t c = off[n + 1] - off[n];
-        if (c == 0) continue;
-        unsigned long long o = base + off[n];
-        if (flag[n] == 1) {
-            const Dbl4 m = mom64[n];
-            pos_out[3 * o] = m.x;
-            pos_out[3 * o + 1] = m.y;
-            pos_out[3 * o + 2] = m.z;
-            mass_out[o] = (float)m.w;
-            if (ref_out) ref_out[o] = -1 - (int64_t)n;
-            continue;
-        }
-        const Node nd = nodes[n];
-        for (uint32_t j = nd.begin; j < nd.end; j++) {
-            if (!let_particle_in(pcell[j], b, bp)) continue;
-            pos_out[3 * o] = xs[j];
-            pos_out[3 * o + 1] = ys[j];
-            pos_out[3 * o + 2] = zs[j];
-            mass_out[o] = ms[j];
-            if (ref_out) ref_out[o] = (int64_t)j;
-            o++;
+        for (int j = 0; j < bx.n; j++) {
+            const size_t k = (size_t)j * run + n;
+            const uint32_t c = off[k + 1] - off[k];
+            if (c == 0) continue;
+            unsigned long long o = base + off[k];
+            if (((flag[n] >> (2 * j)) & 3u) == 1u) {
+                const Dbl4 m = mom64[n];
+                pos_out[3 * o] = m.x;
+                pos_out[3 * o + 1] = m.y;
+                pos_out[3 * o + 2] = m.z;
+                mass_out[o] = (float)m.w;
+                if (ref_out) ref_out[o] = -1 - (int64_t)n;
+                continue;
+            }
+            const Node nd = nodes[n];
+            for (uint32_t i = nd.begin; i < nd.end; i++) {
+                if (!let_particle_in(pcell[i], bx.b[j], bp)) continue;
+                pos_out[3 * o] = xs[i];
+                pos_out[3 * o + 1] = ys[i];
+                pos_out[3 * o + 2] = zs[i];
+                mass_out[o] = ms[i];
+                if (ref_out) ref_out[o] = (int64_t)i;
+                o++;
+            }
         }
     }
 }
 
-void launch_let_count(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox &b, const BoxPar *bps,
-                      const unsigned long long *pcell, uint8_t *flag, uint32_t *cnt, cudaStream_t s, int nsm)
+// The offsets at the ends of the boxes' runs: ends[j] = off[(j + 1) * (ncap + 1) - 1 + 1].
+__global__ void k_let_ends(const uint32_t *__restrict__ off, uint32_t ncap, int nb, uint32_t *__restrict__ ends)
 {
-    k_let_flags<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, ncap, b, bps, flag);
-    k_let_count<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, ncap, flag, pcell, b, bps, cnt);
+    const int j = threadIdx.x;
+    if (j <= nb) ends[j] = off[(size_t)j * ((size_t)ncap + 1)];
+}
+
+void launch_let_count(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox *b, int nb,
+                      const BoxPar *bps, const unsigned long long *pcell, uint32_t *flag, uint32_t *cnt, cudaStream_t s,
+                      int nsm)
+{
+    LetBoxes bx;
+    bx.n = nb;
+    for (int j = 0; j < nb; j++) bx.b[j] = b[j];
+    k_let_flags<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, ncap, bx, bps, flag);
+    k_let_count<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, ncap, flag, pcell, bx, bps, cnt);
     g_launches += 2;
 }
 
-void launch_let_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox &b, const BoxPar *bps,
-                     const unsigned long long *pcell, const uint8_t *flag, const uint32_t *off, const double *xs,
-                     const double *ys, const double *zs, const float *ms, const Dbl4 *mom64, double *pos_out,
-                     float *mass_out, int64_t *ref_out, unsigned long long base, cudaStream_t s, int nsm)
+void launch_let_ends(const uint32_t *off, uint32_t ncap, int nb, uint32_t *ends, cudaStream_t s)
 {
-    k_let_fill<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, ncap, flag, off, pcell, b, bps, xs, ys, zs, ms, mom64, pos_out,
-                                       mass_out, ref_out, base);
+    k_let_ends<<<1, 32, 0, s>>>(off, ncap, nb, ends);
+    g_launches++;
+}
+
+void launch_let_fill(const Node *nodes, const uint32_t *n_nodes, uint32_t ncap, const LetBox *b, int nb,
+                     const BoxPar *bps, const unsigned long long *pcell, const uint32_t *flag, const uint32_t *off,
+                     const double *xs, const double *ys, const double *zs, const float *ms, const Dbl4 *mom64,
+                     double *pos_out, float *mass_out, int64_t *ref_out, unsigned long long base, cudaStream_t s,
+                     int nsm)
+{
+    LetBoxes bx;
+    bx.n = nb;
+    for (int j = 0; j < nb; j++) bx.b[j] = b[j];
+    k_let_fill<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, ncap, flag, off, pcell, bx, bps, xs, ys, zs, ms, mom64,
+                                       pos_out, mass_out, ref_out, base);
     g_launches++;
 }
 
