@@ -53,6 +53,7 @@ struct greem_ctx {
     DBuf<uint64_t> k0, k1;
     DBuf<uint32_t> v0, v1, hist, scratch;
     DBuf<unsigned long long> rs_status;
+    DBuf<uint32_t> rs_runs;
     DBuf<double> xs, ys, zs;
     DBuf<float> ms;
     // S3-S4
@@ -387,6 +388,7 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
     ENS(v1, N);
     ENS(hist, radix_hist_elems((uint32_t)N));
     ENS(rs_status, radix_status_elems((uint32_t)N));
+    ENS(rs_runs, radix_runs_elems((uint32_t)N));
     const size_t big = std::max<size_t>(N + 1, c->node_cap + 1);
     ENS(scratch, scan_scratch_elems(big) + 64);
     ENS(xs, N);
@@ -517,8 +519,8 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     const int box_passes = nbox <= 1 ? 0 : (nbox <= 256 ? 1 : 2);
     uint64_t *ks = nullptr;
     uint32_t *perm = nullptr;
-    radix_sort(c->k0.p, c->k1.p, c->v0.p, c->v1.p, N, 8, box_passes, c->box_off.p, nbox, c->hist.p, c->rs_status.p,
-               c->st.p, &ks, &perm, s, nsm);
+    radix_sort(c->k0.p, c->k1.p, c->v0.p, c->v1.p, N, radix_key_passes(), box_passes, c->box_off.p, nbox, c->hist.p,
+               c->rs_status.p, c->rs_runs.p, c->st.p, &ks, &perm, s, nsm);
     launch_gather(r.pos, r.mass, perm, N, c->box_off.p, nbox, c->bps.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->st.p,
                   s);
     ev_record(c, r, ev, 2);
@@ -851,7 +853,7 @@ void greem_destroy(greem_ctx *c)
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     release(c->k0); release(c->k1); release(c->v0); release(c->v1); release(c->hist); release(c->scratch);
-    release(c->rs_status);
+    release(c->rs_status); release(c->rs_runs);
     release(c->xs); release(c->ys); release(c->zs); release(c->ms);
     release(c->d8); release(c->K8); release(c->nchild); release(c->own); release(c->base); release(c->ctr);
     release(c->gflag); release(c->gidx); release(c->nodes); release(c->raw); release(c->mom64); release(c->noff);

@@ -170,9 +170,11 @@ void launch_keys(const double *pos, uint32_t N, const uint32_t *box_off, int nbo
                  uint64_t *keys, DevStatus *st, cudaStream_t s);
 size_t radix_hist_elems(uint32_t n);
 size_t radix_status_elems(uint32_t n);
+size_t radix_runs_elems(uint32_t n);
+int radix_key_passes();
 void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t n, int key_passes, int box_passes,
-                const uint32_t *box_off, int nbox, uint32_t *hist, unsigned long long *status, DevStatus *st,
-                uint64_t **k_out, uint32_t **v_out, cudaStream_t s, int nsm);
+                const uint32_t *box_off, int nbox, uint32_t *hist, unsigned long long *status, uint32_t *runs,
+                DevStatus *st, uint64_t **k_out, uint32_t **v_out, cudaStream_t s, int nsm);
 void launch_gather(const double *pos, const float *mass, const uint32_t *perm, uint32_t N, const uint32_t *box_off,
                    int nbox, const BoxPar *bps, double *xs, double *ys, double *zs, float *ms, DevStatus *st,
                    cudaStream_t s);

@@ -64,7 +64,9 @@ void launch_keys(const double *pos, uint32_t N, const uint32_t *box_off, int nbo
 }
 
 // ------------------------------------------------------------------ radix sort
-// Stable LSD radix sort of (key, index) pairs, 8-bit digits, one kernel per digit in the
+// The sort runs in two phases.  Phase A: a stable LSD radix sort of (key, index) pairs on
+// the key's top 36 bits (its cells down to level 12), five 8-bit digits, one kernel per
+// digit in the
 // single-pass ("onesweep") form of decoupled look-back (Merrill & Garland 2016; Adinets
 // & Merrill 2022): one pass over the keys histograms every digit at once, then each
 // digit pass reads and writes the pairs once.  A block takes the next tile by ticket,
@@ -73,6 +75,14 @@ void launch_keys(const double *pos, uint32_t N, const uint32_t *box_off, int nbo
 // inclusive prefix; the tile is then written out in digit order through shared memory.
 // Tickets make every block wait only on blocks that started before it.  Each wait has an
 // iteration limit, after which the status records a timeout (the call then fails).
+// Phase B: the pairs now form runs of equal top bits (particles that share a level-12
+// cell), each in input order; every run is sorted by its low 27 bits in place, stably.
+// Most runs hold one particle and cost nothing; runs of up to 16 are insertion-sorted by
+// the thread at their head, longer ones by a block (a bitonic sort of (low bits, position
+// in the run), so equal keys keep their order), and runs beyond a block's shared memory
+// by a slower exact one-warp LSD pass over their low bits.  The result is the stable sort
+// by the full 63-bit key, whatever the clustering: phase A leaves equal top bits in input
+// order and phase B orders each run by the rest of the key.
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 #ifndef GREEM_RS_ITEMS
@@ -83,15 +93,26 @@ constexpr int kRsWarps = kRsThreads / 32;
 #endif
 constexpr int kRsItems = GREEM_RS_ITEMS;
 constexpr int kRsTile = kRsThreads * kRsItems;  // pairs per tile
-constexpr int kRsMaxPasses = 10;                // 8 key digits + up to 2 box digits
+constexpr int kRsMaxPasses = 10;                // key digits + up to 2 box digits
+constexpr int kRsLowBits = 27;                  // bits left to phase B: levels 13-21
+constexpr int kRsKeyPasses = 5;                 // 8-bit digits over the top 36 bits
+constexpr int kShortRun = 16;                   // runs sorted by the thread at their head
+constexpr int kRunCap = 8192;                   // runs sorted by a block in shared memory
+constexpr int kRunThreads = 1024;
+constexpr size_t kRunSmem = (size_t)kRunCap * (sizeof(uint64_t) + sizeof(uint32_t));
 constexpr int kRsLook = 8;                      // predecessors loaded at once in the look-back
 constexpr unsigned long long kRsAgg = 1ull << 62, kRsPrefix = 2ull << 62, kRsValue = (1ull << 62) - 1;
 constexpr size_t kRsSmem = (size_t)kRsTile * (sizeof(uint64_t) + sizeof(uint32_t));
 
 static inline uint32_t rs_tiles(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
 
-// u32 words: [passes][256] digit counts, [passes][256] digit starts, [passes] tickets
-size_t radix_hist_elems(uint32_t) { return (size_t)kRsMaxPasses * 512 + kRsMaxPasses; }
+// u32 words: [passes][256] digit counts, [passes][256] digit starts, [passes] tickets, then
+// phase B's count of long runs and its work counter
+size_t radix_hist_elems(uint32_t) { return (size_t)kRsMaxPasses * 512 + kRsMaxPasses + 2; }
+// phase B's list of runs longer than kShortRun: (start, end) pairs
+static inline uint32_t runs_cap(uint32_t n) { return n / (kShortRun + 1) + 64; }
+size_t radix_runs_elems(uint32_t n) { return 2 * (size_t)runs_cap(n); }
+int radix_key_passes() { return kRsKeyPasses; }
 // u64 look-back words: [passes][tiles][256]
 size_t radix_status_elems(uint32_t n) { return (size_t)kRsMaxPasses * rs_tiles(n) * 256; }
 
@@ -122,7 +143,7 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d)
 // every lane adds its own.
 __global__ void __launch_bounds__(256) k_rs_hist_all(const uint64_t *__restrict__ key, uint32_t n, int key_passes,
                                                      int box_passes, const uint32_t *__restrict__ box_off, int nbox,
-                                                     uint32_t *__restrict__ hist)
+                                                     uint32_t *__restrict__ hist, int kshift0)
 {
     __shared__ uint32_t h[kRsMaxPasses][256];
     const int passes = key_passes + box_passes;
@@ -136,7 +157,8 @@ __global__ void __launch_bounds__(256) k_rs_hist_all(const uint64_t *__restrict_
         const uint64_t k = ok ? key[i] : 0ull;
         const uint32_t b = (ok && box_passes) ? (uint32_t)box_of(i, box_off, nbox) : 0u;
         for (int p = 0; p < passes; p++) {
-            const uint32_t d = ok ? (p < key_passes ? (uint32_t)(k >> (8 * p)) & 255u : (b >> (8 * (p - key_passes))) & 255u)
+            const uint32_t d = ok ? (p < key_passes ? (uint32_t)(k >> (kshift0 + 8 * p)) & 255u
+                                                    : (b >> (8 * (p - key_passes))) & 255u)
                                   : 256u;
             const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
             if (__all_sync(0xffffffffu, d == d0)) {
@@ -321,9 +343,202 @@ __global__ void __launch_bounds__(kRsThreads, GREEM_RS_MINB) k_rs_onesweep(const
     }
 }
 
+// ------------------------------------------------------------------ phase B
+__device__ __forceinline__ uint64_t run_top(uint64_t k) { return k >> kRsLowBits; }
+
+// Lanes of the warp whose 9-bit digit equals this lane's (d < 512; d = 512 matches only
+// lanes with d = 512).
+__device__ __forceinline__ unsigned digit9_peers(uint32_t d)
+{
+    unsigned peers = __ballot_sync(0xffffffffu, d >= 512u) ^ (d >= 512u ? 0u : 0xffffffffu);
+#pragma unroll
+    for (int b = 0; b < 9; b++) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bb : ~bb;
+    }
+    return peers;
+}
+
+// Every run head: a run of up to kShortRun pairs is insertion-sorted (stable) by the head's
+// thread in place; a longer one goes to the list for k_runs_long, its end found by binary
+// search (the top bits are sorted within a box).  Other threads only read the top bits of
+// pairs that runs permute among themselves, so the concurrent sorts do not disturb them.
+__global__ void __launch_bounds__(256) k_runs_short(uint64_t *__restrict__ key, uint32_t *__restrict__ val, uint32_t n,
+                                                    const uint32_t *__restrict__ box_off, int nbox,
+                                                    uint32_t *__restrict__ runs, uint32_t run_cap,
+                                                    uint32_t *__restrict__ n_long)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t t = run_top(key[i]);
+        uint32_t e_box = n;
+        bool head = i == 0 || run_top(key[i - 1]) != t;
+        if (nbox > 1) {
+            const int b = box_of(i, box_off, nbox);
+            e_box = box_off[b + 1];
+            if (box_off[b] == i) head = true;
+        }
+        if (!head) continue;
+        uint32_t e = i + 1;
+        while (e < e_box && e - i <= (uint32_t)kShortRun && run_top(key[e]) == t) e++;
+        if (e - i <= (uint32_t)kShortRun) {
+            const uint32_t len = e - i;
+            if (len < 2) continue;
+            uint64_t kk[kShortRun];
+            uint32_t vv[kShortRun];
+            for (uint32_t q = 0; q < len; q++) {
+                kk[q] = key[i + q];
+                vv[q] = val[i + q];
+            }
+            for (uint32_t q = 1; q < len; q++) {
+                const uint64_t x = kk[q];
+                const uint32_t y = vv[q];
+                int r = (int)q - 1;
+                while (r >= 0 && kk[r] > x) {
+                    kk[r + 1] = kk[r];
+                    vv[r + 1] = vv[r];
+                    r--;
+                }
+                kk[r + 1] = x;
+                vv[r + 1] = y;
+            }
+            for (uint32_t q = 0; q < len; q++) {
+                key[i + q] = kk[q];
+                val[i + q] = vv[q];
+            }
+        } else {
+            uint32_t lo = e, hi = e_box;  // the first index from e on whose top differs (or e_box)
+            while (lo < hi) {
+                const uint32_t mid = lo + (hi - lo) / 2;
+                if (run_top(key[mid]) == t) lo = mid + 1;
+                else hi = mid;
+            }
+            const uint32_t slot = atomicAdd(n_long, 1u);
+            if (slot < run_cap) {  // always: a run longer than kShortRun takes more than kShortRun pairs
+                runs[2 * slot] = i;
+                runs[2 * slot + 1] = lo;
+            }
+        }
+    }
+}
+
+// The listed runs, one block each: up to kRunCap pairs by a bitonic sort in shared memory
+// of (low bits << 14 | position in the run), unique keys whose order is the stable one;
+// longer runs by one warp, three stable 9-bit LSD passes over the low 27 bits through the
+// other ping-pong buffer (tkey, tval) at the same positions, then copied back.
+__global__ void __launch_bounds__(kRunThreads) k_runs_long(uint64_t *__restrict__ key, uint32_t *__restrict__ val,
+                                                           uint64_t *__restrict__ tkey, uint32_t *__restrict__ tval,
+                                                           const uint32_t *__restrict__ runs, uint32_t run_cap,
+                                                           const uint32_t *__restrict__ n_long,
+                                                           uint32_t *__restrict__ ctr)
+{
+    extern __shared__ __align__(16) unsigned char run_smem[];
+    uint64_t *comp = reinterpret_cast<uint64_t *>(run_smem);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(run_smem + (size_t)kRunCap * sizeof(uint64_t));
+    __shared__ uint32_t s_r;
+    __shared__ uint64_t s_top;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t nl = min(*n_long, run_cap);
+    const uint64_t lowmask = (1ull << kRsLowBits) - 1ull;
+    for (;;) {
+        if (tid == 0) s_r = atomicAdd(ctr, 1u);
+        __syncthreads();
+        const uint32_t r = s_r;
+        if (r >= nl) break;
+        const uint32_t s = runs[2 * r], e = runs[2 * r + 1], len = e - s;
+        if (len <= (uint32_t)kRunCap) {
+            uint32_t P = 1;
+            while (P < len) P <<= 1;
+            for (uint32_t j = tid; j < P; j += kRunThreads) {
+                if (j < len) {
+                    const uint64_t k = key[s + j];
+                    comp[j] = ((k & lowmask) << 14) | j;
+                    vals[j] = val[s + j];
+                } else {
+                    comp[j] = ~0ull;
+                }
+            }
+            if (tid == 0) s_top = run_top(key[s]);
+            __syncthreads();
+            for (uint32_t k2 = 2; k2 <= P; k2 <<= 1) {
+                for (uint32_t j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+                    for (uint32_t t = tid; t < P; t += kRunThreads) {
+                        const uint32_t u = t ^ j2;
+                        if (u > t) {
+                            const uint64_t a = comp[t], b = comp[u];
+                            const bool asc = (t & k2) == 0;
+                            if ((a > b) == asc) {
+                                comp[t] = b;
+                                comp[u] = a;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (uint32_t j = tid; j < len; j += kRunThreads) {
+                const uint64_t c = comp[j];
+                key[s + j] = (s_top << kRsLowBits) | (c >> 14);
+                val[s + j] = vals[c & 0x3fffu];
+            }
+        } else if (tid < 32) {
+            uint32_t *hist = vals;  // 512 digit starts
+            const unsigned lt = (1u << lane) - 1u;
+            uint64_t *sk = key, *dk = tkey;
+            uint32_t *sv = val, *dv = tval;
+            for (int pass = 0; pass < 3; pass++) {
+                const int shift = 9 * pass;
+                for (int d = lane; d < 512; d += 32) hist[d] = 0;
+                __syncwarp();
+                for (uint32_t j = s + lane; j < e; j += 32) atomicAdd(&hist[(uint32_t)(sk[j] >> shift) & 511u], 1u);
+                __syncwarp();
+                uint32_t carry = s;
+                for (int b = 0; b < 512; b += 32) {
+                    const uint32_t v = hist[b + lane];
+                    uint32_t x = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    hist[b + lane] = carry + x - v;
+                    carry += __shfl_sync(0xffffffffu, x, 31);
+                }
+                __syncwarp();
+                for (uint32_t c0 = s; c0 < e; c0 += 32) {
+                    const uint32_t j = c0 + lane;
+                    const bool ok = j < e;
+                    const uint32_t d = ok ? (uint32_t)(sk[j] >> shift) & 511u : 512u;
+                    const unsigned peers = digit9_peers(d);
+                    const uint32_t base = ok ? hist[d] : 0u;
+                    if (ok) {
+                        const uint32_t dst = base + __popc(peers & lt);
+                        dk[dst] = sk[j];
+                        dv[dst] = sv[j];
+                    }
+                    __syncwarp();
+                    if (ok && (peers & lt) == 0u) hist[d] = base + __popc(peers);
+                    __syncwarp();
+                }
+                uint64_t *tk = sk;
+                sk = dk;
+                dk = tk;
+                uint32_t *tv = sv;
+                sv = dv;
+                dv = tv;
+            }
+            // three passes leave the run in tkey/tval
+            for (uint32_t j = s + lane; j < e; j += 32) {
+                key[j] = tkey[j];
+                val[j] = tval[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t n, int key_passes, int box_passes,
-                const uint32_t *box_off, int nbox, uint32_t *hist, unsigned long long *status, DevStatus *st,
-                uint64_t **k_out, uint32_t **v_out, cudaStream_t s, int nsm)
+                const uint32_t *box_off, int nbox, uint32_t *hist, unsigned long long *status, uint32_t *runs,
+                DevStatus *st, uint64_t **k_out, uint32_t **v_out, cudaStream_t s, int nsm)
 {
     // the shared-memory opt-in applies to the current device only: set once per device
     static std::atomic<bool> attr_set[kMaxDevices];
@@ -331,13 +546,14 @@ void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t
     if (dev < 0 || !attr_set[dev].load()) {
         cudaFuncSetAttribute(k_rs_onesweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem);
         cudaFuncSetAttribute(k_rs_onesweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem);
+        cudaFuncSetAttribute(k_runs_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRunSmem);
         if (dev >= 0) attr_set[dev].store(true);
     }
     const uint32_t ntile = rs_tiles(n);
     const int passes = key_passes + box_passes;
     cudaMemsetAsync(hist, 0, sizeof(uint32_t) * radix_hist_elems(n), s);
     cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)passes * ntile * 256, s);
-    k_rs_hist_all<<<nsm * 4, 256, 0, s>>>(k0, n, key_passes, box_passes, box_off, nbox, hist);
+    k_rs_hist_all<<<nsm * 4, 256, 0, s>>>(k0, n, key_passes, box_passes, box_off, nbox, hist, kRsLowBits);
     k_rs_digit_starts<<<1, 32 * passes, 0, s>>>(hist, passes);
     g_launches += 2;
     uint64_t *ki = k0, *ko = k1;
@@ -345,7 +561,7 @@ void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t
     uint32_t *vfree = v0;
     for (int p = 0; p < passes; p++) {
         const bool boxp = p >= key_passes;
-        const int shift = boxp ? 8 * (p - key_passes) : 8 * p;
+        const int shift = boxp ? 8 * (p - key_passes) : kRsLowBits + 8 * p;
         const uint32_t *ds = hist + kRsMaxPasses * 256 + p * 256;
         uint32_t *tk = hist + kRsMaxPasses * 512 + p;
         unsigned long long *sw = status + (size_t)p * ntile * 256;
@@ -363,6 +579,12 @@ void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t
         vi = vo;
         vo = vt;
     }
+    // phase B: each run of equal top bits by its low bits, in place in (ki, vi); ko and vo
+    // hold nothing that is still needed and serve the one-warp path as scratch
+    uint32_t *n_long = hist + kRsMaxPasses * 512 + kRsMaxPasses;
+    k_runs_short<<<nsm * 8, 256, 0, s>>>(ki, vi, n, box_off, nbox, runs, runs_cap(n), n_long);
+    k_runs_long<<<nsm, kRunThreads, kRunSmem, s>>>(ki, vi, ko, vo, runs, runs_cap(n), n_long, n_long + 1);
+    g_launches += 2;
     *k_out = ki;
     *v_out = vi;
 }

@@ -317,6 +317,30 @@ def test_batched_boxes_with_mixed_leaf_sizes(ctx):
         assert np.array_equal(acc[off[b]:off[b + 1]], singles[b])
 
 
+def test_sort_runs_of_every_size_bit_exact(ctx):
+    """The sort orders the top 36 key bits first, then each run of particles sharing a
+    level-12 cell by the rest of the key: runs of one, short runs (insertion sort), runs of
+    thousands (block sort in shared memory), a run beyond that (the one-warp path) and
+    coincident particles (equal keys: input order).  Keys and permutation bit-exact."""
+    rng = np.random.default_rng(17)
+    L = 1.0
+    cell = L / 4096
+    parts = [rng.random((30000, 3))]                                              # runs of one
+    c0 = (np.floor(rng.random((800, 3)) * 4096) + 0.5) * cell
+    parts.append((c0[:, None, :] + (rng.random((800, 10, 3)) - 0.5) * cell * 0.98).reshape(-1, 3))  # runs of 10
+    parts.append(np.array([0.3, 0.6, 0.2]) + rng.random((5000, 3)) * cell * 0.98)                # a run of 5000
+    parts.append(np.array([0.71, 0.13, 0.55]) + rng.random((20000, 3)) * cell * 0.98)            # a run of 20000
+    parts.append(np.repeat(np.array([[0.9, 0.9, 0.1]]), 300, axis=0))                         # equal keys
+    pos = np.concatenate(parts)
+    pos = pos[rng.permutation(len(pos))]
+    mass = np.full(len(pos), 1.0 / len(pos), np.float32)
+    prm = dict(L=L, r_cut=0.01, theta=0.5, n_crit=64)
+    ctx.build_tree(_t(pos, np.float64), _t(mass, np.float32), greem.params(**prm))
+    key, perm, _, _ = oracle.Tree(pos, mass, L, prm["r_cut"], n_crit=64).sorted()
+    assert np.array_equal(ctx.dump(greem.DUMP_KEYS), key)
+    assert np.array_equal(ctx.dump(greem.DUMP_PERM).astype(np.int64), perm)
+
+
 def test_graph_replay_matches_direct_call(ctx):
     pos, mass = clustered(5000, 40)
     prm = dict(L=1.0, r_cut=0.08, theta=0.5, n_crit=64)
