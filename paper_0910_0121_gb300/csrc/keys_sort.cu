@@ -77,7 +77,7 @@ void launch_keys(const double *pos, uint32_t N, const uint32_t *box_off, int nbo
 // iteration limit, after which the status records a timeout (the call then fails).
 // Phase B: the pairs now form runs of equal top bits (particles that share a level-12
 // cell), each in input order; every run is sorted by its low 27 bits in place, stably.
-// Most runs hold one particle and cost nothing; runs of up to 16 are insertion-sorted by
+// Most runs hold one particle and cost nothing; runs of up to 64 are insertion-sorted by
 // the thread at their head, longer ones by a block (a bitonic sort of (low bits, position
 // in the run), so equal keys keep their order), and runs beyond a block's shared memory
 // by a slower exact one-warp LSD pass over their low bits.  The result is the stable sort
@@ -96,9 +96,9 @@ constexpr int kRsTile = kRsThreads * kRsItems;  // pairs per tile
 constexpr int kRsMaxPasses = 10;                // key digits + up to 2 box digits
 constexpr int kRsLowBits = 27;                  // bits left to phase B: levels 13-21
 constexpr int kRsKeyPasses = 5;                 // 8-bit digits over the top 36 bits
-constexpr int kShortRun = 16;                   // runs sorted by the thread at their head
+constexpr int kShortRun = 64;                   // runs sorted by the thread at their head
 constexpr int kRunCap = 8192;                   // runs sorted by a block in shared memory
-constexpr int kRunThreads = 1024;
+constexpr int kRunThreads = 256;
 constexpr size_t kRunSmem = (size_t)kRunCap * (sizeof(uint64_t) + sizeof(uint32_t));
 constexpr int kRsLook = 8;                      // predecessors loaded at once in the look-back
 constexpr unsigned long long kRsAgg = 1ull << 62, kRsPrefix = 2ull << 62, kRsValue = (1ull << 62) - 1;
@@ -359,65 +359,63 @@ __device__ __forceinline__ unsigned digit9_peers(uint32_t d)
     return peers;
 }
 
-// Every run head: a run of up to kShortRun pairs is insertion-sorted (stable) by the head's
-// thread in place; a longer one goes to the list for k_runs_long, its end found by binary
-// search (the top bits are sorted within a box).  Other threads only read the top bits of
-// pairs that runs permute among themselves, so the concurrent sorts do not disturb them.
+// A short run [i, i + len), sorted (stable insertion sort) in place: its few pairs stay in
+// the L1 cache.  A real call, so that the threads that only test for a run head (nearly
+// all) keep a small register and stack footprint.
+static __device__ __noinline__ void sort_short_run(uint64_t *__restrict__ key, uint32_t *__restrict__ val, uint32_t i,
+                                                   uint32_t len)
+{
+    for (uint32_t q = 1; q < len; q++) {
+        const uint64_t x = key[i + q];
+        const uint32_t y = val[i + q];
+        int r = (int)q - 1;
+        while (r >= 0 && key[i + r] > x) {
+            key[i + r + 1] = key[i + r];
+            val[i + r + 1] = val[i + r];
+            r--;
+        }
+        key[i + r + 1] = x;
+        val[i + r + 1] = y;
+    }
+}
+
+// One thread per pair; the thread at the head of a run of two or more sorts a run of up
+// to kShortRun pairs itself and lists a longer one for k_runs_long, its end found by
+// binary search (the top bits are sorted within a box).  Other threads only read the top
+// bits of pairs that runs permute among themselves, so the concurrent sorts do not
+// disturb them.
 __global__ void __launch_bounds__(256) k_runs_short(uint64_t *__restrict__ key, uint32_t *__restrict__ val, uint32_t n,
                                                     const uint32_t *__restrict__ box_off, int nbox,
                                                     uint32_t *__restrict__ runs, uint32_t run_cap,
                                                     uint32_t *__restrict__ n_long)
 {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint64_t t = run_top(key[i]);
-        uint32_t e_box = n;
-        bool head = i == 0 || run_top(key[i - 1]) != t;
-        if (nbox > 1) {
-            const int b = box_of(i, box_off, nbox);
-            e_box = box_off[b + 1];
-            if (box_off[b] == i) head = true;
-        }
-        if (!head) continue;
-        uint32_t e = i + 1;
-        while (e < e_box && e - i <= (uint32_t)kShortRun && run_top(key[e]) == t) e++;
-        if (e - i <= (uint32_t)kShortRun) {
-            const uint32_t len = e - i;
-            if (len < 2) continue;
-            uint64_t kk[kShortRun];
-            uint32_t vv[kShortRun];
-            for (uint32_t q = 0; q < len; q++) {
-                kk[q] = key[i + q];
-                vv[q] = val[i + q];
-            }
-            for (uint32_t q = 1; q < len; q++) {
-                const uint64_t x = kk[q];
-                const uint32_t y = vv[q];
-                int r = (int)q - 1;
-                while (r >= 0 && kk[r] > x) {
-                    kk[r + 1] = kk[r];
-                    vv[r + 1] = vv[r];
-                    r--;
-                }
-                kk[r + 1] = x;
-                vv[r + 1] = y;
-            }
-            for (uint32_t q = 0; q < len; q++) {
-                key[i + q] = kk[q];
-                val[i + q] = vv[q];
-            }
-        } else {
-            uint32_t lo = e, hi = e_box;  // the first index from e on whose top differs (or e_box)
-            while (lo < hi) {
-                const uint32_t mid = lo + (hi - lo) / 2;
-                if (run_top(key[mid]) == t) lo = mid + 1;
-                else hi = mid;
-            }
-            const uint32_t slot = atomicAdd(n_long, 1u);
-            if (slot < run_cap) {  // always: a run longer than kShortRun takes more than kShortRun pairs
-                runs[2 * slot] = i;
-                runs[2 * slot + 1] = lo;
-            }
-        }
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t t = run_top(key[i]);
+    uint32_t e_box = n;
+    bool head = i == 0 || run_top(key[i - 1]) != t;
+    if (nbox > 1) {
+        const int b = box_of(i, box_off, nbox);
+        e_box = box_off[b + 1];
+        if (box_off[b] == i) head = true;
+    }
+    if (!head || i + 1 >= e_box || run_top(key[i + 1]) != t) return;  // not a head, or a run of one
+    uint32_t e = i + 2;
+    while (e < e_box && e - i <= (uint32_t)kShortRun && run_top(key[e]) == t) e++;
+    if (e - i <= (uint32_t)kShortRun) {
+        sort_short_run(key, val, i, e - i);
+        return;
+    }
+    uint32_t lo = e, hi = e_box;  // the first index from e on whose top differs (or e_box)
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (run_top(key[mid]) == t) lo = mid + 1;
+        else hi = mid;
+    }
+    const uint32_t slot = atomicAdd(n_long, 1u);
+    if (slot < run_cap) {  // always: a run longer than kShortRun takes more than kShortRun pairs
+        runs[2 * slot] = i;
+        runs[2 * slot + 1] = lo;
     }
 }
 
@@ -582,7 +580,7 @@ void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t
     // phase B: each run of equal top bits by its low bits, in place in (ki, vi); ko and vo
     // hold nothing that is still needed and serve the one-warp path as scratch
     uint32_t *n_long = hist + kRsMaxPasses * 512 + kRsMaxPasses;
-    k_runs_short<<<nsm * 8, 256, 0, s>>>(ki, vi, n, box_off, nbox, runs, runs_cap(n), n_long);
+    k_runs_short<<<(n + 255) / 256, 256, 0, s>>>(ki, vi, n, box_off, nbox, runs, runs_cap(n), n_long);
     k_runs_long<<<nsm, kRunThreads, kRunSmem, s>>>(ki, vi, ko, vo, runs, runs_cap(n), n_long, n_long + 1);
     g_launches += 2;
     *k_out = ki;
