@@ -544,7 +544,8 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     launch_leaf_boxes(c->nodes.p, n_nodes, ncap, c->pcell.p, c->lbox.p, s2, nsm);
     launch_record_counts(n_nodes, n_groups, c->st.p, ncap, s2);
     cudaEventRecord(c->ev_join, s2);
-    launch_moments(c->nodes.p, n_nodes, ncap, c->kids.p, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p, c->lvl.p,
+    launch_moments(c->nodes.p, n_nodes, ncap, c->kids.p, c->base.p, N, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p,
+                   c->lvl.p,
                    c->ctr.p, s, nsm);
     launch_node_finish(c->nodes.p, n_nodes, ncap, c->raw.p, c->box_off.p, nbox, c->bps.p, c->mom64.p, c->noff.p, s,
                        nsm);

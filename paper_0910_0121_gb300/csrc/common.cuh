@@ -188,8 +188,8 @@ void launch_tree_fill(const uint64_t *keys, uint32_t N, const uint32_t *box_off,
 void launch_tree_links(Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, uint8_t *nchild, uint32_t *kids,
                        cudaStream_t s, int nsm);
 void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
-                    const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw, uint32_t *lvl,
-                    uint32_t *inodes, cudaStream_t s, int nsm);
+                    const uint32_t *base, uint32_t N, const double *xs, const double *ys, const double *zs,
+                    const float *ms, Dbl4 *raw, uint32_t *lvl, uint32_t *inodes, cudaStream_t s, int nsm);
 void launch_quadrupoles(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
                         const float4 *poff, const float4 *noff, const uint32_t *lvl, const uint32_t *inodes,
                         const uint32_t *box_off, int nbox, const BoxPar *bps, float4 *quad, cudaStream_t s, int nsm);

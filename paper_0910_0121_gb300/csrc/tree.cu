@@ -218,14 +218,14 @@ void launch_tree_links(Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, 
     g_launches++;
 }
 
-// Monopole moments (Sec. 3.1.2, centre-of-mass approximation), bottom up.  The nodes are
-// first bucketed: internal nodes by level (buckets 0-31), leaves by particle count
-// (buckets 32-63, count min(n, 31)).  Leaves then sum their particles in FP64, one
-// thread per leaf in bucket order, so the lanes of a warp loop over equally many
-// particles (an FP64 warp instruction costs the same with idle lanes, and FP64 issue is
-// expensive on this GPU).  Internal nodes follow level by level, deepest first, each
-// summing its children's raw moments in child order.  Every sum has a fixed order, so
-// the result does not depend on scheduling.
+// Monopole moments (Sec. 3.1.2, centre-of-mass approximation), bottom up.  Leaves sum
+// their particles in FP64 by tiles of consecutive particles (k_moments_leaf_tiled below:
+// coalesced loads, and within a tile the leaves taken in order of particle count, so the
+// lanes of a warp loop over equally many particles: an FP64 warp instruction costs the
+// same with idle lanes, and FP64 issue is expensive on this GPU).  Internal nodes are
+// bucketed by level and follow level by level, deepest first, each summing its
+// children's raw moments in child order.  Every sum has a fixed order, so the result
+// does not depend on scheduling.
 //
 // lvl[0..64): nodes per bucket, lvl[64..128): bucket start, lvl[128..192): cursor.
 constexpr int kLeafBucket = 32;
@@ -244,7 +244,10 @@ __global__ void __launch_bounds__(256) k_node_buckets(const Node *__restrict__ n
     __syncthreads();
     const uint32_t nn = node_count(n_nodes, node_cap);
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n < nn) atomicAdd(&cnt[node_bucket(nodes[n])], 1u);
+    if (n < nn) {
+        const Node nd = nodes[n];
+        if (!(nd.lvl & 256u)) atomicAdd(&cnt[node_bucket(nd)], 1u);  // leaves are summed by tiles
+    }
     __syncthreads();
     if (threadIdx.x < 64 && cnt[threadIdx.x]) atomicAdd(&lvl[threadIdx.x], cnt[threadIdx.x]);
 }
@@ -280,38 +283,109 @@ __global__ void __launch_bounds__(256) k_level_scatter(const Node *__restrict__ 
     const uint32_t nn = node_count(n_nodes, node_cap);
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t key = 0, slot = 0;
+    bool inner = false;
     if (n < nn) {
-        key = node_bucket(nodes[n]);
-        slot = atomicAdd(&cnt[key], 1u);
+        const Node nd = nodes[n];
+        inner = !(nd.lvl & 256u);  // leaves are summed by tiles
+        if (inner) {
+            key = node_bucket(nd);
+            slot = atomicAdd(&cnt[key], 1u);
+        }
     }
     __syncthreads();
     if (threadIdx.x < 64 && cnt[threadIdx.x]) base[threadIdx.x] = atomicAdd(&lvl[128 + threadIdx.x], cnt[threadIdx.x]);
     __syncthreads();
-    if (n < nn) inodes[base[key] + slot] = n;
+    if (inner) inodes[base[key] + slot] = n;
 }
 
-__global__ void __launch_bounds__(256) k_moments_leaf(const Node *__restrict__ nodes,
-                                                      const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
-                                                      const uint32_t *__restrict__ lvl,
-                                                      const uint32_t *__restrict__ inodes,
-                                                      const double *__restrict__ xs, const double *__restrict__ ys,
-                                                      const double *__restrict__ zs, const float *__restrict__ ms,
-                                                      Dbl4 *__restrict__ raw)
+// Leaf moments by tiles of consecutive particles: a block takes the leaves that start in
+// its tile of kLeafTile sorted particles (the deepest node a particle owns is a leaf, so
+// particle i starts leaf base[i+1] - 1 when it owns any node), stages the tile's
+// particles and a halo in shared memory with coalesced loads, and orders its leaves by
+// particle count, so that the lanes of a warp loop equally often (an FP64 warp
+// instruction costs the same with idle lanes).  Each leaf sums its particles in sorted
+// order, as a thread alone would.  Leaves reaching past the halo read the rest from
+// global memory.
+constexpr int kLeafTile = 1024;
+constexpr int kLeafHalo = 64;
+
+__global__ void __launch_bounds__(256) k_moments_leaf_tiled(const Node *__restrict__ nodes,
+                                                            const uint32_t *__restrict__ n_nodes, uint32_t node_cap,
+                                                            const uint32_t *__restrict__ base, uint32_t N,
+                                                            const double *__restrict__ xs,
+                                                            const double *__restrict__ ys,
+                                                            const double *__restrict__ zs,
+                                                            const float *__restrict__ ms, Dbl4 *__restrict__ raw)
 {
+    __shared__ double sx_[kLeafTile + kLeafHalo], sy_[kLeafTile + kLeafHalo], sz_[kLeafTile + kLeafHalo];
+    __shared__ float sm_[kLeafTile + kLeafHalo];
+    __shared__ uint32_t leaf_n[kLeafTile], leaf_b[kLeafTile], leaf_e[kLeafTile], order[kLeafTile];
+    __shared__ uint32_t cnt[33], start[33], nleaf;
     const uint32_t nn = node_count(n_nodes, node_cap);
-    for (uint32_t i = lvl[64 + kLeafBucket] + blockIdx.x * blockDim.x + threadIdx.x; i < nn;
-         i += gridDim.x * blockDim.x) {
-        const uint32_t n = inodes[i];
-        const uint32_t b = nodes[n].begin, e = nodes[n].end;
-        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        for (uint32_t j = b; j < e; j++) {
-            const double m = (double)ms[j];
-            M += m;
-            sx = fma(m, xs[j], sx);
-            sy = fma(m, ys[j], sy);
-            sz = fma(m, zs[j], sz);
+    const uint32_t p0 = blockIdx.x * kLeafTile;
+    const uint32_t pe = min(N, p0 + kLeafTile + kLeafHalo);
+    const int tid = threadIdx.x;
+    if (tid < 33) cnt[tid] = 0;
+    if (tid == 0) nleaf = 0;
+    for (uint32_t q = tid; q < pe - p0; q += blockDim.x) {
+        sx_[q] = xs[p0 + q];
+        sy_[q] = ys[p0 + q];
+        sz_[q] = zs[p0 + q];
+        sm_[q] = ms[p0 + q];
+    }
+    __syncthreads();
+    // the leaves that start in the tile
+    const uint32_t pt = min(N, p0 + kLeafTile);
+    for (uint32_t i = p0 + tid; i < pt; i += blockDim.x) {
+        const uint32_t o0 = base[i], o1 = base[i + 1];
+        if (o1 == o0) continue;
+        const uint32_t n = o1 - 1;
+        if (n >= nn) continue;  // a truncated tree: the call is retried
+        const uint32_t e = nodes[n].end;
+        const uint32_t slot = atomicAdd(&nleaf, 1u);
+        leaf_n[slot] = n;
+        leaf_b[slot] = i;
+        leaf_e[slot] = e;
+        atomicAdd(&cnt[min(e - i, 32u)], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) {  // bucket starts by particle count (1..31, then 32 and more)
+        const uint32_t v = cnt[tid + 1];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (tid >= o) x += y;
         }
-        raw[n] = make_dbl4(sx, sy, sz, M);
+        start[tid + 1] = x - v;
+    }
+    __syncthreads();
+    const uint32_t L = nleaf;
+    for (uint32_t k = tid; k < L; k += blockDim.x) order[atomicAdd(&start[min(leaf_e[k] - leaf_b[k], 32u)], 1u)] = k;
+    __syncthreads();
+    for (uint32_t q = tid; q < L; q += blockDim.x) {
+        const uint32_t k = order[q];
+        const uint32_t b = leaf_b[k], e = leaf_e[k];
+        double M = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+        for (uint32_t j = b; j < e; j++) {
+            double m, x, y, z;
+            if (j < pe) {
+                m = (double)sm_[j - p0];
+                x = sx_[j - p0];
+                y = sy_[j - p0];
+                z = sz_[j - p0];
+            } else {
+                m = (double)ms[j];
+                x = xs[j];
+                y = ys[j];
+                z = zs[j];
+            }
+            M += m;
+            ax = fma(m, x, ax);
+            ay = fma(m, y, ay);
+            az = fma(m, z, az);
+        }
+        raw[leaf_n[k]] = make_dbl4(ax, ay, az, M);
     }
 }
 
@@ -340,15 +414,17 @@ __global__ void __launch_bounds__(256) k_moments_level(int level, const uint32_t
 }
 
 void launch_moments(const Node *nodes, const uint32_t *n_nodes, uint32_t node_cap, const uint32_t *kids,
-                    const double *xs, const double *ys, const double *zs, const float *ms, Dbl4 *raw, uint32_t *lvl,
-                    uint32_t *inodes, cudaStream_t s, int nsm)
+                    const uint32_t *base, uint32_t N, const double *xs, const double *ys, const double *zs,
+                    const float *ms, Dbl4 *raw, uint32_t *lvl, uint32_t *inodes, cudaStream_t s, int nsm)
 {
+    (void)nsm;
     cudaMemsetAsync(lvl, 0, 192 * sizeof(uint32_t), s);
     const unsigned grid = (node_cap + 255) / 256;
     k_node_buckets<<<grid, 256, 0, s>>>(nodes, n_nodes, node_cap, lvl);
     k_level_scan<<<1, 32, 0, s>>>(lvl);
     k_level_scatter<<<grid, 256, 0, s>>>(nodes, n_nodes, node_cap, lvl, inodes);
-    k_moments_leaf<<<nsm * 8, 256, 0, s>>>(nodes, n_nodes, node_cap, lvl, inodes, xs, ys, zs, ms, raw);
+    k_moments_leaf_tiled<<<(N + kLeafTile - 1) / kLeafTile, 256, 0, s>>>(nodes, n_nodes, node_cap, base, N, xs, ys,
+                                                                       zs, ms, raw);
     g_launches += 4;
     for (int level = kMaxLevel - 1; level >= 0; level--) {
         k_moments_level<<<nsm * 4, 256, 0, s>>>(level, lvl, inodes, kids, raw);
