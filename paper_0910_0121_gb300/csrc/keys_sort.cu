@@ -77,8 +77,9 @@ void launch_keys(const double *pos, uint32_t N, const uint32_t *box_off, int nbo
 // iteration limit, after which the status records a timeout (the call then fails).
 // Phase B: the pairs now form runs of equal top bits (particles that share a level-12
 // cell), each in input order; every run is sorted by its low 27 bits in place, stably.
-// Most runs hold one particle and cost nothing; runs of up to 64 are insertion-sorted by
-// the thread at their head, longer ones by a block (a bitonic sort of (low bits, position
+// Most runs hold one particle and cost nothing; runs of up to 16 are insertion-sorted by
+// the thread at their head, runs of up to 64 by a warp and longer ones by a block (a
+// bitonic sort of (low bits, position
 // in the run), so equal keys keep their order), and runs beyond a block's shared memory
 // by a slower exact one-warp LSD pass over their low bits.  The result is the stable sort
 // by the full 63-bit key, whatever the clustering: phase A leaves equal top bits in input
@@ -96,7 +97,7 @@ constexpr int kRsTile = kRsThreads * kRsItems;  // pairs per tile
 constexpr int kRsMaxPasses = 10;                // key digits + up to 2 box digits
 constexpr int kRsLowBits = 27;                  // bits left to phase B: levels 13-21
 constexpr int kRsKeyPasses = 5;                 // 8-bit digits over the top 36 bits
-constexpr int kShortRun = 64;                   // runs sorted by the thread at their head
+constexpr int kShortRun = 16;                   // runs sorted by the thread at their head
 constexpr int kRunCap = 8192;                   // runs sorted by a block in shared memory
 constexpr int kRunThreads = 256;
 constexpr size_t kRunSmem = (size_t)kRunCap * (sizeof(uint64_t) + sizeof(uint32_t));
@@ -107,11 +108,14 @@ constexpr size_t kRsSmem = (size_t)kRsTile * (sizeof(uint64_t) + sizeof(uint32_t
 static inline uint32_t rs_tiles(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
 
 // u32 words: [passes][256] digit counts, [passes][256] digit starts, [passes] tickets, then
-// phase B's count of long runs and its work counter
-size_t radix_hist_elems(uint32_t) { return (size_t)kRsMaxPasses * 512 + kRsMaxPasses + 2; }
-// phase B's list of runs longer than kShortRun: (start, end) pairs
-static inline uint32_t runs_cap(uint32_t n) { return n / (kShortRun + 1) + 64; }
-size_t radix_runs_elems(uint32_t n) { return 2 * (size_t)runs_cap(n); }
+// phase B's counts of long and middle runs and their work counters
+size_t radix_hist_elems(uint32_t) { return (size_t)kRsMaxPasses * 512 + kRsMaxPasses + 4; }
+// phase B's lists of runs: (start, end) pairs of kShortRun + 1 .. kWarpRun pairs (sorted
+// by a warp), then of more (sorted by a block)
+constexpr int kWarpRun = 64;
+static inline uint32_t mid_cap(uint32_t n) { return n / (kShortRun + 1) + 64; }
+static inline uint32_t runs_cap(uint32_t n) { return n / (kWarpRun + 1) + 64; }
+size_t radix_runs_elems(uint32_t n) { return 2 * ((size_t)mid_cap(n) + runs_cap(n)); }
 int radix_key_passes() { return kRsKeyPasses; }
 // u64 look-back words: [passes][tiles][256]
 size_t radix_status_elems(uint32_t n) { return (size_t)kRsMaxPasses * rs_tiles(n) * 256; }
@@ -380,14 +384,15 @@ static __device__ __noinline__ void sort_short_run(uint64_t *__restrict__ key, u
 }
 
 // One thread per pair; the thread at the head of a run of two or more sorts a run of up
-// to kShortRun pairs itself and lists a longer one for k_runs_long, its end found by
-// binary search (the top bits are sorted within a box).  Other threads only read the top
-// bits of pairs that runs permute among themselves, so the concurrent sorts do not
-// disturb them.
+// to kShortRun pairs itself and lists a longer one, its end found by binary search (the
+// top bits are sorted within a box): up to kWarpRun pairs for k_runs_warp (mid, n_mid),
+// more for k_runs_long (runs, n_long).  Other threads only read the top bits of pairs that
+// runs permute among themselves, so the concurrent sorts do not disturb them.
 __global__ void __launch_bounds__(256) k_runs_short(uint64_t *__restrict__ key, uint32_t *__restrict__ val, uint32_t n,
                                                     const uint32_t *__restrict__ box_off, int nbox,
                                                     uint32_t *__restrict__ runs, uint32_t run_cap,
-                                                    uint32_t *__restrict__ n_long)
+                                                    uint32_t *__restrict__ n_long, uint32_t *__restrict__ mid,
+                                                    uint32_t mid_cap_, uint32_t *__restrict__ n_mid)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -412,10 +417,75 @@ __global__ void __launch_bounds__(256) k_runs_short(uint64_t *__restrict__ key, 
         if (run_top(key[mid]) == t) lo = mid + 1;
         else hi = mid;
     }
+    if (lo - i <= (uint32_t)kWarpRun) {
+        const uint32_t slot = atomicAdd(n_mid, 1u);
+        if (slot < mid_cap_) {  // always: each listed run takes more than kShortRun pairs
+            mid[2 * slot] = i;
+            mid[2 * slot + 1] = lo;
+        }
+        return;
+    }
     const uint32_t slot = atomicAdd(n_long, 1u);
-    if (slot < run_cap) {  // always: a run longer than kShortRun takes more than kShortRun pairs
+    if (slot < run_cap) {  // always: each listed run takes more than kWarpRun pairs
         runs[2 * slot] = i;
         runs[2 * slot + 1] = lo;
+    }
+}
+
+// Runs of kShortRun + 1 .. kWarpRun pairs, one warp each: lane l holds the run's pairs l
+// and l + 32; a 64-element bitonic network sorts the unique keys (low bits << 14 |
+// position), the step between the two halves inside each lane, the others by shuffles;
+// then every lane fetches the pairs its sorted keys name.
+__global__ void __launch_bounds__(256) k_runs_warp(uint64_t *__restrict__ key, uint32_t *__restrict__ val,
+                                                   const uint32_t *__restrict__ mid, uint32_t mid_cap_,
+                                                   const uint32_t *__restrict__ n_mid, uint32_t *__restrict__ ctr)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nm = min(*n_mid, mid_cap_);
+    const uint64_t lowmask = (1ull << kRsLowBits) - 1ull;
+    for (;;) {
+        uint32_t r = 0;
+        if (lane == 0) r = atomicAdd(ctr, 1u);
+        r = __shfl_sync(FULL, r, 0);
+        if (r >= nm) break;
+        const uint32_t s = mid[2 * r], len = mid[2 * r + 1] - s;
+        const uint32_t e0 = (uint32_t)lane, e1 = (uint32_t)lane + 32u;
+        const uint64_t k0 = e0 < len ? key[s + e0] : 0ull, k1 = e1 < len ? key[s + e1] : 0ull;
+        const uint32_t v0 = e0 < len ? val[s + e0] : 0u, v1 = e1 < len ? val[s + e1] : 0u;
+        const uint64_t top = run_top(__shfl_sync(FULL, k0, 0));
+        uint64_t c0 = e0 < len ? ((k0 & lowmask) << 14) | e0 : ~0ull;
+        uint64_t c1 = e1 < len ? ((k1 & lowmask) << 14) | e1 : ~0ull;
+#pragma unroll
+        for (uint32_t kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll
+            for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+                if (jj == 32) {  // partners in the same lane; kk = 64: ascending
+                    const uint64_t lo_ = c0 < c1 ? c0 : c1, hi_ = c0 < c1 ? c1 : c0;
+                    c0 = lo_;
+                    c1 = hi_;
+                } else {
+                    const uint64_t o0 = __shfl_xor_sync(FULL, c0, jj), o1 = __shfl_xor_sync(FULL, c1, jj);
+                    const bool lower = (e0 & jj) == 0;  // the same for e1 = e0 + 32
+                    const bool up0 = (e0 & kk) == 0, up1 = (e1 & kk) == 0;
+                    c0 = (lower == up0) ? (c0 < o0 ? c0 : o0) : (c0 > o0 ? c0 : o0);
+                    c1 = (lower == up1) ? (c1 < o1 ? c1 : o1) : (c1 > o1 ? c1 : o1);
+                }
+            }
+        }
+        const uint32_t p0 = (uint32_t)(c0 & 0x3fffu), p1 = (uint32_t)(c1 & 0x3fffu);
+        const uint64_t a0 = __shfl_sync(FULL, k0, p0 & 31u), b0 = __shfl_sync(FULL, k1, p0 & 31u);
+        const uint32_t x0 = __shfl_sync(FULL, v0, p0 & 31u), y0 = __shfl_sync(FULL, v1, p0 & 31u);
+        const uint64_t a1 = __shfl_sync(FULL, k0, p1 & 31u), b1 = __shfl_sync(FULL, k1, p1 & 31u);
+        const uint32_t x1 = __shfl_sync(FULL, v0, p1 & 31u), y1 = __shfl_sync(FULL, v1, p1 & 31u);
+        if (e0 < len) {
+            key[s + e0] = (top << kRsLowBits) | ((p0 >> 5) ? (b0 & lowmask) : (a0 & lowmask));
+            val[s + e0] = (p0 >> 5) ? y0 : x0;
+        }
+        if (e1 < len) {
+            key[s + e1] = (top << kRsLowBits) | ((p1 >> 5) ? (b1 & lowmask) : (a1 & lowmask));
+            val[s + e1] = (p1 >> 5) ? y1 : x1;
+        }
     }
 }
 
@@ -579,10 +649,13 @@ void radix_sort(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, uint32_t
     }
     // phase B: each run of equal top bits by its low bits, in place in (ki, vi); ko and vo
     // hold nothing that is still needed and serve the one-warp path as scratch
-    uint32_t *n_long = hist + kRsMaxPasses * 512 + kRsMaxPasses;
-    k_runs_short<<<(n + 255) / 256, 256, 0, s>>>(ki, vi, n, box_off, nbox, runs, runs_cap(n), n_long);
+    uint32_t *n_long = hist + kRsMaxPasses * 512 + kRsMaxPasses;  // n_long, long work, n_mid, mid work
+    uint32_t *mid = runs + 2 * (size_t)runs_cap(n);
+    k_runs_short<<<(n + 255) / 256, 256, 0, s>>>(ki, vi, n, box_off, nbox, runs, runs_cap(n), n_long, mid, mid_cap(n),
+                                                  n_long + 2);
+    k_runs_warp<<<nsm * 4, 256, 0, s>>>(ki, vi, mid, mid_cap(n), n_long + 2, n_long + 3);
     k_runs_long<<<nsm, kRunThreads, kRunSmem, s>>>(ki, vi, ko, vo, runs, runs_cap(n), n_long, n_long + 1);
-    g_launches += 2;
+    g_launches += 3;
     *k_out = ki;
     *v_out = vi;
 }
