@@ -319,15 +319,18 @@ def test_batched_boxes_with_mixed_leaf_sizes(ctx):
 
 def test_sort_runs_of_every_size_bit_exact(ctx):
     """The sort orders the top 36 key bits first, then each run of particles sharing a
-    level-12 cell by the rest of the key: runs of one, short runs (insertion sort), runs of
-    thousands (block sort in shared memory), a run beyond that (the one-warp path) and
-    coincident particles (equal keys: input order).  Keys and permutation bit-exact."""
+    level-12 cell by the rest of the key: runs of one, short runs (insertion sort by the
+    head), runs of 40 (one warp each), runs of thousands (block sort in shared memory), a
+    run beyond that (the one-warp LSD path) and coincident particles (equal keys: input
+    order).  Keys and permutation bit-exact."""
     rng = np.random.default_rng(17)
     L = 1.0
     cell = L / 4096
     parts = [rng.random((30000, 3))]                                              # runs of one
     c0 = (np.floor(rng.random((800, 3)) * 4096) + 0.5) * cell
     parts.append((c0[:, None, :] + (rng.random((800, 10, 3)) - 0.5) * cell * 0.98).reshape(-1, 3))  # runs of 10
+    c1 = (np.floor(rng.random((300, 3)) * 4096) + 0.5) * cell
+    parts.append((c1[:, None, :] + (rng.random((300, 40, 3)) - 0.5) * cell * 0.98).reshape(-1, 3))  # runs of 40
     parts.append(np.array([0.3, 0.6, 0.2]) + rng.random((5000, 3)) * cell * 0.98)                # a run of 5000
     parts.append(np.array([0.71, 0.13, 0.55]) + rng.random((20000, 3)) * cell * 0.98)            # a run of 20000
     parts.append(np.repeat(np.array([[0.9, 0.9, 0.1]]), 300, axis=0))                         # equal keys
