@@ -202,6 +202,12 @@ typedef struct greem_stats {
      * stream beside the moments: what remains of them after the moments, and the
      * second-order moments); lists; force (and PM); total */
     double ms_keys, ms_sort, ms_tree, ms_groups, ms_lists, ms_force, ms_total;
+    /* list walks that started below the root, from the level-K cell table (Sec. 3.1.2
+     * walk; the conditions under which the entries are the same are in lists.cu), and the
+     * leaves above level K those walks took from the table (counted only by calls that
+     * build index lists, GREEM_FLAG_INDEX_LISTS, 0 otherwise; a group whose list is
+     * walked again into fresh pages counts its leaves twice) */
+    int64_t n_start_table, n_start_coarse;
 } greem_stats;
 
 /* Counters of the last call.  Errors: INVALID_ARG for NULL arguments. */
@@ -251,12 +257,17 @@ int greem_debug_dump_group_lists(greem_ctx *ctx, const int64_t *groups, int64_t 
  *                             does from the usual first guesses; greem_stats.retries counts)
  *   GREEM_DEBUG_MAX_ATTEMPTS  attempts per call before GREEM_ERR_CAPACITY is returned
  *                             (default 6; value < 1 restores it).  Stays in effect.
+ *   GREEM_DEBUG_START_LEVEL   the deepest level (<= 7) at which a list walk may start
+ *                             instead of the root (default 7; 0 or 1: every walk starts at
+ *                             the root; value < 0 restores the default).  The lists hold the
+ *                             same entries either way; for timing comparisons.  Stays in effect.
  * Errors: INVALID_ARG (NULL ctx, unknown what, value out of range). */
 #define GREEM_DEBUG_WAIT_POLLS 0
 #define GREEM_DEBUG_NODE_CAP 1
 #define GREEM_DEBUG_LIST_CAP 2
 #define GREEM_DEBUG_STACK_CAP 3
 #define GREEM_DEBUG_MAX_ATTEMPTS 4
+#define GREEM_DEBUG_START_LEVEL 5
 int greem_debug_set(greem_ctx *ctx, int what, int64_t value);
 
 /* The FP32 list entries of selected groups exactly as the force kernel reads them, for

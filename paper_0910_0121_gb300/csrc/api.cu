@@ -72,6 +72,9 @@ struct greem_ctx {
     DBuf<float4> flist;
     DBuf<unsigned long long> ilist, loff;
     DBuf<uint32_t> llen, lraw, kids, stack, order, bins, lvl;
+    DBuf<uint32_t> tbl;   // the list walk's start tables (k_start_table)
+    int tbl_kmax = 0;     // the deepest start level of the current call's boxes
+    int start_cap = 7;    // the deepest level a list walk may start at (greem_debug_set)
     // per call
     DBuf<BoxPar> bps;
     DBuf<uint32_t> box_off, small;
@@ -275,10 +278,30 @@ static int derive_box(const greem_params &p, uint32_t pb, uint32_t pe, BoxPar &b
     }
     bp.p_begin = pb;
     bp.p_end = pe;
+    bp.rprune = (int)std::ceil(std::sqrt((double)bp.T_prune)) + 1;
     bp.lmin = lmin;
     bp.n_crit = p.n_crit;
     bp.n_leaf = p.n_leaf;
     return GREEM_OK;
+}
+
+// The level K at which a box's list walks start (the conditions are in lists.cu's
+// header): the first level at which a node can be accepted, at most cap, and no deeper
+// than the first level with at least one cell per 8 particles; 0 (walks start at the
+// root) for boxes of at most 4096 particles or if K would be below 2.  A level k admits no
+// accepted node when (sqrt(T_prune) + sqrt(3) h_k)^2 <= A[k], h_k the half side in u; the
+// test below keeps a margin above that bound.
+static int start_level(const BoxPar &bp, uint32_t n, int cap)
+{
+    if (cap < 2 || n <= (uint32_t)std::max(4096, bp.n_leaf)) return 0;
+    int kn = 2;
+    while (kn < cap && std::ldexp(1.0, 3 * kn) < n / 8.0) kn++;
+    const double R = std::sqrt((double)bp.T_prune);
+    for (int k = std::max(bp.lmin, 1); k < kn; k++) {
+        const double v = R + 1.7320508075688772 * std::ldexp(1.0, kMaxLevel - k);
+        if (v * v * (1.0 + 1e-9) + 16.0 > (double)bp.A[k]) return k >= 2 ? k : 0;
+    }
+    return kn;
 }
 
 static int check_common(const greem_params &p)
@@ -436,6 +459,18 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
         ENS(flist, c->list_cap);
         if (r.index_lists) ENS(ilist, c->list_cap);
     }
+    // start levels and table offsets (multiples of 64 entries: 16-byte aligned stores)
+    size_t tbl_n = 0;
+    c->tbl_kmax = 0;
+    for (int b = 0; b < r.nbox; b++) {
+        BoxPar &bp = c->bps_host[b];
+        const uint32_t nb = c->box_off_host[b + 1] - c->box_off_host[b];
+        bp.kstart = r.lists_force ? start_level(bp, nb, c->start_cap) : 0;
+        bp.tbl_off = tbl_n;
+        if (bp.kstart) tbl_n += (size_t)1 << (3 * bp.kstart);
+        c->tbl_kmax = std::max(c->tbl_kmax, bp.kstart);
+    }
+    if (tbl_n) ENS(tbl, tbl_n);
 #undef ENS
     return GREEM_OK;
 }
@@ -543,6 +578,8 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     launch_group_box(c->groups.p, n_groups, c->pcell.p, c->gbox.p, s2, nsm);
     launch_leaf_boxes(c->nodes.p, n_nodes, ncap, c->pcell.p, c->lbox.p, s2, nsm);
     launch_record_counts(n_nodes, n_groups, c->st.p, ncap, s2);
+    if (r.lists_force)
+        launch_start_table(c->nodes.p, c->kids.p, c->base.p, c->bps.p, nbox, c->tbl_kmax, c->tbl.p, c->st.p, s2);
     cudaEventRecord(c->ev_join, s2);
     launch_moments(c->nodes.p, n_nodes, ncap, c->kids.p, c->base.p, N, c->xs.p, c->ys.p, c->zs.p, c->ms.p, c->raw.p,
                    c->lvl.p,
@@ -581,6 +618,7 @@ static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
         if (r.quad) cudaMemsetAsync(c->qcnt.p, 0, sizeof(uint32_t) * ncap, s);
         la.cap = c->list_cap;
         la.page = c->page;
+        la.tbl = c->tbl.p;
         la.st = c->st.p;
         launch_lists(la, s, nsm);
         ev_record(c, r, ev, 5);
@@ -648,6 +686,8 @@ static int finish(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
     S.n_list_entries = (int64_t)h.sum_len;
     S.n_interactions = (int64_t)h.sum_inter;
     S.n_evaluated = (int64_t)h.sum_eval;
+    S.n_start_table = (int64_t)h.sum_start;
+    S.n_start_coarse = (int64_t)h.sum_coarse;
     S.list_capacity = (int64_t)c->list_cap;
     S.l_min = c->bps_host[0].lmin;
     if (r.timing && ev) {
@@ -1737,6 +1777,10 @@ int greem_debug_set(greem_ctx *c, int what, int64_t value)
     case GREEM_DEBUG_MAX_ATTEMPTS:
         if (value > 64) return GREEM_ERR_INVALID_ARG;
         c->max_attempts = value < 1 ? 6 : (int)value;
+        return GREEM_OK;
+    case GREEM_DEBUG_START_LEVEL:
+        if (value > 7) return GREEM_ERR_INVALID_ARG;
+        c->start_cap = value < 0 ? 7 : (int)value;
         return GREEM_OK;
     default:
         return GREEM_ERR_INVALID_ARG;

@@ -55,7 +55,10 @@ struct BoxPar {
     uint32_t p_begin, p_end;
     int lmin, n_crit, n_leaf, soft;
     int pow2_e;            // L = 2^pow2_e exactly, or kNotPow2
-    int pad1;
+    // The list walk's start level K (0: every walk starts at the root) and its table of
+    // level-K cells (8^K entries at tbl_off in ListArgs::tbl); rprune > sqrt(T_prune).
+    int kstart, rprune;
+    unsigned long long tbl_off;
 };
 constexpr int kNotPow2 = -100000;
 
@@ -81,6 +84,8 @@ struct DevStatus {
     unsigned long long sum_padded;     // sum of padded list lengths (the pool demand)
     unsigned long long work[4];        // persistent-kernel work queues
     unsigned long long sum_quad;       // entries the quadrupole lists need (on overflow)
+    unsigned long long sum_start;      // list walks started from a start table
+    unsigned long long sum_coarse;     // leaves above the start level taken from a table
 };
 
 enum : unsigned {
@@ -235,9 +240,15 @@ struct ListArgs {
     uint32_t *qcnt;            // per group: accepted node entries (may be null)
     unsigned long long cap;    // entries in the pool
     uint32_t page;             // entries per page
+    const uint32_t *tbl;       // start tables of the boxes with kstart > 0 (k_start_table)
     DevStatus *st;
 };
 void launch_lists(const ListArgs &a, cudaStream_t s, int nsm);
+// The start tables: for every box with kstart = K > 0, the node of each level-K cell
+// (Morton order), the leaf above it with bit 31 set, or kNone where the cell is empty.
+// kmax: the largest kstart over the boxes.
+void launch_start_table(const Node *nodes, const uint32_t *kids, const uint32_t *base, const BoxPar *bps, int nbox,
+                        int kmax, uint32_t *tbl, const DevStatus *st, cudaStream_t s);
 
 // S6 (force.cu)
 struct ForceArgs {

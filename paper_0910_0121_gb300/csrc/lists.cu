@@ -28,6 +28,25 @@
 //
 // Lists are contiguous per group inside pages handed out by an atomic counter; a list
 // that does not fit the warp's current page is walked again into fresh pages.
+//
+// The walk may start below the root.  Let K be a level at or above the first level at
+// which any node can be accepted: with the group's particle box inside its cell, a node of
+// half side h that passes the prune test lies at squared distance at most
+// (sqrt(T_prune) + sqrt(3) h)^2 from the group cell, so no node of a level k with that
+// bound <= A[k] (or k < l_min) is ever accepted, and every node above level K that the
+// recursive walk reaches is opened or, for a leaf, emptied.  A node below the root that
+// passes the prune test has every ancestor passing it too, as long as no ancestor's nearest
+// image differs from the image that holds the node; for an ancestor of half side <= L/4
+// that holds when L/4 > sqrt(T_prune) + the particle box's half side + its offset from
+// the cell centre, on every axis.  Under those two conditions the walk's entries are the
+// level-K nodes that pass their tests (and the leaves above level K that pass the prune
+// test) taken as the first step, which k_start_table makes a lookup: the level-K cells
+// within r_cut of the group's particle box are enumerated, each names its node (or the
+// leaf above it, taken once), and the children of the root down to level K are never
+// tested.  A group that fails a condition, or whose cells are too many, walks from the
+// root.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace greem {
@@ -118,6 +137,225 @@ __device__ __forceinline__ int owner_lane(uint32_t off, uint32_t t)
     return s;
 }
 
+// ---------------------------------------------------------------- start tables
+constexpr uint32_t kCoarseLeaf = 0x80000000u;  // table entry: a leaf above level K
+constexpr uint32_t kMaxStartCells = 512;       // more candidate cells: walk from the root
+
+// A list warp's counters, kept in shared memory by its lane 0 and added to the status
+// word once, when the warp runs out of groups.
+enum { kTallyPadded, kTallyLen, kTallyInter, kTallyStart, kTallyN };
+
+// A 10-bit integer's bits spread to every third bit (Morton interleave).
+__device__ __forceinline__ uint32_t spread_bits3(uint32_t v)
+{
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t cell_morton(uint32_t x, uint32_t y, uint32_t z)
+{
+    return (spread_bits3(x) << 2) | (spread_bits3(y) << 1) | spread_bits3(z);
+}
+
+// One thread per level-(K-1) cell of a box: the descent from the root to the node of
+// that cell gives the entries of its 8 level-K children, written as two 16-byte stores.
+__global__ void __launch_bounds__(256) k_start_table(const Node *__restrict__ nodes, const uint32_t *__restrict__ kids,
+                                                     const uint32_t *__restrict__ base,
+                                                     const BoxPar *__restrict__ bps, int nbox,
+                                                     uint32_t *__restrict__ tbl, const DevStatus *__restrict__ st)
+{
+    if (st->flags & ST_NODE_CAP) return;  // the tree is incomplete; the lists are not walked
+    for (int b = blockIdx.y; b < nbox; b += gridDim.y) {
+        const BoxPar &bp = bps[b];
+        const int K = bp.kstart;
+        if (K < 2) continue;
+        const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+        if (c >= (1u << (3 * (K - 1)))) continue;
+        uint32_t r = base[bp.p_begin];  // the box's root
+        bool empty = false;
+        for (int d = 1; d < K; d++) {
+            const uint32_t lv = nodes[r].lvl;
+            if (lv & 256u) break;  // a leaf above level K-1 holds the cell
+            const uint32_t oct = (c >> (3 * (K - 1 - d))) & 7u;
+            const uint32_t mask = (lv >> 16) & 255u;
+            if (!(mask & (1u << oct))) {
+                empty = true;
+                break;
+            }
+            r = kids[(size_t)r * 8 + __popc(mask & ((1u << oct) - 1u))];
+        }
+        uint32_t e[8];
+        const uint32_t lv = nodes[r].lvl;
+#pragma unroll
+        for (int o = 0; o < 8; o++) {
+            if (empty) e[o] = kNone;
+            else if (lv & 256u) e[o] = r | kCoarseLeaf;
+            else {
+                const uint32_t mask = (lv >> 16) & 255u;
+                e[o] = (mask & (1u << o)) ? kids[(size_t)r * 8 + __popc(mask & ((1u << o) - 1u))] : kNone;
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(tbl + bp.tbl_off + (size_t)c * 8);
+        dst[0] = make_uint4(e[0], e[1], e[2], e[3]);
+        dst[1] = make_uint4(e[4], e[5], e[6], e[7]);
+    }
+}
+
+void launch_start_table(const Node *nodes, const uint32_t *kids, const uint32_t *base, const BoxPar *bps, int nbox,
+                        int kmax, uint32_t *tbl, const DevStatus *st, cudaStream_t s)
+{
+    if (kmax < 2 || nbox < 1) return;
+    const uint32_t cells = 1u << (3 * (kmax - 1));
+    const dim3 grid((cells + 255) / 256, (unsigned)std::min(nbox, 65535));
+    k_start_table<<<grid, 256, 0, s>>>(nodes, kids, base, bps, nbox, tbl, st);
+    g_launches++;
+}
+
+// One tested cell per lane: an accepted node becomes one entry at its centre of mass
+// (acc), a node to open or a leaf to empty goes onto the stack (push).  Returns false
+// when the stack would overflow (the status is set; the call is retried).
+template <bool INDEX>
+__device__ __forceinline__ bool take_cells(const ListArgs &a, bool acc, bool push, uint32_t child, const CellTest &ct,
+                                           float kf, unsigned long long pos0, unsigned long long lim, unsigned lt,
+                                           uint32_t &cnt, uint32_t &nacc, uint32_t *__restrict__ stk, uint32_t &sp,
+                                           uint32_t cap)
+{
+    const unsigned FULL = 0xffffffffu;
+    const unsigned ab = __ballot_sync(FULL, acc);
+    if (acc) {
+        const unsigned long long p = pos0 + cnt + __popc(ab & lt);
+        const float4 v = __ldg(a.noff + child);
+        const float4 e = make_float4(__fadd_rn(__fmul_rn((float)ct.dx, kf), v.x),
+                                     __fadd_rn(__fmul_rn((float)ct.dy, kf), v.y),
+                                     __fadd_rn(__fmul_rn((float)ct.dz, kf), v.z), v.w);
+        if (p < lim) {
+            a.flist[p] = e;
+            if (INDEX) a.ilist[p] = (unsigned long long)child | (1ull << 32) | ((unsigned long long)ct.shc << 33);
+        }
+    }
+    cnt += __popc(ab);
+    nacc += __popc(ab);
+    const unsigned pb = __ballot_sync(FULL, push);
+    if (sp + __popc(pb) > cap) {
+        if (lt == 0u) atomicOr(&a.st->flags, ST_STACK);
+        return false;
+    }
+    if (push) stk[sp + __popc(pb & lt)] = child;
+    sp += __popc(pb);
+    return true;
+}
+
+// The first step of a walk that starts at level K = bp.kstart (see the header): the
+// level-K cells within r_cut of the group's particle box, tested like the children of an
+// opened node.  Returns false if the group must walk from the root instead (sp is then
+// untouched); sets overflow on a stack overflow.
+template <bool INDEX>
+__device__ __forceinline__ bool start_cells(const ListArgs &a, const Group &gr, const int4 tb, const int4 th,
+                                            const BoxPar &bp, uint32_t *__restrict__ stk, unsigned long long pos0,
+                                            unsigned long long lim, int lane, unsigned lt, uint32_t &cnt,
+                                            uint32_t &nacc, uint32_t &sp, bool &overflow)
+{
+    const int K = bp.kstart;
+    if (K < 2) return false;
+    const int R = bp.rprune;
+    const int quarter = kPeriod / 4;
+    if (quarter - th.x - abs(tb.x) <= R || quarter - th.y - abs(tb.y) <= R || quarter - th.z - abs(tb.z) <= R)
+        return false;
+    const int sh = 22 - K, nK = 1 << K;
+    const uint32_t mK = (uint32_t)nK - 1u;
+    // per axis: the level-K cells whose gap to the particle box is at most R (unwrapped
+    // indices from c0, n of them; the whole axis once if that many reach around)
+    auto range = [&](int gc, int t0, int t1, int &c0, int &n) {
+        const int lo = gc + t0 - t1 - R, hi = gc + t0 + t1 + R;
+        c0 = (lo - 1) >> sh;
+        n = (hi >> sh) - c0 + 1;
+        if (n >= nK) {
+            c0 = 0;
+            n = nK;
+        }
+    };
+    int cx0, nx, cy0, ny, cz0, nz;
+    range(gr.cx, tb.x, th.x, cx0, nx);
+    range(gr.cy, tb.y, th.y, cy0, ny);
+    range(gr.cz, tb.z, th.z, cz0, nz);
+    const uint32_t ncand = (uint32_t)(nx * ny * nz);
+    if (ncand > kMaxStartCells) return false;
+    const uint32_t *tb_k = a.tbl + bp.tbl_off;
+    const long long Tp = bp.T_prune;
+    const int hK = 1 << (kMaxLevel - K);  // half side of a level-K cell (u)
+    const bool acc_level = K >= bp.lmin;
+    const long long AK = bp.A[K];
+    const float kf = bp.k_f;
+    // lane's candidate t = (ix ny + iy) nz + iz, advanced by 32 per chunk
+    int iz = lane % nz, iy = (lane / nz) % ny, ix = lane / (nz * ny);
+    const int sz = 32 % nz, qz = 32 / nz, sy = qz % ny, sx = qz / ny;
+    for (uint32_t c0 = 0; c0 < ncand; c0 += 32) {
+        const uint32_t t = c0 + (uint32_t)lane;
+        bool acc = false, push = false, node_coarse = false;
+        uint32_t node = 0;
+        CellTest ct;
+        ct.dx = ct.dy = ct.dz = 0;
+        ct.shc = 0;
+        if (t < ncand) {
+            const uint32_t wx = (uint32_t)(cx0 + ix) & mK, wy = (uint32_t)(cy0 + iy) & mK,
+                           wz = (uint32_t)(cz0 + iz) & mK;
+            const uint32_t e = __ldg(tb_k + cell_morton(wx, wy, wz));
+            if (e != kNone) {
+                if (e & kCoarseLeaf) {
+                    // a leaf above level K: tested once, from the first of its cells among
+                    // the candidates (per axis, the first index whose cell is in its block)
+                    node = e & ~kCoarseLeaf;
+                    node_coarse = true;
+                    const Node nd = load_node(a.nodes + node);
+                    const int kl = (int)(nd.lvl & 255u);
+                    const uint32_t bs = 1u << (K - kl);
+                    auto first = [&](uint32_t a0, int c0a) -> int {
+                        const uint32_t w = (uint32_t)c0a & mK;
+                        return ((w - a0) & mK) < bs ? 0 : (int)((a0 - w) & mK);
+                    };
+                    const int fsh = kMaxLevel - K;
+                    if (ix == first(nd.ix >> fsh, cx0) && iy == first(nd.iy >> fsh, cy0) &&
+                        iz == first(nd.iz >> fsh, cz0)) {
+                        const int hl = 1 << (kMaxLevel - kl);
+                        ct = cell_gap<INDEX>(2 * (int)nd.ix + hl - gr.cx, 2 * (int)nd.iy + hl - gr.cy,
+                                             2 * (int)nd.iz + hl - gr.cz, hl, gr, tb, th);
+                        push = ct.Sg <= Tp;
+                    }
+                } else {
+                    node = e;
+                    ct = cell_gap<INDEX>((int)(wx << sh) + hK - gr.cx, (int)(wy << sh) + hK - gr.cy,
+                                         (int)(wz << sh) + hK - gr.cz, hK, gr, tb, th);
+                    if (ct.Sg <= Tp) {
+                        acc = acc_level && cell_dist2(ct, gr) > AK;
+                        push = !acc;
+                    }
+                }
+            }
+        }
+        if (!take_cells<INDEX>(a, acc, push, node, ct, kf, pos0, lim, lt, cnt, nacc, stk, sp, a.stack_cap)) {
+            overflow = true;
+            break;
+        }
+        if (INDEX) {
+            // a count for tests (each walk of a group counts: the rare walk into fresh
+            // pages counts twice)
+            const unsigned cb = __ballot_sync(0xffffffffu, push && node_coarse);
+            if (cb && lt == 0u) atomicAdd(&a.st->sum_coarse, (unsigned long long)__popc(cb));
+        }
+        iz += sz;
+        const int cz = iz >= nz;
+        iz -= cz ? nz : 0;
+        iy += sy + cz;
+        const int cy = iy >= ny;
+        iy -= cy ? ny : 0;
+        ix += sx + cy;
+    }
+    return true;
+}
+
 // Walks one group's list; writes entries [pos0, pos0+total) clipped at lim; returns
 // total.  stk is this warp's stack (a.stack_cap entries); an overflow sets the status.
 //
@@ -133,7 +371,8 @@ __device__ __forceinline__ int owner_lane(uint32_t off, uint32_t t)
 template <bool INDEX>
 __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb, const int4 th, const BoxPar &bp,
                                uint32_t root, uint32_t *__restrict__ stk, const uint8_t *__restrict__ octq,
-                               unsigned long long pos0, unsigned long long lim, int lane, uint32_t &nacc)
+                               unsigned long long pos0, unsigned long long lim, int lane, uint32_t &nacc,
+                               bool &from_table)
 {
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
@@ -144,9 +383,13 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
     const float kf = bp.k_f;
     const uint32_t cap = a.stack_cap;
     uint32_t cnt = 0;
-    if (lane == 0) stk[0] = root;
-    uint32_t sp = 1;
+    uint32_t sp = 0;
     bool overflow = false;
+    from_table = start_cells<INDEX>(a, gr, tb, th, bp, stk, pos0, lim, lane, lt, cnt, nacc, sp, overflow);
+    if (!from_table) {
+        if (lane == 0) stk[0] = root;
+        sp = 1;
+    }
     __syncwarp();
     while (sp > 0 && !overflow) {
         const uint32_t nb = min(sp, 32u);
@@ -197,29 +440,10 @@ __device__ uint32_t walk_group(const ListArgs &a, const Group &gr, const int4 tb
                     push = !acc;
                 }
             }
-            const unsigned ab = __ballot_sync(FULL, acc);
-            if (acc) {
-                const unsigned long long p = pos0 + cnt + __popc(ab & lt);
-                const float4 v = __ldg(a.noff + child);
-                const float4 e = make_float4(__fadd_rn(__fmul_rn((float)ct.dx, kf), v.x),
-                                             __fadd_rn(__fmul_rn((float)ct.dy, kf), v.y),
-                                             __fadd_rn(__fmul_rn((float)ct.dz, kf), v.z), v.w);
-                if (p < lim) {
-                    a.flist[p] = e;
-                    if (INDEX)
-                        a.ilist[p] = (unsigned long long)child | (1ull << 32) | ((unsigned long long)ct.shc << 33);
-                }
-            }
-            cnt += __popc(ab);
-            nacc += __popc(ab);
-            const unsigned pb = __ballot_sync(FULL, push);
-            if (sp + __popc(pb) > cap) {
-                if (lane == 0) atomicOr(&a.st->flags, ST_STACK);
+            if (!take_cells<INDEX>(a, acc, push, child, ct, kf, pos0, lim, lt, cnt, nacc, stk, sp, cap)) {
                 overflow = true;  // the caller's list is incomplete; the call is retried with a larger stack
                 break;
             }
-            if (push) stk[sp + __popc(pb & lt)] = child;
-            sp += __popc(pb);
         }
         __syncwarp();
         if (overflow) break;
@@ -320,8 +544,12 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
             if (m & (1u << o)) octq[8 * m + q++] = (uint8_t)o;
         for (; q < 8; q++) octq[8 * m + q] = 0;
     }
+    __shared__ unsigned long long tallies[kListWarps][kTallyN];
+    if (lane == 0)
+        for (int k = 0; k < kTallyN; k++) tallies[threadIdx.x >> 5][k] = 0;
     __syncthreads();
     if (a.st->flags & ST_NODE_CAP) return;  // the tree was truncated: the call is retried
+    unsigned long long *tally = tallies[threadIdx.x >> 5];
     const uint32_t G = *a.n_groups;
     uint32_t *stk = a.stack + (size_t)(blockIdx.x * kListWarps + (threadIdx.x >> 5)) * a.stack_cap;
     unsigned long long page_cur = 0, page_end = 0;
@@ -337,9 +565,12 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
         const BoxPar &bp = a.bps[gr.box];
         const uint32_t root = a.base[bp.p_begin];
         uint32_t nacc = 0;
-        const uint32_t len = walk_group<INDEX>(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc);
+        bool from_table = false;
+        const uint32_t len =
+            walk_group<INDEX>(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc, from_table);
+        if (lane == 0) tally[kTallyStart] += from_table ? 1u : 0u;
         const uint32_t padded = (len + 7u) & ~7u;
-        if (lane == 0) atomicAdd(&a.st->sum_padded, (unsigned long long)padded);
+        if (lane == 0) tally[kTallyPadded] += padded;
         if (exhausted) {
             if (lane == 0) {
                 a.loff[g] = 0;
@@ -367,7 +598,7 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
             }
             page_cur = first * a.page;
             page_end = (first + np) * a.page;
-            walk_group<INDEX>(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc);
+            walk_group<INDEX>(a, gr, tb, th, bp, root, stk, octq, page_cur, page_end, lane, nacc, from_table);
         }
         for (uint32_t t = len + lane; t < padded; t += 32) {
             a.flist[page_cur + t] = make_float4(16.f, 16.f, 16.f, 0.f);
@@ -378,10 +609,18 @@ __global__ void __launch_bounds__(kListWarps * 32, kListBlocksPerSM) k_lists(Lis
             a.llen[g] = padded;
             a.lraw[g] = len;
             if (a.qcnt) a.qcnt[g] = nacc;
-            atomicAdd(&a.st->sum_len, (unsigned long long)len);
-            atomicAdd(&a.st->sum_inter, (unsigned long long)len * gr.count);
+            tally[kTallyLen] += len;
+            tally[kTallyInter] += (unsigned long long)len * gr.count;
         }
         page_cur += padded;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        DevStatus *st = a.st;
+        if (tally[kTallyPadded]) atomicAdd(&st->sum_padded, tally[kTallyPadded]);
+        if (tally[kTallyLen]) atomicAdd(&st->sum_len, tally[kTallyLen]);
+        if (tally[kTallyInter]) atomicAdd(&st->sum_inter, tally[kTallyInter]);
+        if (tally[kTallyStart]) atomicAdd(&st->sum_start, tally[kTallyStart]);
     }
 }
 
