@@ -130,7 +130,15 @@ int greem_short_force(const double *pos, const float *mass, int64_t N, double L,
                       int n_crit, float *acc);
 
 /* The whole short-range force with explicit parameters.  acc is float32 [N,3] for
- * GREEM_F32_REL and float64 [N,3] for GREEM_F64.  Errors as greem_build_tree. */
+ * GREEM_F32_REL and float64 [N,3] for GREEM_F64.  Errors as greem_build_tree.
+ * A call that repeats the previous call on this context (the same pos, mass and acc
+ * pointers, N and parameters; new contents of pos and mass are fine) runs as one CUDA
+ * graph launch of the whole step from the third such call on: the same kernels and
+ * results, without the per-kernel launch cost.  If the new positions need more buffer
+ * space than the graph was captured with, the call falls back to the usual path, which
+ * grows the buffers and retries.  Calls with GREEM_FLAG_ADD_PM never replay;
+ * greem_debug_set(GREEM_DEBUG_REPLAY, 0) turns replays off.  greem_stats.replayed tells
+ * whether the last call replayed (stage times are measured in replays too). */
 int greem_short_force_ex(greem_ctx *ctx, const double *pos, const float *mass, int64_t N, const greem_params *p,
                          void *acc);
 
@@ -208,6 +216,7 @@ typedef struct greem_stats {
      * build index lists, GREEM_FLAG_INDEX_LISTS, 0 otherwise; a group whose list is
      * walked again into fresh pages counts its leaves twice) */
     int64_t n_start_table, n_start_coarse;
+    int64_t replayed;  /* 1 if the last greem_short_force_ex call replayed its graph, else 0 */
 } greem_stats;
 
 /* Counters of the last call.  Errors: INVALID_ARG for NULL arguments. */
@@ -257,10 +266,13 @@ int greem_debug_dump_group_lists(greem_ctx *ctx, const int64_t *groups, int64_t 
  *                             does from the usual first guesses; greem_stats.retries counts)
  *   GREEM_DEBUG_MAX_ATTEMPTS  attempts per call before GREEM_ERR_CAPACITY is returned
  *                             (default 6; value < 1 restores it).  Stays in effect.
+ *   GREEM_DEBUG_REPLAY        1 (default): repeated greem_short_force_ex calls replay a
+ *                             graph of the call; 0: they do not.  Stays in effect.
  *   GREEM_DEBUG_START_LEVEL   the deepest level (<= 7) at which a list walk may start
  *                             instead of the root (default 7; 0 or 1: every walk starts at
  *                             the root; value < 0 restores the default).  The lists hold the
  *                             same entries either way; for timing comparisons.  Stays in effect.
+ * Every setting also drops the graph that repeated greem_short_force_ex calls replay.
  * Errors: INVALID_ARG (NULL ctx, unknown what, value out of range). */
 #define GREEM_DEBUG_WAIT_POLLS 0
 #define GREEM_DEBUG_NODE_CAP 1
@@ -268,6 +280,7 @@ int greem_debug_dump_group_lists(greem_ctx *ctx, const int64_t *groups, int64_t 
 #define GREEM_DEBUG_STACK_CAP 3
 #define GREEM_DEBUG_MAX_ATTEMPTS 4
 #define GREEM_DEBUG_START_LEVEL 5
+#define GREEM_DEBUG_REPLAY 6
 int greem_debug_set(greem_ctx *ctx, int what, int64_t value);
 
 /* The FP32 list entries of selected groups exactly as the force kernel reads them, for

@@ -129,6 +129,22 @@ struct greem_ctx {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
     bool capturing = false;
+
+    // greem_short_force_ex replays a graph of a call that repeats the previous one
+    // (greem_short_force_ex below); ag_gen changes whenever a buffer is reallocated or a
+    // debug setting changes, so a graph never outlives the state it was captured from
+    struct CallKey {
+        const void *pos, *mass, *acc;
+        int64_t N;
+        greem_params p;
+        uint64_t gen;
+    };
+    cudaGraphExec_t ag_exec = nullptr;
+    cudaEvent_t stage_ev[7] = {};
+    CallKey ag_key{}, ag_seen{};
+    bool ag_seen_valid = false, ag_enabled = true;
+    long long ag_launches = 0;
+    uint64_t ag_gen = 0;
 };
 
 static bool cuda_ok(cudaError_t e)
@@ -136,6 +152,15 @@ static bool cuda_ok(cudaError_t e)
     if (e == cudaSuccess) return true;
     cudaGetLastError();
     return false;
+}
+
+// Forgets the replayable graph of greem_short_force_ex and the call it was kept for.
+static void drop_auto_graph(greem_ctx *c)
+{
+    if (c->ag_exec) cudaGraphExecDestroy(c->ag_exec);
+    c->ag_exec = nullptr;
+    c->ag_seen_valid = false;
+    c->ag_gen++;
 }
 
 template <class T>
@@ -148,6 +173,7 @@ static int ensure(greem_ctx *c, DBuf<T> &b, size_t n)
         cudaGraphExecDestroy(c->exec);
         c->exec = nullptr;
     }
+    drop_auto_graph(c);
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.n = 0;
@@ -535,7 +561,26 @@ static void download_status(greem_ctx *c, cudaStream_t s)
 
 static void ev_record(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev, int i)
 {
-    if (r.timing && !c->capturing) cudaEventRecord(ev[i], c->stream);
+    if (!r.timing || !ev) return;
+    // under capture a plain record only marks a dependency; an external record becomes a
+    // node of the graph that records the event each time the graph runs
+    if (c->capturing) cudaEventRecordWithFlags(ev[i], c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ev[i], c->stream);
+}
+
+// The stage-time events of the context (created on first use; kept, so that a captured
+// call records them too), or null if they cannot be created.
+static cudaEvent_t *stage_events(greem_ctx *c)
+{
+    if (!c->stage_ev[0])
+        for (auto &e : c->stage_ev)
+            if (!cuda_ok(cudaEventCreate(&e))) {
+                for (auto &f : c->stage_ev)
+                    if (f) cudaEventDestroy(f);
+                for (auto &f : c->stage_ev) f = nullptr;
+                return nullptr;
+            }
+    return c->stage_ev;
 }
 
 static int enqueue(greem_ctx *c, const RunCfg &r, cudaEvent_t *ev)
@@ -749,9 +794,7 @@ static int run(greem_ctx *c, RunCfg r)
     }
     c->next_node_cap = c->next_list_cap = 0;
     c->next_stack_cap = 0;
-    cudaEvent_t ev[7] = {};
-    if (r.timing)
-        for (auto &e : ev) cudaEventCreate(&e);
+    cudaEvent_t *ev = r.timing ? stage_events(c) : nullptr;
     int rc = GREEM_OK;
     c->stats.retries = 0;
     for (int attempt = 0; attempt < c->max_attempts; attempt++) {
@@ -763,8 +806,6 @@ static int run(greem_ctx *c, RunCfg r)
         grow_caps(c);
         c->stats.retries++;
     }
-    if (r.timing)
-        for (auto &e : ev) cudaEventDestroy(e);
     return rc;
 }
 
@@ -876,6 +917,9 @@ void greem_destroy(greem_ctx *c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->ag_exec) cudaGraphExecDestroy(c->ag_exec);
+    for (auto &e : c->stage_ev)
+        if (e) cudaEventDestroy(e);
     pm_plan_destroy(c->pm);
     release(c->pm_grid); release(c->pm_table); release(c->pm_spec); release(c->pm_tmp);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -919,6 +963,39 @@ int greem_build_tree(greem_ctx *c, const double *pos, const float *mass, int64_t
     return run(c, make_cfg(*p, pos, mass, nullptr, (uint32_t)N, 1, false));
 }
 
+// Captures the whole call (the kernels of enqueue, both streams) into c->ag_exec, on the
+// context's own stream (the legacy stream cannot be captured); the graph is launched on
+// the context's stream.  Nothing runs during the capture.  A capture that fails leaves no
+// graph, and the calls run as usual.
+static void capture_auto_graph(greem_ctx *c, const RunCfg &r, const greem_ctx::CallKey &key)
+{
+    if (!c->own_stream && !cuda_ok(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking))) return;
+    cudaStream_t user = c->stream;
+    c->stream = c->own_stream;
+    c->capturing = true;
+    const long long launches = greem::g_launches;
+    greem::g_launches = 0;
+    cudaGraph_t g = nullptr;
+    int rc = GREEM_ERR_CUDA;
+    if (cuda_ok(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal))) {
+        rc = enqueue(c, r, r.timing ? stage_events(c) : nullptr);
+        if (!cuda_ok(cudaStreamEndCapture(c->stream, &g))) rc = GREEM_ERR_CUDA;
+    }
+    c->capturing = false;
+    c->stream = user;
+    c->ag_launches = greem::g_launches;
+    greem::g_launches = launches;
+    if (rc == GREEM_OK && g && cuda_ok(cudaGraphInstantiate(&c->ag_exec, g, 0))) c->ag_key = key;
+    else c->ag_exec = nullptr;
+    if (g) cudaGraphDestroy(g);
+}
+
+// A call that repeats the previous one (the same device pointers, N, parameters, buffers
+// and debug settings) replays a graph of it: the whole step in one launch, with the same
+// kernels and results (stage times included: the context's stage events are recorded by
+// the graph).  The graph is captured after the second such call.  A replay whose new
+// positions overflow a capacity falls back to the usual call, which grows the buffers
+// (and drops the graph) and retries.  Calls with the PM part never replay.
 int greem_short_force_ex(greem_ctx *c, const double *pos, const float *mass, int64_t N, const greem_params *p,
                          void *acc)
 {
@@ -927,7 +1004,49 @@ int greem_short_force_ex(greem_ctx *c, const double *pos, const float *mass, int
     if (!pos || !mass || !acc) return GREEM_ERR_INVALID_ARG;
     RunCfg r = make_cfg(*p, pos, mass, acc, (uint32_t)N, 1, true);
     r.soft = p->eps > 0;
-    return run(c, r);
+    const bool eligible = c->ag_enabled && !r.add_pm && !c->capturing;
+    greem_ctx::CallKey key;
+    auto make_key = [&]() {
+        memset(&key, 0, sizeof(key));
+        key.pos = pos;
+        key.mass = mass;
+        key.acc = acc;
+        key.N = N;
+        key.p = *p;
+        key.gen = c->ag_gen;
+    };
+    auto same = [](const greem_ctx::CallKey &a, const greem_ctx::CallKey &b) { return !memcmp(&a, &b, sizeof(a)); };
+    c->stats.replayed = 0;
+    if (eligible && c->ag_exec) {
+        make_key();
+        if (same(key, c->ag_key)) {
+            c->have_tree = c->have_lists = c->have_index = c->have_quad = false;
+            if (!cuda_ok(cudaGraphLaunch(c->ag_exec, c->stream))) return GREEM_ERR_CUDA;
+            rc = finish(c, r, r.timing ? stage_events(c) : nullptr);
+            c->stats.kernel_launches = c->ag_launches;
+            c->stats.retries = 0;
+            if (rc != GREEM_ERR_CAPACITY) {
+                c->stats.replayed = 1;
+                return rc;
+            }
+            grow_caps(c);  // the usual call below reallocates, which drops the graph
+        }
+    }
+    rc = run(c, r);
+    if (rc == GREEM_OK && eligible) {
+        make_key();
+        if (c->ag_seen_valid && same(key, c->ag_seen)) {
+            if (c->ag_exec && !same(key, c->ag_key)) {  // the graph of an earlier call
+                cudaGraphExecDestroy(c->ag_exec);
+                c->ag_exec = nullptr;
+            }
+            if (!c->ag_exec) capture_auto_graph(c, r, key);
+        } else {
+            c->ag_seen = key;
+            c->ag_seen_valid = true;
+        }
+    }
+    return rc;
 }
 
 int greem_short_force_host(greem_ctx *c, int nstep, const double *const *pos, const float *const *mass,
@@ -1757,6 +1876,7 @@ int greem_let_export(greem_ctx *c, const int32_t *boxes, int ndom, int self, int
 int greem_debug_set(greem_ctx *c, int what, int64_t value)
 {
     if (!c) return GREEM_ERR_INVALID_ARG;
+    drop_auto_graph(c);  // every setting below changes what a call enqueues
     switch (what) {
     case GREEM_DEBUG_WAIT_POLLS:
         if (value > (int64_t)kWaitPolls) return GREEM_ERR_INVALID_ARG;
@@ -1781,6 +1901,10 @@ int greem_debug_set(greem_ctx *c, int what, int64_t value)
     case GREEM_DEBUG_START_LEVEL:
         if (value > 7) return GREEM_ERR_INVALID_ARG;
         c->start_cap = value < 0 ? 7 : (int)value;
+        return GREEM_OK;
+    case GREEM_DEBUG_REPLAY:
+        if (value < 0 || value > 1) return GREEM_ERR_INVALID_ARG;
+        c->ag_enabled = value != 0;
         return GREEM_OK;
     default:
         return GREEM_ERR_INVALID_ARG;

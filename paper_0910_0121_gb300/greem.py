@@ -33,7 +33,8 @@ FLAG_QUADRUPOLE = 16
 ASSIGN_CIC = 0
 ASSIGN_TSC = 1
 
-DEBUG_WAIT_POLLS, DEBUG_NODE_CAP, DEBUG_LIST_CAP, DEBUG_STACK_CAP, DEBUG_MAX_ATTEMPTS, DEBUG_START_LEVEL = range(6)
+DEBUG_WAIT_POLLS, DEBUG_NODE_CAP, DEBUG_LIST_CAP, DEBUG_STACK_CAP, DEBUG_MAX_ATTEMPTS, DEBUG_START_LEVEL, \
+    DEBUG_REPLAY = range(7)
 
 DUMP_KEYS, DUMP_PERM, DUMP_NODES, DUMP_MOMENTS, DUMP_GROUPS, DUMP_LIST_OFFSETS, DUMP_LISTS, DUMP_QUADRUPOLES = range(8)
 
@@ -60,7 +61,7 @@ class Stats(ctypes.Structure):
                [("l_min", ctypes.c_int32), ("retries", ctypes.c_int32)] + \
                [(n, ctypes.c_double) for n in ("ms_keys", "ms_sort", "ms_tree", "ms_groups", "ms_lists",
                                               "ms_force", "ms_total")] + \
-               [("n_start_table", ctypes.c_int64), ("n_start_coarse", ctypes.c_int64)]
+               [("n_start_table", ctypes.c_int64), ("n_start_coarse", ctypes.c_int64), ("replayed", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
