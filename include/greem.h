@@ -131,8 +131,8 @@ int greem_short_force(const double *pos, const float *mass, int64_t N, double L,
 
 /* The whole short-range force with explicit parameters.  acc is float32 [N,3] for
  * GREEM_F32_REL and float64 [N,3] for GREEM_F64.  Errors as greem_build_tree.
- * A call that repeats the previous call on this context (the same pos, mass and acc
- * pointers, N and parameters; new contents of pos and mass are fine) runs as one CUDA
+ * A call that repeats one of the two previous calls on this context (the same pos, mass
+ * and acc pointers, N and parameters; new contents of pos and mass are fine) runs as one CUDA
  * graph launch of the whole step from the third such call on: the same kernels and
  * results, without the per-kernel launch cost.  If the new positions need more buffer
  * space than the graph was captured with, the call falls back to the usual path, which

@@ -139,11 +139,16 @@ struct greem_ctx {
         greem_params p;
         uint64_t gen;
     };
-    cudaGraphExec_t ag_exec = nullptr;
+    // two entries, so that calls alternating between two sets of buffers (the staging
+    // slots of greem_short_force_host) replay too
+    static constexpr int kAgEntries = 2;
+    cudaGraphExec_t ag_exec[kAgEntries] = {};
+    CallKey ag_key[kAgEntries] = {}, ag_seen[kAgEntries] = {};
+    long long ag_launches[kAgEntries] = {};
+    bool ag_seen_valid[kAgEntries] = {};
+    int ag_next = 0;  // the entry the next capture replaces
+    bool ag_enabled = true;
     cudaEvent_t stage_ev[7] = {};
-    CallKey ag_key{}, ag_seen{};
-    bool ag_seen_valid = false, ag_enabled = true;
-    long long ag_launches = 0;
     uint64_t ag_gen = 0;
 };
 
@@ -157,9 +162,11 @@ static bool cuda_ok(cudaError_t e)
 // Forgets the replayable graph of greem_short_force_ex and the call it was kept for.
 static void drop_auto_graph(greem_ctx *c)
 {
-    if (c->ag_exec) cudaGraphExecDestroy(c->ag_exec);
-    c->ag_exec = nullptr;
-    c->ag_seen_valid = false;
+    for (int e = 0; e < greem_ctx::kAgEntries; e++) {
+        if (c->ag_exec[e]) cudaGraphExecDestroy(c->ag_exec[e]);
+        c->ag_exec[e] = nullptr;
+        c->ag_seen_valid[e] = false;
+    }
     c->ag_gen++;
 }
 
@@ -917,7 +924,8 @@ void greem_destroy(greem_ctx *c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     if (c->exec) cudaGraphExecDestroy(c->exec);
-    if (c->ag_exec) cudaGraphExecDestroy(c->ag_exec);
+    for (auto &g : c->ag_exec)
+        if (g) cudaGraphExecDestroy(g);
     for (auto &e : c->stage_ev)
         if (e) cudaEventDestroy(e);
     pm_plan_destroy(c->pm);
@@ -967,7 +975,7 @@ int greem_build_tree(greem_ctx *c, const double *pos, const float *mass, int64_t
 // context's own stream (the legacy stream cannot be captured); the graph is launched on
 // the context's stream.  Nothing runs during the capture.  A capture that fails leaves no
 // graph, and the calls run as usual.
-static void capture_auto_graph(greem_ctx *c, const RunCfg &r, const greem_ctx::CallKey &key)
+static void capture_auto_graph(greem_ctx *c, const RunCfg &r, const greem_ctx::CallKey &key, int slot)
 {
     if (!c->own_stream && !cuda_ok(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking))) return;
     cudaStream_t user = c->stream;
@@ -983,15 +991,16 @@ static void capture_auto_graph(greem_ctx *c, const RunCfg &r, const greem_ctx::C
     }
     c->capturing = false;
     c->stream = user;
-    c->ag_launches = greem::g_launches;
+    c->ag_launches[slot] = greem::g_launches;
     greem::g_launches = launches;
-    if (rc == GREEM_OK && g && cuda_ok(cudaGraphInstantiate(&c->ag_exec, g, 0))) c->ag_key = key;
-    else c->ag_exec = nullptr;
+    if (rc == GREEM_OK && g && cuda_ok(cudaGraphInstantiate(&c->ag_exec[slot], g, 0))) c->ag_key[slot] = key;
+    else c->ag_exec[slot] = nullptr;
     if (g) cudaGraphDestroy(g);
 }
 
-// A call that repeats the previous one (the same device pointers, N, parameters, buffers
-// and debug settings) replays a graph of it: the whole step in one launch, with the same
+// A call that repeats one of the two previous ones (the same device pointers, N,
+// parameters, buffers and debug settings) replays a graph of it: the whole step in one
+// launch, with the same
 // kernels and results (stage times included: the context's stage events are recorded by
 // the graph).  The graph is captured after the second such call.  A replay whose new
 // positions overflow a capacity falls back to the usual call, which grows the buffers
@@ -1017,33 +1026,50 @@ int greem_short_force_ex(greem_ctx *c, const double *pos, const float *mass, int
     };
     auto same = [](const greem_ctx::CallKey &a, const greem_ctx::CallKey &b) { return !memcmp(&a, &b, sizeof(a)); };
     c->stats.replayed = 0;
-    if (eligible && c->ag_exec) {
+    constexpr int E = greem_ctx::kAgEntries;
+    if (eligible) {
         make_key();
-        if (same(key, c->ag_key)) {
+        for (int e = 0; e < E; e++) {
+            if (!c->ag_exec[e] || !same(key, c->ag_key[e])) continue;
             c->have_tree = c->have_lists = c->have_index = c->have_quad = false;
-            if (!cuda_ok(cudaGraphLaunch(c->ag_exec, c->stream))) return GREEM_ERR_CUDA;
+            if (!cuda_ok(cudaGraphLaunch(c->ag_exec[e], c->stream))) return GREEM_ERR_CUDA;
             rc = finish(c, r, r.timing ? stage_events(c) : nullptr);
-            c->stats.kernel_launches = c->ag_launches;
+            c->stats.kernel_launches = c->ag_launches[e];
             c->stats.retries = 0;
             if (rc != GREEM_ERR_CAPACITY) {
                 c->stats.replayed = 1;
                 return rc;
             }
-            grow_caps(c);  // the usual call below reallocates, which drops the graph
+            grow_caps(c);  // the usual call below reallocates, which drops the graphs
+            break;
         }
     }
     rc = run(c, r);
     if (rc == GREEM_OK && eligible) {
-        make_key();
-        if (c->ag_seen_valid && same(key, c->ag_seen)) {
-            if (c->ag_exec && !same(key, c->ag_key)) {  // the graph of an earlier call
-                cudaGraphExecDestroy(c->ag_exec);
-                c->ag_exec = nullptr;
+        make_key();  // run() may have reallocated: the generation is the current one
+        int seen = -1;
+        for (int e = 0; e < E; e++)
+            if (c->ag_seen_valid[e] && same(key, c->ag_seen[e])) seen = e;
+        if (seen >= 0) {
+            // the second call of this kind among the recent ones: capture it for the next
+            int slot = -1;
+            for (int e = 0; e < E; e++)
+                if (c->ag_exec[e] && same(key, c->ag_key[e])) slot = e;
+            if (slot < 0) {
+                slot = c->ag_next;
+                c->ag_next = (c->ag_next + 1) % E;
+                if (c->ag_exec[slot]) cudaGraphExecDestroy(c->ag_exec[slot]);
+                c->ag_exec[slot] = nullptr;
+                capture_auto_graph(c, r, key, slot);
             }
-            if (!c->ag_exec) capture_auto_graph(c, r, key);
         } else {
-            c->ag_seen = key;
-            c->ag_seen_valid = true;
+            // remember it in place of the older of the recent calls
+            for (int e = E - 1; e > 0; e--) {
+                c->ag_seen[e] = c->ag_seen[e - 1];
+                c->ag_seen_valid[e] = c->ag_seen_valid[e - 1];
+            }
+            c->ag_seen[0] = key;
+            c->ag_seen_valid[0] = true;
         }
     }
     return rc;

@@ -1,5 +1,5 @@
-"""greem_short_force_ex replays a CUDA graph of a call that repeats the previous one (the
-same pointers, N and parameters).  A replay must give exactly what the usual call gives,
+"""greem_short_force_ex replays a CUDA graph of a call that repeats one of the two previous
+ones (the same pointers, N and parameters).  A replay must give exactly what the usual call gives,
 also when the buffers hold new positions, and must fall back to the usual call when the
 new positions need more list space than the graph was captured with."""
 import numpy as np
@@ -117,3 +117,26 @@ def test_no_replay_when_off_or_when_the_call_changes(setup):
     assert _call(ctx, P, M, q, other)["replayed"] == 0
     assert _call(ctx, P, M, q, other)["replayed"] == 0
     assert _call(ctx, P, M, q, other)["replayed"] == 1
+
+
+def test_host_buffer_calls_replay_through_both_staging_slots():
+    """greem_short_force_host alternates two device staging slots, so its problems repeat
+    two calls: both are captured, and the later problems replay, with the results of a
+    context that never replays."""
+    mass = np.random.default_rng(4).uniform(0.5, 1.5, N).astype(np.float32) / N
+    p = greem.params(L=1.0, r_cut=0.08, theta=0.5, n_crit=64)
+    sets = [_uniform(10 + k) for k in range(7)]
+    hpos = [torch.from_numpy(x).pin_memory() for x in sets]
+    hmass = [torch.from_numpy(mass).pin_memory() for _ in sets]
+    outs = {}
+    for replay in (0, 1):
+        ctx = greem.Context()
+        ctx.debug_set(greem.DEBUG_REPLAY, replay)
+        try:
+            outs[replay] = [a.numpy().copy() for a in ctx.short_force_host(hpos, hmass, p)]
+            assert ctx.stats()["replayed"] == replay
+        finally:
+            ctx.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(outs[1][0], _direct(sets[0], mass, p))
