@@ -422,6 +422,42 @@ def tree_vs_direct(pos, mass, prm, rows):
     return out
 
 
+def config1_leg(ctx, stream, steps=50):
+    """The 32^3 uniform set (r_cut = 3/32, theta = 0.5, n_crit = 64), whose whole step is
+    short next to the launch cost of its kernels: the call timed as a user repeating it
+    (a graph replay of the whole call from the third call on) and with replays off (every
+    kernel launched on its own)."""
+    import torch
+    from paper_0910_0121_gb300 import greem, synth
+    pos, mass, prm = synth.config_uniform32()
+    N = len(pos)
+    P, M = torch.from_numpy(pos).cuda(), torch.from_numpy(mass).cuda()
+    acc = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    q = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=prm["n_crit"] or 64,
+                     n_leaf=prm.get("n_leaf", 10))
+    out = {"workload": "uniform32: 32^3 uniform", "N": N, "r_cut": prm["r_cut"], "theta": prm["theta"],
+           "n_crit": q.n_crit}
+    try:
+        for name, replay in (("replayed", 1), ("launched", 0)):
+            ctx.debug_set(greem.DEBUG_REPLAY, replay)
+            for _ in range(3):
+                ctx.short_force(P, M, q, acc)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(steps):
+                ctx.short_force(P, M, q, acc)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / steps
+            st = ctx.stats()
+            out[name] = {"ms_per_step": ms, "particles_per_s": N / (ms * 1e-3), "replayed": st["replayed"],
+                         "kernels": st["kernel_launches"]}
+    finally:
+        ctx.debug_set(greem.DEBUG_REPLAY, 1)
+    return out
+
+
 def config2_leg(ctx, stream, steps=5):
     """The 128^3 NFW mix (half uniform, half in 1000 NFW halos), r_cut = 3/128, theta = 0.5,
     n_crit = 64: the FP32 relative-coordinate force against the plain FP64 form, step and
@@ -876,6 +912,7 @@ def gpu_arm(args, rank, world, local):
     if rank == 0 and not args.no_direct:
         line["tree_vs_direct"] = tree_vs_direct(pos, mass, prm, rows)
     if rank == 0 and not args.no_extras:
+        line["extras"]["config1"] = guarded(config1_leg, ctx, stream)
         line["extras"]["config2"] = guarded(config2_leg, ctx, stream)
         line["extras"]["domains8"] = guarded(domains8_leg, P, M, p, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
