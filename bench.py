@@ -232,7 +232,7 @@ def reference_arm(args, rank, world):
     v = N / statistics.mean(times)
     line = {"metric": METRIC, "value": v, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "N": N, "theta": prm["theta"], "r_cut": prm["r_cut"], "n_crit": n_crit,
                        "n_leaf": 10},
@@ -940,7 +940,7 @@ def config5_arm(args):
     _build.build()
     leg = config5_leg(args)
     line = {k: leg[k] for k in ("metric", "value", "unit", "steps", "warmup", "ms_per_step")}
-    line.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+    line.update({"n_gpus": 1, "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
                  "data": "synthetic",
                  "config": {k: leg[k] for k in ("workload", "N", "r_cut", "theta", "n_crit", "n_pm", "assign",
                                                  "graph")}})
