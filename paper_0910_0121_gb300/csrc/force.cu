@@ -304,6 +304,57 @@ __device__ __forceinline__ void quad_pair(float dx, float dy, float dz, const fl
     az = fmaf(B, fmaf(q1.z, dz, qz), fmaf(sd, dz, az));
 }
 
+// Packed form of quad_pair for I = 2H i-particles: the same operations in the same order
+// on pairs of i-particles, so each half gives quad_pair's result bit for bit; the r = 0
+// select and the saturating clamps are scalar.
+template <int H>
+__device__ __forceinline__ void interact_quad2(const float4 j, const float4 q0, const float4 q1,
+                                               const f32x2 (&xi)[H], const f32x2 (&yi)[H], const f32x2 (&zi)[H],
+                                               f32x2 (&ax)[H], f32x2 (&ay)[H], f32x2 (&az)[H])
+{
+    const f32x2 jx = pk(j.x, j.x), jy = pk(j.y, j.y), jz = pk(j.z, j.z);
+    const f32x2 qxx = pk(q0.x, q0.x), qyy = pk(q0.y, q0.y), qzz = pk(q0.z, q0.z), qxy = pk(q0.w, q0.w);
+    const f32x2 qxz = pk(q1.x, q1.x), qyz = pk(q1.y, q1.y), qtr = pk(q1.z, q1.z);
+    auto c2 = [](float c) { return pk(c, c); };
+#pragma unroll
+    for (int h = 0; h < H; h++) {
+        const f32x2 dx = sub2(jx, xi[h]), dy = sub2(jy, yi[h]), dz = sub2(jz, zi[h]);
+        const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+        float rl, rh;
+        upk(r2, rl, rh);
+        const f32x2 rinv = pk(rl > 0.0f ? rsqrtf(rl) : 0.0f, rh > 0.0f ? rsqrtf(rh) : 0.0f);
+        const f32x2 R = mul2(r2, rinv);
+        float Rl, Rh;
+        upk(R, Rl, Rh);
+        const f32x2 v = pk(fma_sat(Rl, -0.5f, 1.0f), fma_sat(Rh, -0.5f, 1.0f));
+        const f32x2 u = pk(add_sat(1.0f, -Rl), add_sat(1.0f, -Rh));
+        const f32x2 v2 = mul2(v, v), v3 = mul2(v2, v), v4 = mul2(v2, v2);
+        const f32x2 u2 = mul2(u, u), u4 = mul2(u2, u2), u5 = mul2(u4, u);
+        const f32x2 F = fma2(fma2(fma2(fma2(R, c2(-4.0f), c2(-10.057142857142857f)), R, c2(-8.457142857142857f)), R,
+                                  c2(-5.485714285714286f)),
+                             R, c2(-2.742857142857143f));
+        const f32x2 G = fma2(fma2(fma2(R, c2(-1.0f), c2(-2.257142857142857f)), R, c2(-1.2857142857142858f)), R,
+                             c2(-0.2571428571428571f));
+        const f32x2 Hp = fma2(fma2(fma2(fma2(fma2(R, c2(3.0f), c2(7.0285714285714285f)), R, c2(12.17142857142857f)), R,
+                                        c2(12.685714285714285f)),
+                                   R, c2(10.285714285714286f)),
+                              R, c2(6.857142857142857f));
+        const f32x2 K = fma2(fma2(fma2(fma2(R, c2(1.5f), c2(3.257142857142857f)), R, c2(4.0285714285714285f)), R,
+                                  c2(2.5714285714285716f)),
+                             R, c2(0.6428571428571429f));
+        const f32x2 ri2 = mul2(rinv, rinv), ri5 = mul2(mul2(ri2, ri2), rinv), ri7 = mul2(ri5, ri2);
+        const f32x2 B = mul2(fma2(v4, F, mul2(u5, G)), ri5);
+        const f32x2 Ch = mul2(fma2(v3, Hp, mul2(u4, K)), ri7);
+        const f32x2 qx = fma2(qxx, dx, fma2(qxy, dy, mul2(qxz, dz)));
+        const f32x2 qy = fma2(qxy, dx, fma2(qyy, dy, mul2(qyz, dz)));
+        const f32x2 qz = fma2(qxz, dx, fma2(qyz, dy, mul2(qzz, dz)));
+        const f32x2 sd = mul2(Ch, fma2(dx, qx, fma2(dy, qy, mul2(dz, qz))));
+        ax[h] = fma2(B, fma2(qtr, dx, qx), fma2(sd, dx, ax[h]));
+        ay[h] = fma2(B, fma2(qtr, dy, qy), fma2(sd, dy, ay[h]));
+        az[h] = fma2(B, fma2(qtr, dz, qz), fma2(sd, dz, az[h]));
+    }
+}
+
 template <int I>
 __device__ __forceinline__ void interact_quad(const float4 j, const float4 q0, const float4 q1, const float (&xi)[I],
                                               const float (&yi)[I], const float (&zi)[I], float (&ax)[I],
@@ -467,7 +518,7 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
         zi[s] = QUAD ? 2.0f * v.z : v.z;
         ax[s] = ay[s] = az[s] = 0.f;
     }
-    constexpr bool kPacked = !QUAD && (I % 2) == 0;
+    constexpr bool kPacked = (I % 2) == 0;
     constexpr uint32_t stride = QUAD ? 3u : 1u;
     const uint32_t ce = QUAD ? (uint32_t)a.chunk / 4u : (uint32_t)a.chunk;
     const float4 *src = QUAD ? a.qlist : a.flist;
@@ -502,7 +553,11 @@ __device__ __noinline__ bool group_pass(const ForceArgs &a, const Group &gr, uin
         wp.ph[b] ^= 1u;
         const float4 *buf = wp.buf[b];
         const uint32_t nj = min(ce, len - c * ce);
-        if constexpr (QUAD) {
+        if constexpr (QUAD && kPacked) {
+#pragma unroll 1
+            for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S)
+                interact_quad2<H>(buf[3 * t], buf[3 * t + 1], buf[3 * t + 2], xi2, yi2, zi2, ax2, ay2, az2);
+        } else if constexpr (QUAD) {
 #pragma unroll 1
             for (uint32_t t = (uint32_t)part; t < nj; t += (uint32_t)S)
                 interact_quad<I>(buf[3 * t], buf[3 * t + 1], buf[3 * t + 2], xi, yi, zi, ax, ay, az);
