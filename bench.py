@@ -802,7 +802,7 @@ def gpu_arm(args, rank, world, local):
     if args.n_crit:
         best = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=args.n_crit, n_leaf=10)
     else:
-        best = ctx.autotune(P, M, base, acc, candidates=[48, 64, 96, 128, 192, 256])
+        best = ctx.autotune(P, M, base, acc, candidates=[48, 64, 96, 128, 160, 192, 256])
     p = greem.params(L=best.L, r_cut=best.r_cut, theta=best.theta, n_crit=best.n_crit, n_leaf=best.n_leaf,
                      list_chunk=best.list_chunk, block_shape=best.block_shape, flags=greem.FLAG_STAGE_TIMES)
 

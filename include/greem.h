@@ -298,8 +298,8 @@ int greem_debug_dump_group_entries(greem_ctx *ctx, const int64_t *groups, int64_
                                    float *entries, int64_t *index_entries, int64_t cap_entries,
                                    int64_t *n_entries);
 
-/* Picks n_crit from candidates[0..ncand) (ncand = 0 -> 32, 48, 64, 96, 128, 192, 256, 384,
- * 512) at p's list_chunk and block_shape, then list_chunk and block_shape at that n_crit,
+/* Picks n_crit from candidates[0..ncand) (ncand = 0 -> 32, 48, 64, 96, 128, 160, 192, 256,
+ * 384, 512) at p's list_chunk and block_shape, then list_chunk and block_shape at that n_crit,
  * then re-times the neighbouring n_crit candidates at the chosen shape; each setting is
  * timed on the whole force over these inputs (best of three calls).  Writes the best
  * parameters to *best (a copy of *p with those three fields set).  acc is scratch output

@@ -1554,7 +1554,7 @@ int greem_autotune(greem_ctx *c, const double *pos, const float *mass, int64_t N
                    const int *candidates, int ncand, void *acc, greem_params *best)
 {
     if (!c || !p || !best) return GREEM_ERR_INVALID_ARG;
-    static const int def_cand[] = {32, 48, 64, 96, 128, 192, 256, 384, 512};
+    static const int def_cand[] = {32, 48, 64, 96, 128, 160, 192, 256, 384, 512};
     if (!candidates || ncand <= 0) {
         candidates = def_cand;
         ncand = (int)(sizeof(def_cand) / sizeof(def_cand[0]));
