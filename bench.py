@@ -889,6 +889,7 @@ def gpu_arm(args, rank, world, local):
         "force_kernel_ms": fms, "lists_kernel_ms": statistics.mean(lists_ms),
         "stage_ms": {k: round(statistics.mean(v), 3) for k, v in stage.items()},
         "n_groups": st["n_groups"], "n_nodes": st["n_nodes"], "n_list_entries": st["n_list_entries"],
+        "list_walks_from_level_K": st["n_start_table"], "step_replays_a_graph": bool(st["replayed"]),
         "pct_fp32_peak_force": 100.0 * achieved / peak,
         "pct_fp32_measured_ffma_force": 100.0 * achieved / peak_meas,
         "fp32_ffma_microbench_tflops": peak_meas,
