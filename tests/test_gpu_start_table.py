@@ -3,7 +3,9 @@ exactly the entries of the walk from the root, so they are compared with the ora
 recursive lists bit for bit, and with the GPU's own root walk (start level 0) entry by
 entry, FP32 values included.
 
-Each set is built to reach one branch of the start:
+Each of the first three sets is built to reach one branch of the start (the others are
+edge cases: just above the size from which walks start below the root, every particle at
+one point, positions outside the box and on its faces):
   coarse -- a dense clump in a sparse background: most of the box's leaves sit above the
             start level, so the table names them and each must be taken once;
   wide   -- r_cut close to L/4: groups whose particle box reaches too far for the image
@@ -45,7 +47,30 @@ def _many():
     return rng.random((40000, 3)), dict(L=1.0, r_cut=0.05, theta=0.5, n_crit=800, n_leaf=10)
 
 
-SETS = {"coarse": _coarse, "wide": _wide, "many": _many}
+def _threshold():
+    """One particle above the size from which the walks start below the root."""
+    rng = np.random.default_rng(34)
+    return rng.random((4097, 3)), dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=32, n_leaf=10)
+
+
+def _coincident():
+    """Every particle at one point: one leaf at the finest level holds them all."""
+    return np.tile(np.array([[0.3, 0.7, 0.1]]), (5000, 1)), dict(L=1.0, r_cut=0.1, theta=0.5, n_crit=64, n_leaf=10)
+
+
+def _wrapped():
+    """Positions outside [0, L) (wrapped), on the faces, and a coincident clump."""
+    rng = np.random.default_rng(35)
+    pos = rng.random((6000, 3))
+    pos[:600] += rng.integers(-3, 4, (600, 3))
+    pos[600] = [1.0, 0.0, -0.0]
+    pos[601] = [np.nextafter(1.0, 0), 0.5, 0.5]
+    pos[700:760] = pos[761]
+    return pos, dict(L=1.0, r_cut=0.08, theta=0.6, n_crit=48, n_leaf=10)
+
+
+SETS = {"coarse": _coarse, "wide": _wide, "many": _many, "threshold": _threshold, "coincident": _coincident,
+        "wrapped": _wrapped}
 
 
 def _t(a, dt):
@@ -90,9 +115,11 @@ def test_start_table_lists_equal_root_walk_and_oracle(name):
     assert st0["n_start_table"] == 0
     if name == "coarse":
         assert st["n_start_table"] > n_groups // 2 and st["n_start_coarse"] > 0, st
-    else:
+    elif name in ("wide", "many"):
         # the fallback: some (wide: typically all) groups walk from the root
         assert st["n_start_table"] < n_groups, st
+    else:
+        assert st["n_start_table"] > 0, st
     T = oracle.Tree(pos, mass, prm["L"], prm["r_cut"], n_crit=prm["n_crit"], n_leaf=prm["n_leaf"])
     T.build_lists(prm["theta"])
     toff, kind, idx, sh = T.lists()
