@@ -234,8 +234,9 @@ def reference_arm(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "N": N, "theta": prm["theta"], "r_cut": prm["r_cut"], "n_crit": n_crit,
-                       "n_leaf": 10},
+            "config": {"workload": WORKLOAD, "N": N, "L": 1.0, "r_cut": prm["r_cut"], "theta": prm["theta"],
+                       "n_crit": n_crit, "n_leaf": 10, "list_chunk": 0, "block_shape": 0,
+                       "l2": "inputs (470 MB) larger than L2, no flush", "parallelism": "domains 1x1x1"},
             "cpu_baseline": {"value": v, "unit": "particles/s", "cores": nth, "kind": "oracle", "sample": desc},
             "projected": True, "sample_wall_ms_per_step": 1e3 * statistics.mean(walls),
             "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -802,7 +803,7 @@ def gpu_arm(args, rank, world, local):
     if args.n_crit:
         best = greem.params(L=prm["L"], r_cut=prm["r_cut"], theta=prm["theta"], n_crit=args.n_crit, n_leaf=10)
     else:
-        best = ctx.autotune(P, M, base, acc, candidates=[48, 64, 96, 128, 160, 192, 256])
+        best = ctx.autotune(P, M, base, acc, candidates=[48, 64, 96, 128, 192, 256])
     p = greem.params(L=best.L, r_cut=best.r_cut, theta=best.theta, n_crit=best.n_crit, n_leaf=best.n_leaf,
                      list_chunk=best.list_chunk, block_shape=best.block_shape, flags=greem.FLAG_STAGE_TIMES)
 
