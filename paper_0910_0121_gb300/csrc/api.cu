@@ -492,13 +492,15 @@ static int size_buffers(greem_ctx *c, const RunCfg &r)
         ENS(flist, c->list_cap);
         if (r.index_lists) ENS(ilist, c->list_cap);
     }
-    // start levels and table offsets (multiples of 64 entries: 16-byte aligned stores)
+    // start levels and table offsets (multiples of 64 entries: 16-byte aligned stores);
+    // a table entry flags a leaf in bit 31, so node indices must stay below 2^31
     size_t tbl_n = 0;
     c->tbl_kmax = 0;
+    const bool tables = r.lists_force && nc < 0x80000000ull;
     for (int b = 0; b < r.nbox; b++) {
         BoxPar &bp = c->bps_host[b];
         const uint32_t nb = c->box_off_host[b + 1] - c->box_off_host[b];
-        bp.kstart = r.lists_force ? start_level(bp, nb, c->start_cap) : 0;
+        bp.kstart = tables ? start_level(bp, nb, c->start_cap) : 0;
         bp.tbl_off = tbl_n;
         if (bp.kstart) tbl_n += (size_t)1 << (3 * bp.kstart);
         c->tbl_kmax = std::max(c->tbl_kmax, bp.kstart);
