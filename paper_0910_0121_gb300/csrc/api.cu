@@ -973,10 +973,10 @@ int greem_build_tree(greem_ctx *c, const double *pos, const float *mass, int64_t
     return run(c, make_cfg(*p, pos, mass, nullptr, (uint32_t)N, 1, false));
 }
 
-// Captures the whole call (the kernels of enqueue, both streams) into c->ag_exec, on the
-// context's own stream (the legacy stream cannot be captured); the graph is launched on
-// the context's stream.  Nothing runs during the capture.  A capture that fails leaves no
-// graph, and the calls run as usual.
+// Captures the whole call (the kernels of enqueue, both streams) into c->ag_exec[slot],
+// on the context's own stream (the legacy stream cannot be captured); the graph is
+// launched on the context's stream.  Nothing runs during the capture.  A capture that
+// fails leaves no graph and turns the context's replays off; the calls run as usual.
 static void capture_auto_graph(greem_ctx *c, const RunCfg &r, const greem_ctx::CallKey &key, int slot)
 {
     if (!c->own_stream && !cuda_ok(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking))) return;
@@ -995,18 +995,22 @@ static void capture_auto_graph(greem_ctx *c, const RunCfg &r, const greem_ctx::C
     c->stream = user;
     c->ag_launches[slot] = greem::g_launches;
     greem::g_launches = launches;
-    if (rc == GREEM_OK && g && cuda_ok(cudaGraphInstantiate(&c->ag_exec[slot], g, 0))) c->ag_key[slot] = key;
-    else c->ag_exec[slot] = nullptr;
+    if (rc == GREEM_OK && g && cuda_ok(cudaGraphInstantiate(&c->ag_exec[slot], g, 0))) {
+        c->ag_key[slot] = key;
+    } else {
+        c->ag_exec[slot] = nullptr;
+        c->ag_enabled = false;  // not retried on every later call
+    }
     if (g) cudaGraphDestroy(g);
 }
 
 // A call that repeats one of the two previous ones (the same device pointers, N,
 // parameters, buffers and debug settings) replays a graph of it: the whole step in one
-// launch, with the same
-// kernels and results (stage times included: the context's stage events are recorded by
-// the graph).  The graph is captured after the second such call.  A replay whose new
-// positions overflow a capacity falls back to the usual call, which grows the buffers
-// (and drops the graph) and retries.  Calls with the PM part never replay.
+// launch, with the same kernels and results (stage times included: the context's stage
+// events are recorded by the graph).  The graph is captured after the second such call;
+// if a capture fails, the context stops replaying.  A replay whose new positions
+// overflow a capacity falls back to the usual call, which grows the buffers (and drops
+// the graph) and retries.  Calls with the PM part never replay.
 int greem_short_force_ex(greem_ctx *c, const double *pos, const float *mass, int64_t N, const greem_params *p,
                          void *acc)
 {
