@@ -958,7 +958,7 @@ void greem_destroy(greem_ctx *c)
     release(c->lvl); release(c->bps); release(c->box_off); release(c->small); release(c->st);
     release(c->qlist); release(c->qcnt); release(c->qoff);
     release(c->dom_boxes); release(c->dom); release(c->dom_cnt); release(c->let_flag); release(c->let_cnt);
-    release(c->let_ends);
+    release(c->let_ends); release(c->tbl);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->bps_host) cudaFreeHost(c->bps_host);
     if (c->box_off_host) cudaFreeHost(c->box_off_host);
