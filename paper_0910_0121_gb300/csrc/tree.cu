@@ -14,6 +14,8 @@
 // prefix, so K_i comes from a sliding maximum over such windows.  Particle i then owns
 // the nodes (i, d_i) ... (i, K_i); an exclusive scan of the ownership counts numbers
 // the nodes in DFS preorder, because preorder is the order of (begin, level).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace greem {
@@ -116,18 +118,13 @@ __device__ __forceinline__ uint32_t cell_end(const uint64_t *__restrict__ keys, 
     return hi;
 }
 
-__global__ void __launch_bounds__(256) k_tree_fill(const uint64_t *__restrict__ keys, uint32_t N,
-                                                   const uint32_t *__restrict__ box_off, int nbox,
-                                                   const uint8_t *__restrict__ d8, const uint8_t *__restrict__ K8,
-                                                   const uint32_t *__restrict__ base, Node *__restrict__ nodes,
-                                                   uint32_t node_cap, DevStatus *st)
+// The nodes owned by sorted particle i (own > 0 of them, numbered from b0).
+__device__ __forceinline__ void fill_nodes(const uint64_t *__restrict__ keys, uint32_t i, uint32_t b0,
+                                           const uint32_t *__restrict__ box_off, int nbox,
+                                           const uint8_t *__restrict__ d8, const uint8_t *__restrict__ K8,
+                                           const uint32_t *__restrict__ base, Node *__restrict__ nodes,
+                                           uint32_t node_cap)
 {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const uint32_t b0 = base[i];
-    const uint32_t own = base[i + 1] - b0;
-    if (i == N - 1 && base[N] > node_cap) atomicOr(&st->flags, ST_NODE_CAP);
-    if (own == 0) return;
     const int b = box_of(i, box_off, nbox);
     const uint32_t e = box_off[b + 1];
     const int d = d8[i], K = K8[i];
@@ -158,12 +155,54 @@ __global__ void __launch_bounds__(256) k_tree_fill(const uint64_t *__restrict__ 
     }
 }
 
+// About one particle in five owns nodes.  Each warp queues the owners among its 32
+// particles in shared memory and fills nodes 32 owners at a time, so that every lane of
+// a filling warp has an owner's galloping searches to run.
+__global__ void __launch_bounds__(256) k_tree_fill(const uint64_t *__restrict__ keys, uint32_t N,
+                                                   const uint32_t *__restrict__ box_off, int nbox,
+                                                   const uint8_t *__restrict__ d8, const uint8_t *__restrict__ K8,
+                                                   const uint32_t *__restrict__ base, Node *__restrict__ nodes,
+                                                   uint32_t node_cap, DevStatus *st)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ uint32_t queue[8][64];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t *q = queue[w];
+    uint32_t qn = 0;  // queued owners (the same in every lane)
+    const uint32_t nchunks = (N + 31) / 32, nwarps = gridDim.x * 8;
+    for (uint32_t ch = blockIdx.x * 8 + (uint32_t)w; ch < nchunks; ch += nwarps) {
+        const uint32_t i = ch * 32 + (uint32_t)lane;
+        bool owner = false;
+        if (i < N) {
+            owner = base[i + 1] > base[i];
+            if (i == N - 1 && base[N] > node_cap) atomicOr(&st->flags, ST_NODE_CAP);
+        }
+        const unsigned m = __ballot_sync(FULL, owner);
+        if (owner) q[qn + __popc(m & lt)] = i;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            const uint32_t j = q[lane];
+            fill_nodes(keys, j, base[j], box_off, nbox, d8, K8, base, nodes, node_cap);
+            __syncwarp();
+            if ((uint32_t)lane < qn - 32) q[lane] = q[32 + lane];  // at most 31 left, from slots 32..62
+            __syncwarp();
+            qn -= 32;
+        }
+    }
+    if ((uint32_t)lane < qn) {
+        const uint32_t j = q[lane];
+        fill_nodes(keys, j, base[j], box_off, nbox, d8, K8, base, nodes, node_cap);
+    }
+}
+
 void launch_tree_fill(const uint64_t *keys, uint32_t N, const uint32_t *box_off, int nbox, const uint8_t *d8,
                       const uint8_t *K8, const uint32_t *base, Node *nodes, uint32_t node_cap, DevStatus *st,
                       cudaStream_t s, int nsm)
 {
-    (void)nsm;
-    k_tree_fill<<<(N + 255) / 256, 256, 0, s>>>(keys, N, box_off, nbox, d8, K8, base, nodes, node_cap, st);
+    const unsigned grid = (unsigned)std::min<size_t>((N + 255) / 256, (size_t)nsm * 8);
+    k_tree_fill<<<grid, 256, 0, s>>>(keys, N, box_off, nbox, d8, K8, base, nodes, node_cap, st);
     g_launches++;
 }
 
