@@ -134,3 +134,37 @@ def test_start_table_lists_equal_root_walk_and_oracle(name):
         assert np.array_equal(a, b)
     print(f"{name}: {n_groups} groups, {st['n_start_table']} from the table, "
           f"{st['n_start_coarse']} coarse leaves, {len(ls)} entries")
+
+
+def test_batched_boxes_each_with_their_own_table():
+    """Several boxes in one call, each above the size threshold with its own start level and
+    its own table (at its own offset), beside a small box that walks from the root; box
+    sides 1, 3 (not a power of two) and 0.5.  Each box's accelerations equal its single-box
+    call bit for bit."""
+    rng = np.random.default_rng(36)
+    specs = [(6000, 1.0, 0.06), (9000, 3.0, 0.2), (700, 1.0, 0.1), (5000, 0.5, 0.03)]
+    boxes, prms = [], []
+    for n, L, rc in specs:
+        boxes.append(rng.random((n, 3)) * L)
+        prms.append(dict(L=L, r_cut=rc, theta=0.5, n_crit=48, n_leaf=10))
+    masses = [rng.uniform(0.5, 1.5, len(b)).astype(np.float32) / len(b) for b in boxes]
+    ctx = greem.Context()
+    try:
+        singles, starts = [], []
+        for p, m, prm in zip(boxes, masses, prms):
+            a = ctx.short_force(_t(p, np.float64), _t(m, np.float32), greem.params(**prm))
+            torch.cuda.synchronize()
+            singles.append(a.cpu().numpy())
+            starts.append(ctx.stats()["n_start_table"])
+        assert all(s > 0 for s, (n, _, _) in zip(starts, specs) if n > 4096), starts
+        assert starts[2] == 0
+        off = np.cumsum([0] + [len(b) for b in boxes])
+        acc = ctx.short_force_batched(_t(np.concatenate(boxes), np.float64), _t(np.concatenate(masses), np.float32),
+                                      off, [greem.params(**q) for q in prms])
+        torch.cuda.synchronize()
+        assert ctx.stats()["n_start_table"] == sum(starts)
+        acc = acc.cpu().numpy()
+        for b in range(len(boxes)):
+            assert np.array_equal(acc[off[b]:off[b + 1]], singles[b]), b
+    finally:
+        ctx.close()
