@@ -140,3 +140,25 @@ def test_host_buffer_calls_replay_through_both_staging_slots():
     for a, b in zip(outs[0], outs[1]):
         assert np.array_equal(a, b)
     assert np.array_equal(outs[1][0], _direct(sets[0], mass, p))
+
+
+@pytest.mark.parametrize("variant", ["quadrupole", "fp64", "softened", "eq12"])
+def test_replays_of_every_variant_equal_the_usual_call(setup, variant):
+    """The second-order passes, the FP64 form, softening and the Eq. 12 opening angle each
+    enqueue other kernels: their replays too equal a context that never replays."""
+    ctx, P, M, _, mass = setup
+    kw = dict(L=1.0, r_cut=0.08, theta=0.5, n_crit=64)
+    if variant == "quadrupole":
+        kw.update(flags=greem.FLAG_QUADRUPOLE)
+    elif variant == "fp64":
+        kw.update(precision=greem.F64)
+    elif variant == "softened":
+        kw.update(eps=1e-3)
+    else:
+        kw.update(flags=greem.FLAG_THETA_EQ12, theta0=0.25, theta=0.7)
+    p = greem.params(**kw)
+    dt = torch.float64 if variant == "fp64" else torch.float32
+    out = torch.empty((N, 3), dtype=dt, device="cuda")
+    seen = [_call(ctx, P, M, p, out)["replayed"] for _ in range(3)]
+    assert seen == [0, 0, 1]
+    assert np.array_equal(out.cpu().numpy(), _direct(_uniform(1), mass, p))
