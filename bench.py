@@ -235,7 +235,7 @@ def reference_arm(args, rank, world):
             "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "N": N, "L": 1.0, "r_cut": prm["r_cut"], "theta": prm["theta"],
-                       "n_crit": n_crit, "n_leaf": 10, "list_chunk": 0, "block_shape": 0,
+                       "n_crit": n_crit, "n_leaf": 10, "list_chunk": 256, "block_shape": 16,
                        "l2": "inputs (470 MB) larger than L2, no flush", "parallelism": "domains 1x1x1"},
             "cpu_baseline": {"value": v, "unit": "particles/s", "cores": nth, "kind": "oracle", "sample": desc},
             "projected": True, "sample_wall_ms_per_step": 1e3 * statistics.mean(walls),
@@ -756,7 +756,8 @@ def domain_arm(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "L": 1.0, "r_cut": fprm["r_cut"], "theta": fprm["theta"],
                    "n_crit": fprm["n_crit"], "n_leaf": 10, "list_chunk": 256, "block_shape": 16,
-                   "l2": "inputs larger than L2, no flush", "parallelism": f"domains {grid[0]}x{grid[1]}x{grid[2]}",
+                   "l2": "inputs (470 MB) larger than L2, no flush",
+                   "parallelism": f"domains {grid[0]}x{grid[1]}x{grid[2]}",
                    "dist_backend": args.dist_backend},
         "domains": {"grid": list(grid), "n_local": per["n_local"], "n_import": per["n_import"],
                     "force_ms": per["force_ms"], "let_bytes_sent": per["let_bytes_sent"],
@@ -883,7 +884,7 @@ def gpu_arm(args, rank, world, local):
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "L": 1.0, "r_cut": p.r_cut, "theta": p.theta, "n_crit": p.n_crit,
-                   "n_leaf": p.n_leaf, "list_chunk": p.list_chunk, "block_shape": p.block_shape,
+                   "n_leaf": p.n_leaf, "list_chunk": p.list_chunk or 256, "block_shape": p.block_shape or 16,
                    "l2": "inputs (470 MB) larger than L2, no flush", "parallelism": "domains 1x1x1"},
         "interactions_per_s": world * inter / (ms * 1e-3),
         "N_int": inter / N,
