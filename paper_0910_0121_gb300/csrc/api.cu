@@ -806,6 +806,7 @@ static int run(greem_ctx *c, RunCfg r)
     cudaEvent_t *ev = r.timing ? stage_events(c) : nullptr;
     int rc = GREEM_OK;
     c->stats.retries = 0;
+    c->stats.replayed = 0;
     for (int attempt = 0; attempt < c->max_attempts; attempt++) {
         greem::g_launches = 0;
         rc = enqueue(c, r, ev);
